@@ -1,0 +1,409 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test ties an oracle function to a closed form, a brute-force Kronecker
+construction, an invariant, an independent dense-matrix evolution, or the
+paper's own listing, so that a dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import workloads as W
+from oracle import ensemble as oe
+from oracle import qaoa as oq
+from oracle import statevector as sv
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2.0)
+I2 = np.eye(2, dtype=np.complex128)
+P0 = np.diag([1.0, 0.0]).astype(np.complex128)
+P1 = np.diag([0.0, 1.0]).astype(np.complex128)
+
+
+def kron_all(factors_by_qubit):
+    """Dense operator from per-qubit factors; factor k acts on qubit k
+    (bit k of the index), so the most significant qubit is leftmost."""
+    M = np.array([[1.0 + 0j]])
+    for k in reversed(range(len(factors_by_qubit))):
+        M = np.kron(M, factors_by_qubit[k])
+    return M
+
+
+def rand_state(n, g):
+    z = g.standard_normal(1 << n) + 1j * g.standard_normal(1 << n)
+    return z / np.linalg.norm(z)
+
+
+# ---------------------------------------------------------------- gates
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 6])
+def test_apply_1q_matches_kronecker(n):
+    g = W.rng(100 + n)
+    for q in range(n):
+        for U in (W.haar_u2(g), g.standard_normal((2, 2)) + 1j * g.standard_normal((2, 2))):
+            psi = rand_state(n, g)
+            f = [I2] * n
+            f = list(f)
+            f[q] = U
+            ref = kron_all(f) @ psi
+            got = sv.apply_1q(psi, q, U)
+            np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_apply_c1q_matches_kronecker(n):
+    g = W.rng(200 + n)
+    for c in range(n):
+        for t in range(n):
+            if c == t:
+                continue
+            U = W.haar_u2(g)
+            psi = rand_state(n, g)
+            f0 = [I2] * n
+            f1 = [I2] * n
+            f0 = list(f0)
+            f1 = list(f1)
+            f0[c] = P0
+            f1[c] = P1
+            f1[t] = U
+            M = kron_all(f0) + kron_all(f1)
+            np.testing.assert_allclose(sv.apply_c1q(psi, c, t, U), M @ psi, rtol=0, atol=1e-13)
+
+
+def test_c1q_rejects_equal_qubits():
+    with pytest.raises(ValueError):
+        sv.apply_c1q(sv.basis_state(3, 0), 1, 1, I2)
+
+
+def test_unitary_preserves_norm_and_inverts():
+    g = W.rng(7)
+    n = 8
+    psi = rand_state(n, g)
+    cur = psi
+    gates = [(int(g.integers(n)), W.haar_u2(g)) for _ in range(40)]
+    for q, U in gates:
+        cur = sv.apply_1q(cur, q, U)
+        assert abs(sv.norm2(cur) - 1.0) < 1e-13
+    for q, U in reversed(gates):
+        cur = sv.apply_1q(cur, q, U.conj().T)
+    np.testing.assert_allclose(cur, psi, rtol=0, atol=1e-13)
+
+
+def test_pauli_x_and_cnot_are_exact_permutations():
+    g = W.rng(8)
+    n = 6
+    psi = rand_state(n, g)
+    x = np.arange(1 << n)
+    for q in range(n):
+        out = sv.apply_1q(psi, q, sv.PAULI["X"])
+        assert np.array_equal(out, psi[x ^ (1 << q)])
+    for c, t in [(0, 5), (5, 0), (2, 3)]:
+        out = sv.apply_c1q(psi, c, t, sv.PAULI["X"])
+        perm = np.where((x >> c) & 1, x ^ (1 << t), x)
+        assert np.array_equal(out, psi[perm])
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("n", [1, 4, 9])
+def test_hadamard_everywhere_gives_uniform(n):
+    psi = sv.basis_state(n, 0)
+    for q in range(n):
+        psi = sv.apply_1q(psi, q, H)
+    np.testing.assert_allclose(psi, np.full(1 << n, 2.0 ** (-n / 2)), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(psi, sv.uniform_state(n), rtol=0, atol=1e-15)
+    for q in range(n):
+        assert abs(sv.probability(psi, q) - 0.5) < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_ghz_state_and_its_expectations(n):
+    psi = sv.apply_1q(sv.basis_state(n, 0), 0, H)
+    for k in range(1, n):
+        psi = sv.apply_c1q(psi, 0, k, sv.PAULI["X"])
+    ref = np.zeros(1 << n, dtype=np.complex128)
+    ref[0] = ref[-1] = 1 / np.sqrt(2)
+    np.testing.assert_allclose(psi, ref, rtol=0, atol=1e-15)
+    assert abs(sv.expectation(psi, "X" * n) - 1.0) < 1e-14
+    for i in range(n):
+        assert abs(sv.expectation(psi, "".join("Z" if k == i else "I" for k in range(n)))) < 1e-14
+        for j in range(i + 1, n):
+            s = "".join("Z" if k in (i, j) else "I" for k in range(n))
+            assert abs(sv.expectation(psi, s) - 1.0) < 1e-14
+    if n == 3:
+        # GHZ: <XXX> = 1 and <XYY> = <YXY> = <YYX> = -1 fix the sign of Y.
+        for s in ("XYY", "YXY", "YYX"):
+            assert abs(sv.expectation(psi, s) + 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("n,j", [(3, 5), (5, 11), (6, 0), (7, 93)])
+def test_qft_of_basis_state(n, j):
+    """QFT from H and controlled phases diag(1, e^{i pi / 2^k}) (bit order
+    reversed at the end instead of swaps): |j> -> sum_k e^{2 pi i j k / N} |k> / sqrt(N)."""
+    psi = sv.basis_state(n, j)
+    for i in reversed(range(n)):
+        psi = sv.apply_1q(psi, i, H)
+        for m in reversed(range(i)):
+            k = i - m
+            Rk = np.diag([1.0, np.exp(1j * np.pi / 2 ** k)])
+            psi = sv.apply_c1q(psi, m, i, Rk)
+    N = 1 << n
+    k = np.arange(N)
+    rev = np.array([int(format(x, f"0{n}b")[::-1], 2) for x in k])
+    expect = np.exp(2j * np.pi * j * k / N) / np.sqrt(N)
+    np.testing.assert_allclose(psi[rev], expect, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- measurement
+def test_probability_of_basis_states_is_exact():
+    n = 5
+    for idx in (0, 1, 6, 31, 20):
+        psi = sv.basis_state(n, idx)
+        for q in range(n):
+            assert sv.probability(psi, q) == float((idx >> q) & 1)
+
+
+def test_probability_brute_force_and_z_identity():
+    g = W.rng(11)
+    n = 6
+    psi = rand_state(n, g)
+    for q in range(n):
+        brute = sum(abs(psi[i]) ** 2 for i in range(1 << n) if (i >> q) & 1)
+        p = sv.probability(psi, q)
+        assert abs(p - brute) < 1e-14
+        z = sv.expectation(psi, "".join("Z" if k == q else "I" for k in range(n)))
+        assert abs(z.real - sv.expectation_z_from_probability(p)) < 1e-14
+        assert abs(z.real - (1 - 2 * p)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_pauli_expectation_matches_kronecker_all_strings(n):
+    g = W.rng(300 + n)
+    psi = rand_state(n, g)
+    import itertools
+    for chars in itertools.product("IXYZ", repeat=n):
+        s = "".join(chars)
+        M = kron_all([sv.PAULI[c] for c in s])
+        ref = np.vdot(psi, M @ psi)
+        got = sv.expectation(psi, s)
+        assert abs(got - ref) < 1e-14
+        assert abs(got.imag) < 1e-14
+
+
+def test_masks_to_pauli():
+    assert sv.masks_to_pauli(4, 0b0011, 0b0110) == "XYZI"
+    assert sv.masks_to_pauli(3, 0, 0) == "III"
+
+
+def test_paper_listing_golden():
+    with open(os.path.join(GOLDEN, "paper_listing_basic_use.json")) as f:
+        gd = json.load(f)
+    n = gd["num_qubits"]
+    named = {"X": sv.PAULI["X"], "H": H}
+    ops = []
+    for op in gd["ops"]:
+        if op[0] == "1q":
+            ops.append(("1q", op[1], named[op[2]]))
+        else:
+            ops.append(("cx", op[1], op[2]))
+    psi = oe.run_ops(n, ops, sv.basis_state(n, gd["init_basis_index"]))
+    ref = np.zeros(1 << n, dtype=np.complex128)
+    for k, (re, im) in gd["amplitudes_nonzero"].items():
+        ref[int(k)] = re + 1j * im
+    np.testing.assert_allclose(psi, ref, rtol=0, atol=1e-15)
+    p = sv.probability(psi, gd["measured_qubit"])
+    assert abs(p - gd["probability"]) < 1e-15
+    assert abs(sv.expectation_z_from_probability(p) - gd["expectation_z"]) < 1e-15
+
+
+def test_rx_product_state_probabilities():
+    """Pool-of-states appendix circuit without noise: RX(theta_q) on each
+    qubit of |0..0> gives P(q = 1) = sin^2(theta_q / 2)."""
+    g = W.rng(777777)
+    n = 10
+    th = g.uniform(0, np.pi, size=n)
+    psi = oe.run_ops(n, [("1q", q, oq.rx(th[q])) for q in range(n)])
+    for q in range(n):
+        assert abs(sv.probability(psi, q) - np.sin(th[q] / 2) ** 2) < 1e-14
+
+
+# ---------------------------------------------------------------- Max-Cut phase
+def test_cut_values_brute_force():
+    g = W.rng(5)
+    n = 7
+    edges = np.array([(0, 1), (1, 2), (2, 6), (3, 5), (0, 6), (4, 5)])
+    w = g.uniform(0.5, 2.0, size=len(edges))
+    C = sv.cut_values(n, edges, w)
+    Cu = sv.cut_values(n, edges)
+    for x in range(1 << n):
+        bits = [(x >> k) & 1 for k in range(n)]
+        assert abs(C[x] - sum(wi for (u, v), wi in zip(edges, w) if bits[u] != bits[v])) < 1e-13
+        assert Cu[x] == sum(1 for (u, v) in edges if bits[u] != bits[v])
+
+
+def test_zz_phase_matches_cnot_phase_cnot():
+    """exp(-i gamma (x_u XOR x_v)) per edge equals CNOT(u->v), the phase
+    diag(1, e^{-i gamma}) on v, CNOT(u->v): built from the gate path."""
+    g = W.rng(9)
+    n = 6
+    edges = W.random_3regular_graph(n, 3)
+    gamma = 0.7318
+    psi = rand_state(n, g)
+    ref = psi.copy()
+    for u, v in edges:
+        ref = sv.apply_c1q(ref, int(u), int(v), sv.PAULI["X"])
+        ref = sv.apply_1q(ref, int(v), np.diag([1.0, np.exp(-1j * gamma)]))
+        ref = sv.apply_c1q(ref, int(u), int(v), sv.PAULI["X"])
+    np.testing.assert_allclose(sv.apply_zz_phase(psi, edges, None, gamma), ref, rtol=0, atol=1e-13)
+
+
+def test_random_3regular_graph_is_simple_and_regular():
+    for n, s in [(4, 1), (16, 2), (24, 3), (28, 4)]:
+        e = W.random_3regular_graph(n, s)
+        assert e.shape == (3 * n // 2, 2)
+        assert np.all(e[:, 0] < e[:, 1])
+        assert len({tuple(x) for x in e}) == len(e)
+        assert np.all(np.bincount(e.ravel(), minlength=n) == 3)
+
+
+# ---------------------------------------------------------------- QAOA
+def _wang_p1_energy(n, edges, gamma, beta):
+    """Closed form of p=1 QAOA Max-Cut (Wang, Hadfield, Jiang, Rieffel,
+    PRA 97, 022304 (2018)), per edge (u, v) with d = deg(u)-1, e = deg(v)-1
+    and f triangles through the edge:
+      1/2 + 1/4 sin(4b) sin(g) (cos^d g + cos^e g)
+          - 1/4 sin^2(2b) cos^(d+e-2f) g (1 - cos^f 2g).
+    Works for complex arguments (used for complex-step derivatives)."""
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        adj[int(u)].add(int(v))
+        adj[int(v)].add(int(u))
+    tot = 0
+    for u, v in edges:
+        u, v = int(u), int(v)
+        d, e = len(adj[u]) - 1, len(adj[v]) - 1
+        f = len(adj[u] & adj[v])
+        tot = tot + 0.5 + 0.25 * np.sin(4 * beta) * np.sin(gamma) * (np.cos(gamma) ** d + np.cos(gamma) ** e) \
+            - 0.25 * np.sin(2 * beta) ** 2 * np.cos(gamma) ** (d + e - 2 * f) * (1 - np.cos(2 * gamma) ** f)
+    return tot
+
+
+GRAPHS = {
+    "k4": np.array([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]),
+    "prism": np.array([(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (0, 3), (1, 4), (2, 5)]),
+    "path5": np.array([(0, 1), (1, 2), (2, 3), (3, 4)]),
+    "rr8": W.random_3regular_graph(8, 21),
+    "rr10": W.random_3regular_graph(10, 22),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_qaoa_p1_matches_closed_form(name):
+    edges = GRAPHS[name]
+    n = int(edges.max()) + 1
+    g = W.rng(31)
+    for _ in range(4):
+        gm, bt = g.uniform(-np.pi, np.pi), g.uniform(-np.pi / 2, np.pi / 2)
+        E = oq.qaoa_energy(n, edges, [gm], [bt])
+        assert abs(E - _wang_p1_energy(n, edges, gm, bt)) < 1e-12
+
+
+def _dense_qaoa_energy(n, edges, gammas, betas):
+    """Independent construction: dense matrices and scipy's expm."""
+    C = np.zeros(1 << n)
+    for x in range(1 << n):
+        C[x] = sum(1 for u, v in edges if ((x >> int(u)) & 1) != ((x >> int(v)) & 1))
+    B = sum(kron_all([sv.PAULI["X"] if k == j else I2 for k in range(n)]) for j in range(n))
+    psi = np.full(1 << n, 2 ** (-n / 2), dtype=np.complex128)
+    for gm, bt in zip(gammas, betas):
+        psi = np.exp(-1j * gm * C) * psi
+        psi = scipy.linalg.expm(-1j * bt * B) @ psi
+    return float(np.real(np.vdot(psi, C * psi)))
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_qaoa_deeper_matches_dense_expm(p):
+    edges = W.random_3regular_graph(6, 40 + p)
+    gm, bt = W.qaoa_parameter_sets(p, 2, 50 + p)
+    for k in range(2):
+        E = oq.qaoa_energy(6, edges, gm[k], bt[k])
+        assert abs(E - _dense_qaoa_energy(6, edges, gm[k], bt[k])) < 1e-12
+        assert -1e-12 <= E <= oq.maxcut_brute_force(6, edges) + 1e-12
+        assert abs(E - oq.qaoa_energy(6, edges, -gm[k], -bt[k])) < 1e-12
+
+
+def test_qaoa_gradient_p1_complex_step_of_closed_form():
+    h = 1e-30
+    for name in ("k4", "prism", "rr8"):
+        edges = GRAPHS[name]
+        n = int(edges.max()) + 1
+        gm, bt = 0.6123, -0.2871
+        dg_ref = _wang_p1_energy(n, edges, gm + 1j * h, bt).imag / h
+        db_ref = _wang_p1_energy(n, edges, gm, bt + 1j * h).imag / h
+        E, dg, db = oq.qaoa_energy_grad_stored(n, edges, [gm], [bt])
+        assert abs(E - _wang_p1_energy(n, edges, gm, bt)) < 1e-12
+        assert abs(dg[0] - dg_ref) < 1e-11
+        assert abs(db[0] - db_ref) < 1e-11
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_qaoa_gradient_stored_matches_finite_differences(p):
+    n = 8
+    edges = W.random_3regular_graph(n, 60 + p)
+    gm, bt = W.qaoa_parameter_sets(p, 1, 70 + p)
+    E, dg, db = oq.qaoa_energy_grad_stored(n, edges, gm[0], bt[0])
+    fg, fb = oq.qaoa_energy_grad_fd(n, edges, gm[0], bt[0])
+    assert abs(E - oq.qaoa_energy(n, edges, gm[0], bt[0])) < 1e-12
+    np.testing.assert_allclose(dg, fg, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(db, fb, rtol=0, atol=1e-7)
+
+
+# ---------------------------------------------------------------- noise ensemble
+def _density_matrix_channel(n, ops, sigma):
+    """Exact mean state of the noisy trajectories: each X/Z rotation with
+    angle ~ N(0, sigma^2) averages to rho -> a rho + (1 - a) s rho s with
+    a = (1 + exp(-sigma^2 / 2)) / 2."""
+    a = (1 + np.exp(-sigma ** 2 / 2)) / 2
+    rho = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    rho[0, 0] = 1
+    def op_matrix(op):
+        if op[0] == "1q":
+            return kron_all([op[2] if k == op[1] else I2 for k in range(n)])
+        c, t = op[1], op[2]
+        return kron_all([P0 if k == c else I2 for k in range(n)]) + \
+            kron_all([P1 if k == c else (sv.PAULI["X"] if k == t else I2) for k in range(n)])
+    for op in ops:
+        M = op_matrix(op)
+        rho = M @ rho @ M.conj().T
+        touched = (op[1],) if op[0] == "1q" else (op[1], op[2])
+        for q in touched:
+            for s in ("X", "Z"):
+                S = kron_all([sv.PAULI[s] if k == q else I2 for k in range(n)])
+                rho = a * rho + (1 - a) * S @ rho @ S
+    return np.real(np.diag(rho))
+
+
+def test_noise_ensemble_converges_to_channel():
+    n, sigma, T = 3, 0.35, 3000
+    g = W.rng(99)
+    ops = [("1q", q, W.haar_u2(g)) for q in range(n)] + [("cx", 0, 1), ("cx", 1, 2)] + \
+          [("1q", q, W.haar_u2(g)) for q in range(n)]
+    n_noise = sum(1 if op[0] == "1q" else 2 for op in ops)
+    angles = g.normal(0, sigma, size=(T, n_noise, 2))
+    per = np.array([oe.all_probabilities(oe.run_ops(n, oe.noisy_trajectory_ops(ops, a))) for a in angles])
+    mean = oe.pool_average(per)
+    diag = _density_matrix_channel(n, ops, sigma)
+    x = np.arange(1 << n)
+    exact = np.array([diag[(x >> q) & 1 == 1].sum() for q in range(n)])
+    stderr = per.std(axis=0) / np.sqrt(T)
+    assert np.all(np.abs(mean - exact) < 5 * stderr + 1e-12)
+    # zero angles reduce the trajectory to the noiseless circuit
+    zero = oe.run_ops(n, oe.noisy_trajectory_ops(ops, np.zeros((n_noise, 2))))
+    np.testing.assert_allclose(zero, oe.run_ops(n, ops), rtol=0, atol=1e-15)
+
+
+def test_pool_average_is_sum_over_count():
+    v = np.array([[1.0, 2.0], [3.0, 6.0], [5.0, 1.0]])
+    np.testing.assert_array_equal(oe.pool_average(v), np.array([3.0, 3.0]))
