@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark of the state-vector gate engine on GB300.
+
+Workload (one "step"): the single-state gate sweep on a 30-qubit complex128
+state (16 GiB, seeded Gaussian amplitudes, normalised): apply_1q with a
+seeded Haar-random unitary on every target q = 0..29, apply_c1q CNOT on 64
+seeded random (control, target) pairs, then GetProbability of every qubit (one
+read), one Pauli-product expectation and the squared norm.  This mirrors the
+paper's "random 2x2 gate on every qubit" sweep (Section 3, "Strong scaling").
+
+value = algorithmic HBM bytes of the step (2 x 16 B x 2^n per one-qubit gate,
+2 x 16 B x 2^(n-1) per CNOT, 16 B x 2^n per reduction read) / step time, GB/s.
+
+Multi-GPU: the single state does not shard (no collectives); with N ranks
+each GPU runs an independent replica and value sums the replicas' bytes over
+the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the host on a bounded sample
+of the same sweep (a smaller state, same gate mix) in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1q-gate HBM GB/s at 30q (frac of peak); batched QAOA energy+grad evals/s vs plain"
+SEED_STATE, SEED_U, SEED_CNOT = 30, 31, 32
+N_CNOT = 64
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["iqs", "reference"], default="iqs")
+    ap.add_argument("--qubits", type=int, default=30)
+    ap.add_argument("--math", choices=["auto", "emulated", "native"], default="auto")
+    ap.add_argument("--cpu-qubits", type=int, default=24, help="state size of the CPU-oracle sample")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+def sweep_ops(n: int):
+    import workloads as W
+    Us = W.haar_u2_list(SEED_U, n)
+    pairs = W.cnot_pairs(n, N_CNOT, SEED_CNOT)
+    pauli = "".join("XYZI"[(3 * k + 1) % 4] for k in range(n))
+    return Us, pairs, pauli
+
+
+def step_bytes(n: int, amp: int = 16) -> dict:
+    N = 1 << n
+    return {"1q": n * 2 * amp * N, "cnot": N_CNOT * 2 * amp * (N // 2), "reduce": 3 * amp * N}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def run_oracle_sample(n: int):
+    """One pass of the sweep (the same gate mix, drawn for n qubits) through
+    the FP64 oracle on an n-qubit state; returns seconds."""
+    import workloads as W
+    from oracle import statevector as sv
+    Us, pairs, pauli = sweep_ops(n)
+    psi = W.gaussian_state(n, SEED_STATE)
+    X = sv.PAULI["X"]
+    t0 = time.perf_counter()
+    for q in range(n):
+        psi = sv.apply_1q(psi, q, Us[q])
+    for c, t in pairs:
+        psi = sv.apply_c1q(psi, int(c), int(t), X)
+    _ = [sv.probability(psi, q) for q in range(n)]
+    _ = sv.expectation(psi, pauli)
+    _ = sv.norm2(psi)
+    return time.perf_counter() - t0
+
+
+def oracle_bytes(n: int) -> int:
+    N = 1 << n
+    return n * 2 * 16 * N + N_CNOT * 2 * 16 * (N // 2) + 3 * 16 * N
+
+
+def cpu_baseline(args):
+    n = args.cpu_qubits
+    dt = run_oracle_sample(n)
+    return {"value": round(oracle_bytes(n) / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one sweep pass (n 1q gates + {N_CNOT} CNOT + all P(1) + Pauli expectation + norm) "
+                      f"on a {n}-qubit complex128 state instead of 30 qubits; numpy FP64, single thread, "
+                      f"{dt:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.cpu_qubits
+    for _ in range(args.warmup):
+        run_oracle_sample(n)
+    times = [run_oracle_sample(n) for _ in range(args.steps)]
+    tot = sum(times)
+    v = oracle_bytes(n) * args.steps / tot / 1e9
+    line = {"metric": METRIC, "value": round(v, 3), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"gate sweep through the FP64 CPU oracle, {n}-qubit complex128 sample of the "
+                                   f"30-qubit sweep", "qubits": n},
+            "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n}-qubit complex128 state, full sweep per step"},
+            "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9 or parts[0] not in ("0",):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power))}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(kernel_key: str):
+    """Per-launch DRAM bytes recorded from ncu for ``kernel_key``, if its
+    sources are unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel_key]
+    except (OSError, KeyError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for rel in rec["sources"]:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
+
+
+# ---------------------------------------------------------------- GPU arm
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2001_10554_gb300 as iqs
+    from paper_2001_10554_gb300 import _lib
+    from paper_2001_10554_gb300.register import mat8
+
+    n = args.qubits
+    N = 1 << n
+    Us, pairs, pauli = sweep_ops(n)
+    U8 = [mat8(U) for U in Us]
+    X8 = mat8(np.array([[0, 1], [1, 0]]))
+
+    # seeded Gaussian state, generated on the device (input data), normalised
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(SEED_STATE + rank)
+        state = torch.empty(N, dtype=torch.complex128, device=dev)
+        state.view(torch.float64).normal_(generator=gen)
+        state.div_(torch.linalg.vector_norm(state))
+    stream.synchronize()
+    reg = iqs.Register.wrap(state, stream=stream)
+    reg.set_math(args.math)
+    L = _lib.lib
+
+    ev_pairs = []
+
+    def step(record_1q: bool):
+        h = reg.handle
+        for q in range(n):
+            if record_1q:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            _lib.check(L.iqs_apply_1q(h, q, U8[q]), "iqs_apply_1q")
+            if record_1q:
+                b.record(stream)
+                ev_pairs.append((a, b))
+        for c, t in pairs:
+            _lib.check(L.iqs_apply_c1q(h, int(c), int(t), X8), "iqs_apply_c1q")
+        probs = reg.probabilities()
+        ex = reg.expectation(pauli)
+        nn = reg.norm2()
+        return probs, ex, nn
+
+    for _ in range(args.warmup):
+        step(False)
+    reg.synchronize()
+
+    clocks = ClockSampler() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    launches0 = _lib.kernel_launches()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        probs, ex, nn = step(True)
+    t_end.record(stream)
+    t_end.synchronize()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    launches = _lib.kernel_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    reg.synchronize()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    sb = step_bytes(n)
+    bytes_step = sum(sb.values())
+    value = world * bytes_step * args.steps / (elapsed_ms * 1e-3) / 1e9
+    g1 = [a.elapsed_time(b) for a, b in ev_pairs]
+    avg_1q_ms = float(np.mean(g1))
+    per_q = np.array(g1).reshape(args.steps, n).mean(axis=0)
+    achieved = sb["1q"] / n / (avg_1q_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    kernel_key = "k_c128_df" if (args.math != "native") else "k_c128_native"
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        try:
+            host_in = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+            host_out = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+            host_in.copy_(state)
+            nbytes = N * 16
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                reg.upload_ptr(host_in.data_ptr(), nbytes)
+                step(False)
+                reg.download_ptr(host_out.data_ptr(), nbytes)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            e2e = {"value": round(world * bytes_step * args.e2e_steps / dt / 1e9, 2), "unit": "GB/s",
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * (n + 2),
+                   "steps": args.e2e_steps, "path": "iqs_upload (pinned host) + sweep + iqs_download (pinned host)"}
+            del host_in, host_out
+        except RuntimeError as exc:
+            e2e = {"value": None, "unit": "GB/s", "error": str(exc)[:200]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 storage, double-float arithmetic" if args.math != "native" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"single-state gate sweep, {n}-qubit complex128 "
+                                   f"({N * 16 / 2**30:.0f} GiB): apply_1q(Haar U) on q=0..{n-1} + {N_CNOT} CNOT "
+                                   f"+ all-qubit P(1) + Pauli expectation + norm",
+                       "qubits": n, "math": args.math, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (state 16 GiB >> 129 MB)"},
+            "roofline": {"kernel": kernel_key, "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": kernel_traffic(kernel_key),
+                         "bytes_per_launch": sb["1q"] // n, "avg_launch_ms": round(avg_1q_ms, 4),
+                         "per_target_ms": [round(float(x), 3) for x in per_q]},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "check": {"norm2": nn, "expectation": ex, "p_mean": float(np.mean(probs))},
+        }
+        print(json.dumps(line), flush=True)
+    reg.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

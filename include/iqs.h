@@ -1,0 +1,184 @@
+/*
+ * iqs.h -- C ABI of the GB300 (sm_103a) state-vector gate engine.
+ *
+ * Operations follow arXiv 2001.10554 ("Intel Quantum Simulator"): a register
+ * holds the 2^n complex amplitudes alpha_i of an n-qubit pure state, with
+ * index i = sum_q i_q 2^q, so qubit q is bit q and qubit 0 the least
+ * significant bit (Section 2, "Distributed implementation", Eq. 1 and the
+ * binary index notation before it).  The whole state lives in the memory of
+ * one GPU; there is no sharding and no inter-GPU communication.
+ *
+ * Memory layout: amplitudes are stored interleaved (re, im), contiguous, in
+ * index order -- complex64 = 8 bytes (two float32), complex128 = 16 bytes
+ * (two float64) per amplitude.  This is the layout of a 1-D torch.complex64
+ * / torch.complex128 CUDA tensor.
+ *
+ * Arithmetic: complex64 registers compute gates in FP32.  complex128
+ * registers compute gates either in native FP64 or, by default on large
+ * states, in a double-float emulation on the FP32 pipe (the sm_103a FP64 pipe
+ * is far too slow to keep pace with HBM); the emulation keeps about 47
+ * significant bits per operation.  Every reduction (norm, probability,
+ * expectation, energy) accumulates in at least FP64-equivalent precision for
+ * both dtypes.
+ *
+ * Conventions for every function:
+ *   - Matrices U are 2x2 complex, row-major, as 8 doubles
+ *     {Re U00, Im U00, Re U01, Im U01, Re U10, Im U10, Re U11, Im U11},
+ *     always given in FP64 on the host (rounded to FP32 for complex64).
+ *   - Calls are ordered on the register's CUDA stream and asynchronous,
+ *     except those that return a host value (they synchronise that stream).
+ *   - Host pointers are only read during the call; the caller keeps
+ *     ownership of every pointer it passes.
+ *   - Every call returns an iqs_status and never aborts or prints.  On
+ *     IQS_EINVAL the register's state is left untouched; IQS_ERANGE reports
+ *     out-of-range amplitudes met by earlier emulated complex128 kernels;
+ *     iqs_last_error() gives a message (thread-local).
+ */
+#ifndef IQS_H
+#define IQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iqs_reg iqs_reg; /* opaque register handle */
+
+typedef enum { IQS_C64 = 0, IQS_C128 = 1 } iqs_dtype;
+
+typedef enum {
+  IQS_OK = 0,
+  IQS_EINVAL = 1,    /* bad argument: qubit out of range, c == t, bad Pauli character, size mismatch */
+  IQS_ENOMEM = 2,    /* device or pinned-host allocation failed */
+  IQS_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  IQS_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+  IQS_EINTERNAL = 5, /* internal consistency check failed */
+  IQS_ERANGE = 6     /* an amplitude outside the emulated-FP64 range was met (|a| >= 2^64, Inf or NaN) */
+} iqs_status;
+
+typedef enum {
+  IQS_MATH_AUTO = 0,     /* complex128: native FP64 below 2^20 amplitudes, emulated above */
+  IQS_MATH_EMULATED = 1, /* complex128: double-float on the FP32 pipe */
+  IQS_MATH_NATIVE = 2    /* complex128: native FP64 (DFMA) */
+} iqs_math;
+
+#define IQS_MAX_QUBITS 34
+
+/* ------------------------------------------------------------ registers */
+
+/* Section 2 "Scope and basic use": QubitRegister(num_qubits) allocates the
+ * state.  Allocates 2^n amplitudes of ``dtype`` on the current CUDA device
+ * (owned; freed by iqs_destroy) plus small scratch for reductions, and sets
+ * the state to |0...0>.  ``stream`` is a cudaStream_t or NULL (legacy default
+ * stream).  n in [1, IQS_MAX_QUBITS].  Errors: IQS_EINVAL, IQS_ENOMEM, IQS_ECUDA. */
+iqs_status iqs_create(int n, int dtype, void* stream, iqs_reg** out);
+
+/* Same as iqs_create but borrows ``device_ptr`` (2^n amplitudes of ``dtype``,
+ * 16-byte aligned, on the current device), e.g. a torch tensor's storage.
+ * The contents are not modified; iqs_destroy never frees the borrowed buffer,
+ * and the caller keeps it alive while the register exists. */
+iqs_status iqs_wrap(int n, int dtype, void* device_ptr, void* stream, iqs_reg** out);
+
+/* Frees what the register owns (synchronising its stream first).  NULL is OK. */
+iqs_status iqs_destroy(iqs_reg* reg);
+
+/* Device address of the amplitudes, number of qubits, dtype. */
+iqs_status iqs_data(const iqs_reg* reg, void** device_ptr);
+iqs_status iqs_info(const iqs_reg* reg, int* n, int* dtype);
+
+/* Stream on which later calls are ordered (cudaStream_t or NULL). */
+iqs_status iqs_set_stream(iqs_reg* reg, void* stream);
+
+/* Arithmetic mode of complex128 gates (an iqs_math value); ignored for complex64. */
+iqs_status iqs_set_math(iqs_reg* reg, int math);
+
+/* Block the host until the register's stream is idle; reports IQS_ERANGE if
+ * an emulated complex128 gate met an out-of-range amplitude since the last
+ * check (the flag is cleared by the check). */
+iqs_status iqs_synchronize(iqs_reg* reg);
+
+/* ------------------------------------------------------------ state set-up */
+
+/* Section 2 "Scope and basic use", Initialize("base", index): |index>. */
+iqs_status iqs_init_basis(iqs_reg* reg, uint64_t index);
+
+/* Section 2 "Scope and basic use", balanced superposition: every amplitude 2^(-n/2). */
+iqs_status iqs_init_uniform(iqs_reg* reg);
+
+/* Copy ``bytes`` (must equal 2^n x amplitude size) between a host buffer and
+ * the register; synchronous.  Pinned host memory gives full bandwidth. */
+iqs_status iqs_upload(iqs_reg* reg, const void* host, size_t bytes);
+iqs_status iqs_download(const iqs_reg* reg, void* host, size_t bytes);
+
+/* ------------------------------------------------------------ gates */
+
+/* Section 2 "Distributed implementation", the one-qubit gate equation:
+ * for every index i with i_q = 0, (alpha_i, alpha_{i+2^q}) <- U (alpha_i, alpha_{i+2^q}).
+ * q in [0, n).  U may be any 2x2 complex matrix (the paper's "random 2x2
+ * matrix"); matrices whose entries are all 0, +-1 or +-i and that have one
+ * nonzero per row and column (X, Y, Z, S, ...) are applied exactly. */
+iqs_status iqs_apply_1q(iqs_reg* reg, int q, const double U[8]);
+
+/* Section 2 "Scope and basic use" and "Distributed implementation", last
+ * paragraph: controlled one-qubit gate, U applied to target t on the basis
+ * states whose control bit c is 1 (CNOT = ApplyCPauliX with U = X).
+ * c, t in [0, n), c != t. */
+iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]);
+
+/* Section 2 footnote on the QAOA-specialised methods (one global diagonal
+ * operation per step) and Section 4 (H_MaxCut counts the cut edges):
+ *   psi_x <- exp(-i gamma C(x)) psi_x,  C(x) = sum_{(u,v)} w_uv (x_u XOR x_v).
+ * ``edges``: host int32 array of 2*n_edges vertex indices (u0, v0, u1, v1, ...),
+ * each in [0, n), u != v.  ``weights``: host array of n_edges doubles or NULL
+ * for weight 1 (the unweighted case uses an FP64-built table of
+ * exp(-i gamma k), k = 0..n_edges).  0 <= n_edges <= 4096. */
+iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges,
+                              const double* weights, double gamma);
+
+/* ------------------------------------------------------------ reductions (FP64 results, synchronous) */
+
+/* Section 2 "Scope and basic use", GetProbability(q): sum of |alpha_i|^2 over
+ * i with bit q set (the raw sum; the state is not renormalised first). */
+iqs_status iqs_probability(iqs_reg* reg, int q, double* out);
+
+/* GetProbability for every qubit in one read of the state: out[q] for q in [0, n). */
+iqs_status iqs_probabilities(iqs_reg* reg, double* out);
+
+/* Section 2 "Scope and basic use": expectation of a product of Pauli matrices,
+ * Re <psi| P |psi>.  ``pauli`` is a NUL-terminated string of length n over
+ * {I, X, Y, Z}; character k acts on qubit k. */
+iqs_status iqs_expectation(iqs_reg* reg, const char* pauli, double* out);
+
+/* The same by bit masks: bit k of ``xmask`` and ``zmask`` marks an X (x only),
+ * Z (z only) or Y (both) on qubit k.  Bits at or above n must be zero. */
+iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, double* out);
+
+/* Squared norm sum_i |alpha_i|^2. */
+iqs_status iqs_norm2(iqs_reg* reg, double* out);
+
+/* psi <- psi / ||psi|| (norm accumulated in FP64); IQS_EINVAL for a zero state. */
+iqs_status iqs_renormalize(iqs_reg* reg);
+
+/* Section 4: <H_MaxCut> = sum_x C(x) |alpha_x|^2 with C as in iqs_apply_zz_phase. */
+iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges,
+                             const double* weights, double* out);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* iqs_last_error(void);
+
+/* Library version string. */
+const char* iqs_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * registers, all threads); for launch accounting in benchmarks. */
+uint64_t iqs_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IQS_H */

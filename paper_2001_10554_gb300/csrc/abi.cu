@@ -1,0 +1,368 @@
+// C ABI (include/iqs.h): register lifecycle, argument checks, dispatch to the
+// kernel launchers, and synchronous result delivery.  No call aborts or
+// prints; failures return a status and leave a thread-local message.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include <atomic>
+
+#include "internal.h"
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+thread_local char g_err[512] = "";
+
+iqs_status fail(iqs_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+iqs_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error where possible
+  return fail(IQS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CHECK_REG(r)                                                  \
+  do {                                                                \
+    if ((r) == nullptr) return fail(IQS_EINVAL, "register is NULL");  \
+  } while (0)
+
+#define CUDA_TRY(expr, what)                         \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+iqs_status check_dtype(int dtype) {
+  if (dtype != IQS_C64 && dtype != IQS_C128) return fail(IQS_EINVAL, "dtype must be IQS_C64 or IQS_C128");
+  return IQS_OK;
+}
+
+iqs_status check_n(int n) {
+  if (n < 1 || n > IQS_MAX_QUBITS) return fail(IQS_EINVAL, "number of qubits %d outside [1, %d]", n, IQS_MAX_QUBITS);
+  return IQS_OK;
+}
+
+iqs_status alloc_scratch(iqs_reg* r) {
+  using namespace iqs;
+  if (cudaMalloc(&r->partials, sizeof(double) * kRedBlocks * kRedSlots) != cudaSuccess ||
+      cudaMalloc(&r->results, sizeof(double) * kRedSlots) != cudaSuccess ||
+      cudaMalloc(&r->flag, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IQS_ENOMEM, "cannot allocate reduction scratch");
+  }
+  if (cudaMallocHost(&r->host_results, sizeof(double) * kRedSlots) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IQS_ENOMEM, "cannot allocate pinned result buffer");
+  }
+  CUDA_TRY(cudaMemsetAsync(r->flag, 0, sizeof(unsigned), r->stream), "clear flag");
+  return IQS_OK;
+}
+
+void free_reg(iqs_reg* r) {
+  if (r->owns && r->data) cudaFree(r->data);
+  if (r->partials) cudaFree(r->partials);
+  if (r->results) cudaFree(r->results);
+  if (r->flag) cudaFree(r->flag);
+  if (r->host_results) cudaFreeHost(r->host_results);
+  delete r;
+}
+
+iqs_status new_reg(int n, int dtype, void* ptr, bool owns, void* stream, iqs_reg** out) {
+  if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
+  *out = nullptr;
+  iqs_status s = check_n(n);
+  if (s != IQS_OK) return s;
+  if ((s = check_dtype(dtype)) != IQS_OK) return s;
+  iqs_reg* r = new (std::nothrow) iqs_reg();
+  if (r == nullptr) return fail(IQS_ENOMEM, "host allocation failed");
+  r->n = n;
+  r->dtype = dtype;
+  r->stream = (cudaStream_t)stream;
+  cudaGetDevice(&r->device);
+  if (owns) {
+    const size_t bytes = (size_t)iqs::num_amps(r) * iqs::amp_bytes(r);
+    if (cudaMalloc(&r->data, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      delete r;
+      return fail(IQS_ENOMEM, "cannot allocate %zu bytes for the state", bytes);
+    }
+    r->owns = true;
+  } else {
+    if (ptr == nullptr || ((uintptr_t)ptr & 15u)) {
+      delete r;
+      return fail(IQS_EINVAL, "device pointer is NULL or not 16-byte aligned");
+    }
+    r->data = ptr;
+  }
+  if ((s = alloc_scratch(r)) != IQS_OK) {
+    free_reg(r);
+    return s;
+  }
+  if (owns) {
+    const cudaError_t e = iqs::launch_init_basis(r, 0);
+    if (e != cudaSuccess) {
+      free_reg(r);
+      return cuda_fail(e, "initialise state");
+    }
+  }
+  *out = r;
+  return IQS_OK;
+}
+
+iqs_status read_results(iqs_reg* r, int count, double* out) {
+  CUDA_TRY(cudaMemcpyAsync(r->host_results, r->results, sizeof(double) * count, cudaMemcpyDeviceToHost, r->stream),
+           "copy results");
+  CUDA_TRY(cudaStreamSynchronize(r->stream), "synchronise");
+  std::memcpy(out, r->host_results, sizeof(double) * count);
+  return IQS_OK;
+}
+
+iqs_status check_flag(iqs_reg* r) {
+  unsigned f = 0;
+  CUDA_TRY(cudaMemcpyAsync(&f, r->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, r->stream), "read flag");
+  CUDA_TRY(cudaStreamSynchronize(r->stream), "synchronise");
+  if (f) {
+    CUDA_TRY(cudaMemsetAsync(r->flag, 0, sizeof(unsigned), r->stream), "clear flag");
+    return fail(IQS_ERANGE, "an amplitude with |a| >= 2^64, Inf or NaN was met by emulated complex128 arithmetic");
+  }
+  return IQS_OK;
+}
+
+iqs::Mat2 to_mat(const double* U) {
+  iqs::Mat2 m;
+  for (int k = 0; k < 4; ++k) {
+    m.re[k] = U[2 * k];
+    m.im[k] = U[2 * k + 1];
+  }
+  return m;
+}
+
+iqs_status check_edges(const iqs_reg* r, int n_edges, const int32_t* edges) {
+  if (n_edges < 0 || n_edges > iqs::kMaxEdges) return fail(IQS_EINVAL, "n_edges %d outside [0, %d]", n_edges, iqs::kMaxEdges);
+  if (n_edges > 0 && edges == nullptr) return fail(IQS_EINVAL, "edges is NULL");
+  for (int e = 0; e < n_edges; ++e) {
+    const int u = edges[2 * e], v = edges[2 * e + 1];
+    if (u < 0 || u >= r->n || v < 0 || v >= r->n || u == v)
+      return fail(IQS_EINVAL, "edge %d = (%d, %d) invalid for %d qubits", e, u, v, r->n);
+  }
+  return IQS_OK;
+}
+
+}  // namespace
+
+void iqs::note_launches(int k) { g_launches.fetch_add((uint64_t)k); }
+
+extern "C" {
+
+iqs_status iqs_create(int n, int dtype, void* stream, iqs_reg** out) { return new_reg(n, dtype, nullptr, true, stream, out); }
+
+iqs_status iqs_wrap(int n, int dtype, void* device_ptr, void* stream, iqs_reg** out) {
+  return new_reg(n, dtype, device_ptr, false, stream, out);
+}
+
+iqs_status iqs_destroy(iqs_reg* reg) {
+  if (reg == nullptr) return IQS_OK;
+  cudaStreamSynchronize(reg->stream);
+  free_reg(reg);
+  return IQS_OK;
+}
+
+iqs_status iqs_data(const iqs_reg* reg, void** device_ptr) {
+  CHECK_REG(reg);
+  if (device_ptr == nullptr) return fail(IQS_EINVAL, "out is NULL");
+  *device_ptr = reg->data;
+  return IQS_OK;
+}
+
+iqs_status iqs_info(const iqs_reg* reg, int* n, int* dtype) {
+  CHECK_REG(reg);
+  if (n) *n = reg->n;
+  if (dtype) *dtype = reg->dtype;
+  return IQS_OK;
+}
+
+iqs_status iqs_set_stream(iqs_reg* reg, void* stream) {
+  CHECK_REG(reg);
+  reg->stream = (cudaStream_t)stream;
+  return IQS_OK;
+}
+
+iqs_status iqs_set_math(iqs_reg* reg, int math) {
+  CHECK_REG(reg);
+  if (math != IQS_MATH_AUTO && math != IQS_MATH_EMULATED && math != IQS_MATH_NATIVE)
+    return fail(IQS_EINVAL, "unknown math mode %d", math);
+  reg->math = math;
+  return IQS_OK;
+}
+
+iqs_status iqs_synchronize(iqs_reg* reg) {
+  CHECK_REG(reg);
+  return check_flag(reg);
+}
+
+iqs_status iqs_init_basis(iqs_reg* reg, uint64_t index) {
+  CHECK_REG(reg);
+  if (index >= iqs::num_amps(reg)) return fail(IQS_EINVAL, "basis index out of range");
+  CUDA_TRY(iqs::launch_init_basis(reg, index), "init_basis");
+  return IQS_OK;
+}
+
+iqs_status iqs_init_uniform(iqs_reg* reg) {
+  CHECK_REG(reg);
+  CUDA_TRY(iqs::launch_init_uniform(reg), "init_uniform");
+  return IQS_OK;
+}
+
+iqs_status iqs_upload(iqs_reg* reg, const void* host, size_t bytes) {
+  CHECK_REG(reg);
+  if (host == nullptr || bytes != iqs::num_amps(reg) * iqs::amp_bytes(reg))
+    return fail(IQS_EINVAL, "upload: NULL buffer or size %zu != state size", bytes);
+  CUDA_TRY(cudaMemcpyAsync(reg->data, host, bytes, cudaMemcpyHostToDevice, reg->stream), "upload");
+  CUDA_TRY(cudaStreamSynchronize(reg->stream), "upload sync");
+  return IQS_OK;
+}
+
+iqs_status iqs_download(const iqs_reg* reg, void* host, size_t bytes) {
+  CHECK_REG(reg);
+  if (host == nullptr || bytes != iqs::num_amps(reg) * iqs::amp_bytes(reg))
+    return fail(IQS_EINVAL, "download: NULL buffer or size %zu != state size", bytes);
+  CUDA_TRY(cudaMemcpyAsync(host, reg->data, bytes, cudaMemcpyDeviceToHost, reg->stream), "download");
+  CUDA_TRY(cudaStreamSynchronize(reg->stream), "download sync");
+  return IQS_OK;
+}
+
+iqs_status iqs_apply_1q(iqs_reg* reg, int q, const double U[8]) {
+  CHECK_REG(reg);
+  if (U == nullptr) return fail(IQS_EINVAL, "U is NULL");
+  if (q < 0 || q >= reg->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, reg->n);
+  CUDA_TRY(iqs::launch_1q(reg, q, to_mat(U)), "apply_1q");
+  return IQS_OK;
+}
+
+iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]) {
+  CHECK_REG(reg);
+  if (U == nullptr) return fail(IQS_EINVAL, "U is NULL");
+  if (c < 0 || c >= reg->n || t < 0 || t >= reg->n) return fail(IQS_EINVAL, "control/target outside [0, %d)", reg->n);
+  if (c == t) return fail(IQS_EINVAL, "control and target are the same qubit (%d)", c);
+  if (reg->n < 2) return fail(IQS_EINVAL, "a controlled gate needs 2 qubits");
+  CUDA_TRY(iqs::launch_c1q(reg, c, t, to_mat(U)), "apply_c1q");
+  return IQS_OK;
+}
+
+iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges, const double* weights, double gamma) {
+  CHECK_REG(reg);
+  iqs_status s = check_edges(reg, n_edges, edges);
+  if (s != IQS_OK) return s;
+  if (!std::isfinite(gamma)) return fail(IQS_EINVAL, "gamma is not finite");
+  if (weights)
+    for (int e = 0; e < n_edges; ++e)
+      if (!std::isfinite(weights[e])) return fail(IQS_EINVAL, "weight %d is not finite", e);
+  CUDA_TRY(iqs::launch_zz_phase(reg, n_edges, edges, weights, gamma), "apply_zz_phase");
+  return IQS_OK;
+}
+
+iqs_status iqs_norm2(iqs_reg* reg, double* out) {
+  CHECK_REG(reg);
+  if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
+  CUDA_TRY(iqs::launch_norm2(reg), "norm2");
+  iqs_status s = read_results(reg, 1, out);
+  return s != IQS_OK ? s : check_flag(reg);
+}
+
+iqs_status iqs_probability(iqs_reg* reg, int q, double* out) {
+  CHECK_REG(reg);
+  if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
+  if (q < 0 || q >= reg->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, reg->n);
+  CUDA_TRY(iqs::launch_probability(reg, q), "probability");
+  iqs_status s = read_results(reg, 1, out);
+  return s != IQS_OK ? s : check_flag(reg);
+}
+
+iqs_status iqs_probabilities(iqs_reg* reg, double* out) {
+  CHECK_REG(reg);
+  if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
+  CUDA_TRY(iqs::launch_probabilities(reg), "probabilities");
+  iqs_status s = read_results(reg, reg->n, out);
+  return s != IQS_OK ? s : check_flag(reg);
+}
+
+iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, double* out) {
+  CHECK_REG(reg);
+  if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
+  const uint64_t all = reg->n >= 64 ? ~0ull : ((1ull << reg->n) - 1ull);
+  if ((xmask | zmask) & ~all) return fail(IQS_EINVAL, "mask bits at or above n = %d", reg->n);
+  CUDA_TRY(iqs::launch_expectation(reg, xmask, zmask), "expectation");
+  double v;
+  iqs_status s = read_results(reg, 1, &v);
+  if (s != IQS_OK) return s;
+  if (xmask != 0) {
+    // pair sum times 2 * (sign from i^{nY}): nY = 0 -> +Re, 1 -> -Im, 2 -> -Re, 3 -> +Im
+    const int nY = __builtin_popcountll(xmask & zmask) & 3;
+    const double sgn = (nY == 0 || nY == 3) ? 1.0 : -1.0;
+    v = 2.0 * sgn * v;
+  }
+  *out = v;
+  return check_flag(reg);
+}
+
+iqs_status iqs_expectation(iqs_reg* reg, const char* pauli, double* out) {
+  CHECK_REG(reg);
+  if (pauli == nullptr) return fail(IQS_EINVAL, "pauli is NULL");
+  const size_t len = strnlen(pauli, IQS_MAX_QUBITS + 2);
+  if ((int)len != reg->n) return fail(IQS_EINVAL, "Pauli string length %zu != n = %d", len, reg->n);
+  uint64_t xm = 0, zm = 0;
+  for (int k = 0; k < reg->n; ++k) {
+    switch (pauli[k]) {
+      case 'I': break;
+      case 'X': xm |= 1ull << k; break;
+      case 'Y': xm |= 1ull << k; zm |= 1ull << k; break;
+      case 'Z': zm |= 1ull << k; break;
+      default: return fail(IQS_EINVAL, "bad Pauli character '%c' at %d", pauli[k], k);
+    }
+  }
+  return iqs_expectation_masks(reg, xm, zm, out);
+}
+
+iqs_status iqs_renormalize(iqs_reg* reg) {
+  CHECK_REG(reg);
+  double nn;
+  iqs_status s = iqs_norm2(reg, &nn);
+  if (s != IQS_OK) return s;
+  if (!(nn > 0.0) || !std::isfinite(nn)) return fail(IQS_EINVAL, "cannot renormalise a state of squared norm %g", nn);
+  CUDA_TRY(iqs::launch_scale(reg, 1.0 / std::sqrt(nn)), "renormalize");
+  return IQS_OK;
+}
+
+iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges, const double* weights, double* out) {
+  CHECK_REG(reg);
+  if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
+  iqs_status s = check_edges(reg, n_edges, edges);
+  if (s != IQS_OK) return s;
+  double total = 0.0;
+  for (int base = 0; base < n_edges; base += 255) {
+    const int m = n_edges - base < 255 ? n_edges - base : 255;
+    CUDA_TRY(iqs::launch_energy(reg, m, edges + 2 * base, weights ? weights + base : nullptr), "energy");
+    double v;
+    if ((s = read_results(reg, 1, &v)) != IQS_OK) return s;
+    total += v;
+  }
+  *out = total;
+  return check_flag(reg);
+}
+
+const char* iqs_last_error(void) { return g_err; }
+
+const char* iqs_version(void) { return "iqs-gb300 0.1.0 (sm_103a)"; }
+
+uint64_t iqs_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

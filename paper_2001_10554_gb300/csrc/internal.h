@@ -1,0 +1,81 @@
+// Internal declarations shared by the C-ABI layer and the kernel files.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "iqs.h"
+
+struct iqs_reg {
+  int n = 0;
+  int dtype = IQS_C64;
+  int math = IQS_MATH_AUTO;
+  int device = 0;
+  bool owns = false;
+  void* data = nullptr;          // 2^n amplitudes, interleaved (re, im)
+  cudaStream_t stream = nullptr;
+  // scratch: per-block FP64 partials of reductions, their final values, and
+  // the out-of-range flag of the emulated complex128 arithmetic
+  double* partials = nullptr;    // kRedBlocks * kRedSlots doubles
+  double* results = nullptr;     // kRedSlots doubles
+  unsigned* flag = nullptr;      // 1 unsigned
+  double* host_results = nullptr;  // pinned, kRedSlots doubles
+};
+
+namespace iqs {
+
+constexpr int kRedBlocks = 1024;        // blocks of every reduction kernel (fixed: deterministic order)
+constexpr int kRedSlots = 40;           // values reduced at once (n + 1 for all-qubit probabilities)
+constexpr int kMaxEdgesFast = 255;      // unweighted ZZ phase: table-driven fast path bound
+constexpr int kMaxEdges = 4096;
+
+// Kernel-launch accounting (iqs_kernel_launches).
+void note_launches(int k);
+// cudaGetLastError(), counting ``k`` launches when it reports success.
+inline cudaError_t launched(int k) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) note_launches(k);
+  return e;
+}
+
+inline uint64_t num_amps(const iqs_reg* r) { return 1ull << r->n; }
+inline size_t amp_bytes(const iqs_reg* r) { return r->dtype == IQS_C128 ? 16 : 8; }
+inline bool use_emulated(const iqs_reg* r) {
+  if (r->dtype != IQS_C128) return false;
+  if (r->math == IQS_MATH_EMULATED) return true;
+  if (r->math == IQS_MATH_NATIVE) return false;
+  return r->n >= 20;
+}
+
+// 2x2 gate in FP64, row-major: U[2*row + col] = (re, im)
+struct Mat2 {
+  double re[4], im[4];
+};
+
+// Monomial gate with unit entries in {1, i, -1, -i}: row r takes input
+// (perm ? 1 - r : r) times i^k[r].
+struct Mono {
+  bool perm;
+  int k[2];
+};
+bool as_monomial(const Mat2& u, Mono* m);
+
+// ---- gates.cu
+cudaError_t launch_1q(iqs_reg* r, int q, const Mat2& u);
+cudaError_t launch_c1q(iqs_reg* r, int c, int t, const Mat2& u);
+
+// ---- phase.cu
+cudaError_t launch_init_basis(iqs_reg* r, uint64_t index);
+cudaError_t launch_init_uniform(iqs_reg* r);
+cudaError_t launch_zz_phase(iqs_reg* r, int n_edges, const int32_t* edges, const double* w, double gamma);
+cudaError_t launch_scale(iqs_reg* r, double s);
+
+// ---- reduce.cu: results land in r->results[0..count) (device); the caller copies them.
+cudaError_t launch_norm2(iqs_reg* r);
+cudaError_t launch_probability(iqs_reg* r, int q);
+cudaError_t launch_probabilities(iqs_reg* r);                    // n values
+cudaError_t launch_expectation(iqs_reg* r, uint64_t xm, uint64_t zm);
+cudaError_t launch_energy(iqs_reg* r, int n_edges, const int32_t* edges, const double* w);
+
+}  // namespace iqs
