@@ -165,6 +165,28 @@ iqs_status iqs_renormalize(iqs_reg* reg);
 iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges,
                              const double* weights, double* out);
 
+/* ------------------------------------------------------------ allocation-free variant */
+
+/* The paper has no counterpart to this call: it is an interface for callers
+ * that cannot call cudaMalloc (an allocator that owns all device memory, a
+ * loop that must not allocate after start-up).  It computes what
+ * iqs_probabilities computes -- P(q = 1) for every qubit in one read -- from a
+ * caller-owned state and writes the n results to a caller-owned DEVICE array,
+ * without a register and without allocating anything.
+ *   state   device pointer to 2^n amplitudes of ``dtype`` (16-byte aligned).
+ *   n       number of qubits, 1..IQS_MAX_QUBITS; anything else is rejected
+ *           with IQS_EINVAL (the fixed scratch is sized for at most 34 qubits).
+ *   stream  cudaStream_t or NULL; the call is asynchronous on it.
+ *   out     device pointer to n doubles (8-byte aligned), written on ``stream``;
+ *           all NaN if a complex128 amplitude was outside the emulated range.
+ * Scratch is one static device array of about 320 KiB that every GPU loading
+ * the library keeps until exit.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture on that device.  All calls share the array:
+ * calls that overlap on the GPU race and must be ordered by the caller.
+ * Never calls cudaMalloc, cudaFree or any allocating routine. */
+iqs_status iqs_probabilities_noalloc(const void* state, int n, int dtype, void* stream, double* out);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* Message for the last failed call on this thread ("" if none). */

@@ -60,6 +60,7 @@ SIGNATURES = {
     "iqs_last_error": ([], C.c_char_p),
     "iqs_version": ([], C.c_char_p),
     "iqs_kernel_launches": ([], C.c_uint64),
+    "iqs_probabilities_noalloc": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, _dp], C.c_int),
 }
 
 for _name, (_args, _res) in SIGNATURES.items():

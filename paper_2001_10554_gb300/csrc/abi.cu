@@ -161,6 +161,14 @@ iqs_status check_edges(const iqs_reg* r, int n_edges, const int32_t* edges) {
 
 void iqs::note_launches(int k) { g_launches.fetch_add((uint64_t)k); }
 
+iqs_status iqs::report(iqs_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
 extern "C" {
 
 iqs_status iqs_create(int n, int dtype, void* stream, iqs_reg** out) { return new_reg(n, dtype, nullptr, true, stream, out); }

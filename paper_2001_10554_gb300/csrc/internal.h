@@ -77,5 +77,10 @@ cudaError_t launch_probability(iqs_reg* r, int q);
 cudaError_t launch_probabilities(iqs_reg* r);                    // n values
 cudaError_t launch_expectation(iqs_reg* r, uint64_t xm, uint64_t zm);
 cudaError_t launch_energy(iqs_reg* r, int n_edges, const int32_t* edges, const double* w);
+cudaError_t launch_probabilities_raw(const void* data, int n, int dtype, cudaStream_t s, double* partials,
+                                     double* results, unsigned* flag);
+
+// ---- abi.cu: record a failure message for iqs_last_error() and return ``s``.
+iqs_status report(iqs_status s, const char* fmt, ...);
 
 }  // namespace iqs

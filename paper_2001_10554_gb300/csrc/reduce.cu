@@ -417,6 +417,27 @@ cudaError_t launch_probabilities(iqs_reg* r) {
   return e != cudaSuccess ? e : finalize(r, r->n, kRedSlots);
 }
 
+// All-qubit probabilities with caller-supplied scratch: ``partials`` holds
+// kRedBlocks x kRedSlots doubles, ``results`` receives n doubles (device).
+cudaError_t launch_probabilities_raw(const void* data, int n, int dtype, cudaStream_t s, double* partials,
+                                     double* results, unsigned* flag) {
+  if (n >= 9) {
+    if (dtype == IQS_C64)
+      k_probs_all<float2><<<kRedBlocks, kThreads, 0, s>>>((const float2*)data, n, partials, flag);
+    else
+      k_probs_all<double2><<<kRedBlocks, kThreads, 0, s>>>((const double2*)data, n, partials, flag);
+  } else {
+    if (dtype == IQS_C64)
+      k_probs_small<float2><<<kRedBlocks, kThreads, 0, s>>>((const float2*)data, n, partials, flag);
+    else
+      k_probs_small<double2><<<kRedBlocks, kThreads, 0, s>>>((const double2*)data, n, partials, flag);
+  }
+  cudaError_t e = launched(1);
+  if (e != cudaSuccess) return e;
+  k_finalize<<<1, kThreads, 0, s>>>(partials, kRedBlocks, n, kRedSlots, results);
+  return launched(1);
+}
+
 cudaError_t launch_expectation(iqs_reg* r, uint64_t xm, uint64_t zm) {
   const uint64_t N = num_amps(r);
   if (xm == 0) {
