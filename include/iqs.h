@@ -165,6 +165,44 @@ iqs_status iqs_renormalize(iqs_reg* reg);
 iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges,
                              const double* weights, double* out);
 
+/* ------------------------------------------------------------ QAOA energy and adjoint gradient */
+
+/* Section 4 ("QAOA with swarm particle optimization"): the objective
+ * L(theta) = <0| U^dagger H_MaxCut U |0> of QAOA Max-Cut, evaluated for a pool
+ * of parameter sets at once (Section 2, "Pool of multiple states": each pool
+ * state runs the same circuit with its own parameters).  Circuit:
+ * |+>^n, then for l = 1..p the cost phase exp(-i gamma_l C) and the mixer
+ * RX(2 beta_l) = exp(-i beta_l X) on every qubit; C(x) counts cut edges.
+ * The gradient is the adjoint derivative dE/dtheta = 2 Im <lambda|G|phi>,
+ * computed by uncomputing the state with inverse gates (no stored states). */
+typedef struct iqs_qaoa iqs_qaoa;
+
+/* Workspace for up to ``batch_max`` parameter sets of an unweighted graph
+ * with ``n_edges`` (1..255) edges (host int32 pairs, u != v, in [0, n)) on n
+ * qubits (2..34).  Allocates two state vectors per parameter set (phi and
+ * lambda), one byte of cut count per basis state, parameter tables and
+ * scratch on the current device.  ``stream`` may be NULL (a private stream is
+ * created).  Errors: IQS_EINVAL, IQS_ENOMEM, IQS_ECUDA. */
+iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const int32_t* edges, void* stream,
+                           iqs_qaoa** out);
+iqs_status iqs_qaoa_destroy(iqs_qaoa* q);
+
+/* renorm_every = R > 0 renormalises phi (to 1) and lambda (to its initial norm)
+ * every R uncomputed layers, in FP64; use_graphs != 0 (default) replays each
+ * (batch, p, gradient) shape from a captured CUDA graph. */
+iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs);
+
+/* Evaluate ``batch`` parameter sets of depth p (1..64).  Host arrays,
+ * row-major [batch][p]: gammas, betas.  Outputs (host): energies[batch] and,
+ * when both are non-NULL, grad_gammas[batch][p] and grad_betas[batch][p].
+ * Synchronous.  IQS_ERANGE if a complex128 amplitude left the emulated range. */
+iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, const double* betas,
+                        double* energies, double* grad_gammas, double* grad_betas);
+
+/* Copy the final state phi of parameter set ``index`` (after the last forward
+ * pass, or after the uncompute when a gradient was computed) to host memory. */
+iqs_status iqs_qaoa_download_state(iqs_qaoa* q, int index, void* host, size_t bytes);
+
 /* ------------------------------------------------------------ allocation-free variant */
 
 /* The paper has no counterpart to this call: it is an interface for callers

@@ -1,0 +1,673 @@
+// QAOA Max-Cut engine: energy and adjoint gradient for a batch of B parameter
+// sets on one graph, complex64 or complex128 (Section 4: L(theta) =
+// <0|U^dagger H_MaxCut U|0> evaluated per particle; Section 2 "Pool of multiple
+// states": many parameter sets of one circuit simulated side by side).
+//
+// States are stored as B contiguous vectors of 2^n amplitudes.  Every kernel
+// takes the state index from blockIdx.y, so one launch advances all B states
+// by one layer operation.
+//
+// Forward:  uniform |+>^n; per layer l the cost phase exp(-i gamma_l C) (a
+//           per-state FP64-built table exp(-i gamma k) indexed by the
+//           precomputed cut count C(x), one byte per basis state) and the
+//           mixer RX(2 beta_l) on every qubit, applied in shared-memory tiles
+//           of up to 12 qubits per pass.
+// Energy:   E = sum C |psi|^2, accumulated in double-float, finished in FP64.
+// Backward: adjoint by uncompute (no stored states): lambda = C psi, then for
+//           l = p..1 the fused mixer step (accumulate Im<lambda|X_j|phi> for
+//           every qubit and apply RX(2 beta)^dagger to both vectors) and the
+//           fused phase step (accumulate Im<lambda|C|phi> and apply
+//           exp(+i gamma C) to both); dE/dtheta = 2 Im <lambda|G|phi>.
+//           Optional periodic renormalisation restores |phi| = 1 and |lambda|
+//           to its initial value (both invariant under the exact uncompute).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "cut.cuh"
+#include "df64.cuh"
+#include "internal.h"
+#include "qaoa_ops.cuh"
+
+namespace iqs {
+namespace {
+
+using qops::S2;
+
+constexpr int kMaxP = 64;
+
+// ---------------------------------------------------------------- storage traits
+struct T64 {
+  using V = float2;   // HBM element
+  using W = float2;   // working (shared-memory) element
+  using RX = float2;  // (cos beta, sin beta)
+  using PH = float2;  // exp(-i gamma k)
+  static constexpr int kTileBits = 12;  // 4096 x 8 B = 32 KiB per vector
+  static constexpr int kRowBits = 4;    // 16 contiguous amplitudes (128 B) per tile row
+  __device__ static W load(V v, unsigned&) { return v; }
+  __device__ static V store(const W& w) { return w; }
+  __device__ static RX rx_inv(RX k) { return make_float2(k.x, -k.y); }
+  __device__ static void rx(W& a, W& b, const RX& k) { qops::rx_pair(a, b, k.x, k.y); }
+  __device__ static PH conj(PH t) { return make_float2(t.x, -t.y); }
+  __device__ static W mul(const PH& t, const W& x) { return qops::cmul(t, x); }
+};
+
+struct T128 {
+  using V = double2;
+  using W = S2;
+  using RX = qops::RXc;
+  using PH = qops::Ph;
+  static constexpr int kTileBits = 11;  // 2048 x 16 B = 32 KiB per vector
+  static constexpr int kRowBits = 3;    // 8 contiguous amplitudes (128 B) per tile row
+  __device__ static W load(V v, unsigned& bad) { return qops::to_split(v, bad); }
+  __device__ static V store(const W& w) { return qops::from_split(w); }
+  __device__ static RX rx_inv(RX k) {
+    RX r = k;
+    r.s = k.ns;
+    r.ns = k.s;
+    return r;
+  }
+  __device__ static void rx(W& a, W& b, const RX& k) { qops::rx_pair(a, b, k); }
+  __device__ static PH conj(PH t) {
+    PH r = t;
+    r.ti = t.nti;
+    r.nti = t.ti;
+    return r;
+  }
+  __device__ static W mul(const PH& t, const W& x) { return qops::cmul(t, x); }
+};
+
+// ---------------------------------------------------------------- tile geometry
+// Tile bits: [0, c) and [s, s + m), s >= c.  Local index l = (h << c) | low.
+struct Geo {
+  int c, s, m;
+};
+
+__device__ __forceinline__ uint64_t tile_x(const Geo& g, uint64_t t, unsigned l) {
+  const uint64_t low = l & ((1u << g.c) - 1u);
+  const uint64_t h = l >> g.c;
+  const int mid = g.s - g.c;
+  const uint64_t tlo = t & ((1ull << mid) - 1ull);
+  const uint64_t thi = t >> mid;
+  return (thi << (g.s + g.m)) | (h << g.s) | (tlo << g.c) | low;
+}
+
+// ---------------------------------------------------------------- block reduction of one FP64 value
+__device__ __forceinline__ void block_partial(double v, double* out) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    *out = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- kernels
+template <class V>
+__global__ void k_fill_uniform(V* a, uint64_t total, V v) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+template <class X>
+__global__ void k_cut_table(uint8_t* cut, uint64_t N, EdgesU8 E) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
+    cut[i] = (uint8_t)cut_count((X)i, E);
+}
+
+// Mixer pass: RX on the qubits [s, s+m) of every tile (or its inverse, with the
+// gradient term, on two vectors when ADJ).
+template <class TR, bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_mixer(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam,
+                                                    uint64_t N, Geo g, const typename TR::RX* __restrict__ rx,
+                                                    double* __restrict__ partials, int part_stride, unsigned* flag) {
+  using W = typename TR::W;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* sp = reinterpret_cast<W*>(smem_raw);
+  const unsigned T = 1u << (g.c + g.m);
+  W* sl = sp + T;
+  const unsigned b = blockIdx.y;
+  typename TR::V* P = phi + (uint64_t)b * N;
+  typename TR::V* L = ADJ ? lam + (uint64_t)b * N : nullptr;
+  const typename TR::RX k = ADJ ? TR::rx_inv(rx[b]) : rx[b];
+  const uint64_t tiles = N >> (g.c + g.m);
+  unsigned bad = 0;
+  dfx::Acc acc;
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (unsigned l = threadIdx.x; l < T; l += blockDim.x) {
+      const uint64_t x = tile_x(g, t, l);
+      sp[l] = TR::load(P[x], bad);
+      if (ADJ) sl[l] = TR::load(L[x], bad);
+    }
+    __syncthreads();
+    for (int j = 0; j < g.m; ++j) {
+      const int lb = g.c + j;
+      for (unsigned pi = threadIdx.x; pi < (T >> 1); pi += blockDim.x) {
+        const unsigned i0 = (unsigned)insert_zero(pi, lb), i1 = i0 | (1u << lb);
+        W x0 = sp[i0], x1 = sp[i1];
+        if (ADJ) {
+          W y0 = sl[i0], y1 = sl[i1];
+          float p, e;
+          qops::im_conj_mul(y0, x1, p, e);
+          acc.add(p, e);
+          qops::im_conj_mul(y1, x0, p, e);
+          acc.add(p, e);
+          TR::rx(y0, y1, k);
+          sl[i0] = y0;
+          sl[i1] = y1;
+        }
+        TR::rx(x0, x1, k);
+        sp[i0] = x0;
+        sp[i1] = x1;
+      }
+      __syncthreads();
+    }
+    for (unsigned l = threadIdx.x; l < T; l += blockDim.x) {
+      const uint64_t x = tile_x(g, t, l);
+      P[x] = TR::store(sp[l]);
+      if (ADJ) L[x] = TR::store(sl[l]);
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(flag, 1u);
+  if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+}
+
+// Cost phase: psi_x <- T_b[C(x)] psi_x.  When ADJ: accumulate Im conj(lambda) C phi
+// first, then multiply both vectors by conj(T_b[C(x)]).
+template <class TR, bool ADJ>
+__global__ void __launch_bounds__(kThreads) k_phase(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam,
+                                                    uint64_t N, const uint8_t* __restrict__ cut,
+                                                    const typename TR::PH* __restrict__ tables, int tsize,
+                                                    double* __restrict__ partials, int part_stride, unsigned* flag) {
+  using PH = typename TR::PH;
+  using W = typename TR::W;
+  __shared__ PH st[kEdgeChunk + 1];
+  const unsigned b = blockIdx.y;
+  for (int i = threadIdx.x; i < tsize; i += blockDim.x) {
+    const PH t = tables[(uint64_t)b * tsize + i];
+    st[i] = ADJ ? TR::conj(t) : t;
+  }
+  __syncthreads();
+  typename TR::V* P = phi + (uint64_t)b * N;
+  typename TR::V* L = ADJ ? lam + (uint64_t)b * N : nullptr;
+  unsigned bad = 0;
+  dfx::Acc acc;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int c = cut[i];
+    W x = TR::load(P[i], bad);
+    if (ADJ) {
+      W y = TR::load(L[i], bad);
+      float p, e;
+      qops::im_conj_mul(y, x, p, e);
+      const float cf = (float)c;
+      const float q = cf * p;
+      acc.add(q, fmaf(cf, p, -q) + cf * e);
+      L[i] = TR::store(TR::mul(st[c], y));
+    }
+    P[i] = TR::store(TR::mul(st[c], x));
+  }
+  if (bad) atomicOr(flag, 1u);
+  if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+}
+
+// Energy sum C |phi|^2, and lambda = C phi when lam != nullptr.
+template <class TR>
+__global__ void __launch_bounds__(kThreads) k_energy_lambda(const typename TR::V* __restrict__ phi,
+                                                            typename TR::V* __restrict__ lam, uint64_t N,
+                                                            const uint8_t* __restrict__ cut,
+                                                            double* __restrict__ partials, int part_stride,
+                                                            unsigned* flag) {
+  const unsigned b = blockIdx.y;
+  const typename TR::V* P = phi + (uint64_t)b * N;
+  typename TR::V* L = lam ? lam + (uint64_t)b * N : nullptr;
+  unsigned bad = 0;
+  dfx::Acc acc;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    const float cf = (float)cut[i];
+    const typename TR::W x = TR::load(P[i], bad);
+    float p, e;
+    qops::abs2(x, p, e);
+    const float q = cf * p;
+    acc.add(q, fmaf(cf, p, -q) + cf * e);
+    if (L) L[i] = TR::store(qops::scale_int(x, cf));
+  }
+  if (bad) atomicOr(flag, 1u);
+  block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+}
+
+// Squared norm of each state (for renormalisation).
+template <class TR>
+__global__ void __launch_bounds__(kThreads) k_norm_batch(const typename TR::V* __restrict__ a, uint64_t N,
+                                                         double* __restrict__ partials, int part_stride,
+                                                         unsigned* flag) {
+  const unsigned b = blockIdx.y;
+  const typename TR::V* P = a + (uint64_t)b * N;
+  unsigned bad = 0;
+  dfx::Acc acc;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    float p, e;
+    qops::abs2(TR::load(P[i], bad), p, e);
+    acc.add(p, e);
+  }
+  if (bad) atomicOr(flag, 1u);
+  block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+}
+
+// out[b * out_stride + slot] = scale * sum_{j < count} partials[b * part_stride + j]
+__global__ void k_finalize_batch(const double* __restrict__ partials, int count, int part_stride, double scale,
+                                 double* __restrict__ out, int out_stride, int slot) {
+  const unsigned b = blockIdx.x;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) s += partials[(uint64_t)b * part_stride + j];
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[(uint64_t)b * out_stride + slot] = scale * t;
+  }
+}
+
+// a_b <- a_b * sqrt(target_b / norm_b)   (target == nullptr: target 1)
+template <class V>
+__global__ void k_rescale(V* __restrict__ a, uint64_t N, const double* __restrict__ norm, const double* __restrict__ target) {
+  const unsigned b = blockIdx.y;
+  const double nb = norm[b];
+  const double f = nb > 0.0 ? sqrt((target ? target[b] : 1.0) / nb) : 1.0;
+  V* P = a + (uint64_t)b * N;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    V v = P[i];
+    v.x *= f;
+    v.y *= f;
+    P[i] = v;
+  }
+}
+
+}  // namespace
+}  // namespace iqs
+
+// ================================================================ host engine
+struct iqs_qaoa {
+  int n = 0, dtype = IQS_C64, bmax = 0, n_edges = 0;
+  uint64_t N = 0;
+  cudaStream_t stream = nullptr;
+  int renorm_every = 0;
+  void* phi = nullptr;
+  void* lam = nullptr;
+  uint8_t* cut = nullptr;
+  void* rx = nullptr;          // [kMaxP][bmax] RX coefficients
+  void* tables = nullptr;      // [kMaxP][bmax][n_edges + 1] phase factors
+  double* partials = nullptr;  // [bmax][part_stride]
+  double* results = nullptr;   // [bmax][1 + 2 kMaxP]
+  double* norms = nullptr;     // [2][bmax]: current norm, lambda target
+  unsigned* flag = nullptr;
+  unsigned char* host_params = nullptr;  // pinned staging of rx + tables
+  double* host_results = nullptr;        // pinned
+  size_t rx_bytes = 0, table_bytes = 0;
+  std::vector<iqs::Geo> passes;
+  std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int>> graphs;  // (B, p, grad, renorm) -> graph, kernels
+  bool use_graphs = true;
+  bool own_stream = false;
+};
+
+namespace iqs {
+namespace {
+
+int part_stride_for(const iqs_qaoa* q) { return 2432 * 4; }  // partial slots per state: passes x blocks
+
+int blocks_per_state(const iqs_qaoa* q, int B) {
+  const uint64_t by_size = std::max<uint64_t>(1, q->N / 4096);
+  const int by_batch = std::max(1, 2432 / std::max(B, 1));
+  return (int)std::min<uint64_t>(by_size, (uint64_t)std::min(by_batch, 2432));
+}
+
+std::vector<Geo> plan_mixer(int n, int tile_bits, int row_bits) {
+  std::vector<Geo> out;
+  const int m0 = std::min(n, tile_bits);
+  out.push_back(Geo{0, 0, m0});
+  int q0 = m0;
+  while (q0 < n) {
+    const int mm = std::min(n - q0, tile_bits - row_bits);
+    out.push_back(Geo{row_bits, q0, mm});
+    q0 += mm;
+  }
+  return out;
+}
+
+template <class TR>
+size_t tile_smem(const Geo& g, int nvec) {
+  return (size_t)nvec * ((size_t)1 << (g.c + g.m)) * sizeof(typename TR::W);
+}
+
+template <class TR>
+cudaError_t set_smem_attrs() {
+  const int bytes = 2 * (1 << TR::kTileBits) * (int)sizeof(typename TR::W);
+  cudaError_t e = cudaFuncSetAttribute(k_mixer<TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_mixer<TR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// Enqueue one full evaluation (forward, energy, optional backward) for B states and depth p.
+template <class TR>
+cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
+  using V = typename TR::V;
+  using RX = typename TR::RX;
+  using PH = typename TR::PH;
+  const uint64_t N = q->N;
+  cudaStream_t s = q->stream;
+  V* phi = (V*)q->phi;
+  V* lam = (V*)q->lam;
+  const RX* rx = (const RX*)q->rx;
+  const PH* tab = (const PH*)q->tables;
+  const int tsize = q->n_edges + 1;
+  const int out_stride = 1 + 2 * kMaxP;
+  const int PB = blocks_per_state(q, B);
+  const int ps = part_stride_for(q);
+  int launches = 0;
+  const double amp = std::pow(2.0, -q->n / 2.0);
+  V v0;
+  v0.x = (decltype(v0.x))amp;
+  v0.y = 0;
+  k_fill_uniform<V><<<grid_for(N * B, 1, 16), kThreads, 0, s>>>(phi, N * B, v0);
+  ++launches;
+  const dim3 g_stream(PB, B);
+  for (int l = 0; l < p; ++l) {
+    k_phase<TR, false><<<g_stream, kThreads, 0, s>>>(phi, nullptr, N, q->cut, tab + (uint64_t)l * q->bmax * tsize,
+                                                     tsize, nullptr, 0, q->flag);
+    ++launches;
+    for (const Geo& g : q->passes) {
+      const uint64_t tiles = N >> (g.c + g.m);
+      const dim3 grid((unsigned)std::min<uint64_t>(tiles, (uint64_t)PB), B);
+      k_mixer<TR, false><<<grid, kThreads, tile_smem<TR>(g, 1), s>>>(phi, nullptr, N, g, rx + (uint64_t)l * q->bmax,
+                                                                     nullptr, 0, q->flag);
+      ++launches;
+    }
+  }
+  k_energy_lambda<TR><<<g_stream, kThreads, 0, s>>>(phi, grad ? lam : nullptr, N, q->cut, q->partials, ps, q->flag);
+  k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->results, out_stride, 0);
+  launches += 2;
+  if (grad) {
+    const int R = q->renorm_every;
+    if (R > 0) {  // record |lambda|^2 as the target of later rescaling
+      k_norm_batch<TR><<<g_stream, kThreads, 0, s>>>(lam, N, q->partials, ps, q->flag);
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms + q->bmax, 1, 0);
+      launches += 2;
+    }
+    for (int l = p - 1; l >= 0; --l) {
+      int col = 0;
+      for (const Geo& g : q->passes) {
+        const uint64_t tiles = N >> (g.c + g.m);
+        const unsigned gx = (unsigned)std::min<uint64_t>(tiles, (uint64_t)PB);
+        const dim3 grid(gx, B);
+        k_mixer<TR, true><<<grid, kThreads, tile_smem<TR>(g, 2), s>>>(phi, lam, N, g, rx + (uint64_t)l * q->bmax,
+                                                                      q->partials + col, ps, q->flag);
+        col += gx;
+        ++launches;
+      }
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, col, ps, 2.0, q->results, out_stride, 1 + p + l);
+      k_phase<TR, true><<<g_stream, kThreads, 0, s>>>(phi, lam, N, q->cut, tab + (uint64_t)l * q->bmax * tsize, tsize,
+                                                      q->partials, ps, q->flag);
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 2.0, q->results, out_stride, 1 + l);
+      launches += 3;
+      if (R > 0 && l > 0 && ((p - l) % R) == 0) {
+        k_norm_batch<TR><<<g_stream, kThreads, 0, s>>>(phi, N, q->partials, ps, q->flag);
+        k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms, 1, 0);
+        k_rescale<V><<<g_stream, kThreads, 0, s>>>(phi, N, q->norms, nullptr);
+        k_norm_batch<TR><<<g_stream, kThreads, 0, s>>>(lam, N, q->partials, ps, q->flag);
+        k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms, 1, 0);
+        k_rescale<V><<<g_stream, kThreads, 0, s>>>(lam, N, q->norms, q->norms + q->bmax);
+        launches += 6;
+      }
+    }
+  }
+  *n_launches = launches;
+  return cudaGetLastError();
+}
+
+// Host-side parameters: RX(2 beta) coefficients and exp(-i gamma k) tables, FP64-built.
+void fill_params_c64(iqs_qaoa* q, int B, int p, const double* gam, const double* bet) {
+  float2* rx = (float2*)q->host_params;
+  float2* tab = (float2*)(q->host_params + q->rx_bytes);
+  const int tsize = q->n_edges + 1;
+  for (int l = 0; l < p; ++l)
+    for (int b = 0; b < B; ++b) {
+      const double be = bet[(uint64_t)b * p + l], ga = gam[(uint64_t)b * p + l];
+      rx[(uint64_t)l * q->bmax + b] = make_float2((float)std::cos(be), (float)std::sin(be));
+      for (int k = 0; k < tsize; ++k)
+        tab[((uint64_t)l * q->bmax + b) * tsize + k] = make_float2((float)std::cos(ga * k), (float)-std::sin(ga * k));
+    }
+}
+
+void fill_params_c128(iqs_qaoa* q, int B, int p, const double* gam, const double* bet) {
+  qops::RXc* rx = (qops::RXc*)q->host_params;
+  qops::Ph* tab = (qops::Ph*)(q->host_params + q->rx_bytes);
+  const int tsize = q->n_edges + 1;
+  for (int l = 0; l < p; ++l)
+    for (int b = 0; b < B; ++b) {
+      const double be = bet[(uint64_t)b * p + l], ga = gam[(uint64_t)b * p + l];
+      qops::RXc& r = rx[(uint64_t)l * q->bmax + b];
+      r.c = dfx::make_coef(std::cos(be));
+      r.s = dfx::make_coef(std::sin(be));
+      r.ns = dfx::make_coef(-std::sin(be));
+      for (int k = 0; k < tsize; ++k) {
+        qops::Ph& t = tab[((uint64_t)l * q->bmax + b) * tsize + k];
+        const double tr = std::cos(ga * k), ti = -std::sin(ga * k);
+        t.tr = dfx::make_coef(tr);
+        t.ti = dfx::make_coef(ti);
+        t.nti = dfx::make_coef(-ti);
+      }
+    }
+}
+
+void free_qaoa(iqs_qaoa* q) {
+  for (auto& kv : q->graphs) cudaGraphExecDestroy(kv.second.first);
+  if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
+  cudaFree(q->phi);
+  cudaFree(q->lam);
+  cudaFree(q->cut);
+  cudaFree(q->rx);
+  cudaFree(q->tables);
+  cudaFree(q->partials);
+  cudaFree(q->results);
+  cudaFree(q->norms);
+  cudaFree(q->flag);
+  if (q->host_params) cudaFreeHost(q->host_params);
+  if (q->host_results) cudaFreeHost(q->host_results);
+  delete q;
+}
+
+}  // namespace
+}  // namespace iqs
+
+extern "C" {
+
+iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const int32_t* edges, void* stream,
+                           iqs_qaoa** out) {
+  using namespace iqs;
+  if (out == nullptr) return report(IQS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 2 || n > IQS_MAX_QUBITS) return report(IQS_EINVAL, "number of qubits %d outside [2, %d]", n, IQS_MAX_QUBITS);
+  if (dtype != IQS_C64 && dtype != IQS_C128) return report(IQS_EINVAL, "dtype must be IQS_C64 or IQS_C128");
+  if (batch_max < 1 || batch_max > 65535) return report(IQS_EINVAL, "batch_max %d outside [1, 65535]", batch_max);
+  if (n_edges < 1 || n_edges > kEdgeChunk || edges == nullptr)
+    return report(IQS_EINVAL, "n_edges %d outside [1, %d] or edges NULL", n_edges, kEdgeChunk);
+  for (int e = 0; e < n_edges; ++e) {
+    const int u = edges[2 * e], v = edges[2 * e + 1];
+    if (u < 0 || u >= n || v < 0 || v >= n || u == v)
+      return report(IQS_EINVAL, "edge %d = (%d, %d) invalid for %d qubits", e, u, v, n);
+  }
+  iqs_qaoa* q = new (std::nothrow) iqs_qaoa();
+  if (q == nullptr) return report(IQS_ENOMEM, "host allocation failed");
+  q->n = n;
+  q->dtype = dtype;
+  q->bmax = batch_max;
+  q->n_edges = n_edges;
+  q->N = 1ull << n;
+  q->stream = (cudaStream_t)stream;
+  if (q->stream == nullptr) {  // graphs cannot be captured on the legacy stream: use a blocking stream of our own
+    if (cudaStreamCreate(&q->stream) != cudaSuccess) {
+      cudaGetLastError();
+      delete q;
+      return report(IQS_ECUDA, "cannot create a stream");
+    }
+    q->own_stream = true;
+  }
+  const size_t amp = dtype == IQS_C128 ? 16 : 8;
+  const size_t tsize = (size_t)n_edges + 1;
+  q->rx_bytes = (size_t)kMaxP * batch_max * (dtype == IQS_C128 ? sizeof(qops::RXc) : sizeof(float2));
+  q->rx_bytes = (q->rx_bytes + 255) & ~(size_t)255;
+  q->table_bytes = (size_t)kMaxP * batch_max * tsize * (dtype == IQS_C128 ? sizeof(qops::Ph) : sizeof(float2));
+  const int ps = part_stride_for(q);
+  bool ok = cudaMalloc(&q->phi, amp * q->N * batch_max) == cudaSuccess &&
+            cudaMalloc(&q->lam, amp * q->N * batch_max) == cudaSuccess &&
+            cudaMalloc(&q->cut, q->N) == cudaSuccess && cudaMalloc(&q->rx, q->rx_bytes) == cudaSuccess &&
+            cudaMalloc(&q->tables, q->table_bytes) == cudaSuccess &&
+            cudaMalloc(&q->partials, sizeof(double) * (size_t)ps * batch_max) == cudaSuccess &&
+            cudaMalloc(&q->results, sizeof(double) * (size_t)batch_max * (1 + 2 * kMaxP)) == cudaSuccess &&
+            cudaMalloc(&q->norms, sizeof(double) * 2 * (size_t)batch_max) == cudaSuccess &&
+            cudaMalloc(&q->flag, sizeof(unsigned)) == cudaSuccess &&
+            cudaMallocHost(&q->host_params, q->rx_bytes + q->table_bytes) == cudaSuccess &&
+            cudaMallocHost(&q->host_results, sizeof(double) * ((size_t)batch_max * (1 + 2 * kMaxP) + 1)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_qaoa(q);
+    return report(IQS_ENOMEM, "cannot allocate the QAOA workspace (%d states of %d qubits)", batch_max, n);
+  }
+  EdgesU8 E;
+  E.m = n_edges;
+  for (int e = 0; e < n_edges; ++e) {
+    E.u[e] = (uint8_t)edges[2 * e];
+    E.v[e] = (uint8_t)edges[2 * e + 1];
+  }
+  if (n <= 32)
+    k_cut_table<uint32_t><<<grid_for(q->N, 1, 16), kThreads, 0, q->stream>>>(q->cut, q->N, E);
+  else
+    k_cut_table<uint64_t><<<grid_for(q->N, 1, 16), kThreads, 0, q->stream>>>(q->cut, q->N, E);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) note_launches(1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->flag, 0, sizeof(unsigned), q->stream);
+  if (e == cudaSuccess) e = dtype == IQS_C128 ? set_smem_attrs<T128>() : set_smem_attrs<T64>();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+  if (e != cudaSuccess) {
+    free_qaoa(q);
+    return report(IQS_ECUDA, "QAOA set-up: %s", cudaGetErrorString(e));
+  }
+  q->passes = dtype == IQS_C128 ? plan_mixer(n, T128::kTileBits, T128::kRowBits)
+                                : plan_mixer(n, T64::kTileBits, T64::kRowBits);
+  *out = q;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_destroy(iqs_qaoa* q) {
+  if (q == nullptr) return IQS_OK;
+  cudaStreamSynchronize(q->stream);
+  iqs::free_qaoa(q);
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs) {
+  if (q == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (renorm_every < 0) return iqs::report(IQS_EINVAL, "renorm_every must be >= 0");
+  q->renorm_every = renorm_every;
+  q->use_graphs = use_graphs != 0;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, const double* betas, double* energies,
+                        double* grad_gammas, double* grad_betas) {
+  using namespace iqs;
+  if (q == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (batch < 1 || batch > q->bmax) return report(IQS_EINVAL, "batch %d outside [1, %d]", batch, q->bmax);
+  if (p < 1 || p > kMaxP) return report(IQS_EINVAL, "depth p = %d outside [1, %d]", p, kMaxP);
+  if (!gammas || !betas || !energies) return report(IQS_EINVAL, "gammas, betas and energies must not be NULL");
+  const bool grad = grad_gammas != nullptr || grad_betas != nullptr;
+  if (grad && (!grad_gammas || !grad_betas)) return report(IQS_EINVAL, "give both gradient outputs or neither");
+  for (int i = 0; i < batch * p; ++i)
+    if (!std::isfinite(gammas[i]) || !std::isfinite(betas[i])) return report(IQS_EINVAL, "non-finite parameter");
+  if (q->dtype == IQS_C128) fill_params_c128(q, batch, p, gammas, betas);
+  else fill_params_c64(q, batch, p, gammas, betas);
+  cudaStream_t s = q->stream;
+  const size_t rx_elem = q->dtype == IQS_C128 ? sizeof(qops::RXc) : sizeof(float2);
+  const size_t ph_elem = q->dtype == IQS_C128 ? sizeof(qops::Ph) : sizeof(float2);
+  cudaError_t e = cudaMemcpyAsync(q->rx, q->host_params, (size_t)p * q->bmax * rx_elem, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(q->tables, q->host_params + q->rx_bytes, (size_t)p * q->bmax * (q->n_edges + 1) * ph_elem,
+                        cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return report(IQS_ECUDA, "parameter upload: %s", cudaGetErrorString(e));
+  const auto key = std::make_tuple(batch, p, grad ? 1 : 0, q->renorm_every);
+  int kernels = 0;
+  if (q->use_graphs) {
+    auto it = q->graphs.find(key);
+    if (it == q->graphs.end()) {
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t ee = q->dtype == IQS_C128 ? enqueue<T128>(q, batch, p, grad, &kernels)
+                                                    : enqueue<T64>(q, batch, p, grad, &kernels);
+        e = cudaStreamEndCapture(s, &graph);
+        if (ee != cudaSuccess) e = ee;
+      }
+      cudaGraphExec_t exec = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return report(IQS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+      it = q->graphs.emplace(key, std::make_pair(exec, kernels)).first;
+    }
+    kernels = it->second.second;
+    e = cudaGraphLaunch(it->second.first, s);
+  } else {
+    e = q->dtype == IQS_C128 ? enqueue<T128>(q, batch, p, grad, &kernels) : enqueue<T64>(q, batch, p, grad, &kernels);
+  }
+  if (e != cudaSuccess) return report(IQS_ECUDA, "QAOA launch: %s", cudaGetErrorString(e));
+  note_launches(kernels);
+  const int stride = 1 + 2 * kMaxP;
+  e = cudaMemcpyAsync(q->host_results, q->results, sizeof(double) * (size_t)batch * stride, cudaMemcpyDeviceToHost, s);
+  unsigned f = 0;
+  double* flag_slot = q->host_results + (size_t)q->bmax * stride;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flag_slot, q->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return report(IQS_ECUDA, "QAOA results: %s", cudaGetErrorString(e));
+  std::memcpy(&f, flag_slot, sizeof(unsigned));
+  for (int b = 0; b < batch; ++b) {
+    const double* r = q->host_results + (size_t)b * stride;
+    energies[b] = r[0];
+    if (grad)
+      for (int l = 0; l < p; ++l) {
+        grad_gammas[(size_t)b * p + l] = r[1 + l];
+        grad_betas[(size_t)b * p + l] = r[1 + p + l];
+      }
+  }
+  if (f) {
+    cudaMemsetAsync(q->flag, 0, sizeof(unsigned), s);
+    return report(IQS_ERANGE, "an amplitude outside the emulated-FP64 range was met");
+  }
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_download_state(iqs_qaoa* q, int index, void* host, size_t bytes) {
+  using namespace iqs;
+  if (q == nullptr || host == nullptr) return report(IQS_EINVAL, "NULL argument");
+  const size_t amp = q->dtype == IQS_C128 ? 16 : 8;
+  if (index < 0 || index >= q->bmax || bytes != amp * q->N) return report(IQS_EINVAL, "bad index or size");
+  cudaError_t e = cudaMemcpyAsync(host, (const char*)q->phi + amp * q->N * index, bytes, cudaMemcpyDeviceToHost, q->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+  if (e != cudaSuccess) return report(IQS_ECUDA, "download: %s", cudaGetErrorString(e));
+  return IQS_OK;
+}
+
+}  // extern "C"

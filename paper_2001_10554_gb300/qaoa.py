@@ -1,0 +1,119 @@
+"""QAOA Max-Cut energies and adjoint gradients (C ABI ``iqs_qaoa_*``).
+
+``QAOA`` wraps one workspace (graph, qubit count, dtype, maximum batch).
+``QAOAEnergy`` is a ``torch.autograd.Function`` whose forward evaluates the
+energies of a batch of parameter sets and whose backward returns the adjoint
+gradient computed by the CUDA engine (uncompute, no stored states).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import call, lib
+from .register import _dtype_code, _stream_handle
+
+_dp = C.POINTER(C.c_double)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+class QAOA:
+    """Workspace for QAOA Max-Cut on one unweighted graph.
+
+    ``run(gammas, betas, grad=True)`` evaluates all rows of the (batch, p)
+    parameter arrays in one engine call and returns numpy arrays
+    (energies[batch], d/dgamma[batch, p], d/dbeta[batch, p]).
+    """
+
+    def __init__(self, n: int, edges, dtype="complex64", batch_max: int = 1, stream=None,
+                 renorm_every: int = 0, use_graphs: bool = True):
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        self.n, self.n_edges, self.batch_max = int(n), e.shape[0], int(batch_max)
+        self.dtype_code = _dtype_code(dtype)
+        h = C.c_void_p()
+        call("iqs_qaoa_create", self.n, self.dtype_code, self.batch_max, self.n_edges,
+             e.ctypes.data_as(C.POINTER(C.c_int32)), _stream_handle(stream), C.byref(h))
+        self._h = h
+        self.set_options(renorm_every, use_graphs)
+
+    def set_options(self, renorm_every: int = 0, use_graphs: bool = True) -> None:
+        call("iqs_qaoa_set_options", self._h, int(renorm_every), int(bool(use_graphs)))
+
+    def run(self, gammas, betas, grad: bool = True):
+        g = np.ascontiguousarray(np.atleast_2d(np.asarray(gammas, dtype=np.float64)))
+        b = np.ascontiguousarray(np.atleast_2d(np.asarray(betas, dtype=np.float64)))
+        if g.shape != b.shape:
+            raise ValueError("gammas and betas must have the same (batch, p) shape")
+        batch, p = g.shape
+        E = np.empty(batch)
+        if grad:
+            dg, db = np.empty((batch, p)), np.empty((batch, p))
+            call("iqs_qaoa_run", self._h, batch, p, _ptr(g), _ptr(b), _ptr(E), _ptr(dg), _ptr(db))
+            return E, dg, db
+        call("iqs_qaoa_run", self._h, batch, p, _ptr(g), _ptr(b), _ptr(E), None, None)
+        return E
+
+    def state(self, index: int = 0) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.complex128 if self.dtype_code == _lib.IQS_C128 else np.complex64)
+        call("iqs_qaoa_download_state", self._h, int(index), C.c_void_p(out.ctypes.data), C.c_size_t(out.nbytes))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.iqs_qaoa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd_function():
+    import torch
+
+    class QAOAEnergy(torch.autograd.Function):
+        """energies = QAOAEnergy.apply(gammas, betas, engine) for (batch, p) tensors.
+
+        Forward runs the engine once; when gradients are needed it returns the
+        adjoint gradient in the same call and backward scales it by the
+        incoming gradient.
+        """
+
+        @staticmethod
+        def forward(ctx, gammas, betas, engine: QAOA):
+            need = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
+            g = gammas.detach().to("cpu", torch.float64).numpy()
+            b = betas.detach().to("cpu", torch.float64).numpy()
+            squeeze = g.ndim == 1
+            if need:
+                E, dg, db = engine.run(g, b, grad=True)
+                ctx.save_for_backward(torch.from_numpy(dg).to(gammas), torch.from_numpy(db).to(betas))
+            else:
+                E = engine.run(g, b, grad=False)
+            ctx.squeeze = squeeze
+            out = torch.from_numpy(E).to(device=gammas.device, dtype=torch.float64)
+            return out[0] if squeeze else out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dg, db = ctx.saved_tensors
+            go = grad_out.reshape(-1, 1).to(dg)
+            gg, gb = go * dg, go * db
+            if ctx.squeeze:
+                gg, gb = gg[0], gb[0]
+            return gg, gb, None
+
+    return QAOAEnergy
+
+
+def __getattr__(name):
+    if name == "QAOAEnergy":
+        return _autograd_function()
+    raise AttributeError(name)

@@ -1,0 +1,166 @@
+"""QAOA engine (iqs_qaoa_*): energies and adjoint gradients against the FP64
+oracle (plain forward, stored-state adjoint) and central finite differences.
+
+Tolerances:
+* complex128 (double-float emulation): energy 1e-11, gradient 1e-9 absolute
+  (a gradient sums ~2^n * (n + |E|) products per parameter).
+* complex64: the stated bound of the benchmark spec, energy error <= 1e-5
+  absolute against the FP64 oracle on the original parameters; gradients
+  within 1e-4.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import qaoa as oq
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_batch(n, edges, gm, bt):
+    E, dg, db = [], [], []
+    for k in range(gm.shape[0]):
+        e, g, b = oq.qaoa_energy_grad_stored(n, edges, gm[k], bt[k])
+        E.append(e)
+        dg.append(g)
+        db.append(b)
+    return np.array(E), np.array(dg), np.array(db)
+
+
+@pytest.mark.parametrize("n,p,batch", [(6, 1, 1), (8, 2, 3), (12, 3, 2), (13, 2, 1), (14, 4, 2)])
+def test_qaoa_c128_matches_oracle(gpu_lib, n, p, batch):
+    edges = W.random_3regular_graph(n if n % 2 == 0 else n - 1, 100 + n)
+    gm, bt = W.qaoa_parameter_sets(p, batch, 200 + n)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=batch)
+    E, dg, db = eng.run(gm, bt)
+    Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+    np.testing.assert_allclose(E, Eo, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(dg, dgo, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(db, dbo, rtol=0, atol=1e-9)
+    # energy-only path
+    E2 = eng.run(gm, bt, grad=False)
+    np.testing.assert_allclose(E2, Eo, rtol=0, atol=1e-11)
+    eng.close()
+
+
+@pytest.mark.parametrize("n,p,batch", [(8, 1, 4), (12, 4, 3), (14, 2, 2), (16, 3, 2)])
+def test_qaoa_c64_error_bound(gpu_lib, n, p, batch):
+    edges = W.random_3regular_graph(n, 300 + n)
+    gm, bt = W.qaoa_parameter_sets(p, batch, 400 + n)
+    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=batch)
+    E, dg, db = eng.run(gm, bt)
+    Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+    assert np.max(np.abs(E - Eo)) <= 1e-5
+    assert np.max(np.abs(dg - dgo)) <= 1e-4
+    assert np.max(np.abs(db - dbo)) <= 1e-4
+    eng.close()
+
+
+def test_qaoa_forward_state_matches_oracle(gpu_lib):
+    n, p = 10, 3
+    edges = W.random_3regular_graph(n, 5)
+    gm, bt = W.qaoa_parameter_sets(p, 2, 6)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=2)
+    eng.run(gm, bt, grad=False)
+    for k in range(2):
+        ref = oq.qaoa_state(n, edges, gm[k], bt[k])
+        assert np.max(np.abs(eng.state(k) - ref)) <= 1e-12
+    # after the uncompute, phi is back at |+>^n
+    eng.run(gm, bt, grad=True)
+    assert np.max(np.abs(eng.state(1) - 2 ** (-n / 2))) <= 1e-11
+
+
+def test_qaoa_graph_replay_with_new_parameters(gpu_lib):
+    """A cached CUDA graph must read each call's parameters."""
+    n, p = 10, 2
+    edges = W.random_3regular_graph(n, 7)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=4)
+    for seed in (1, 2, 3):
+        gm, bt = W.qaoa_parameter_sets(p, 4, seed)
+        E, dg, db = eng.run(gm, bt)
+        Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+        np.testing.assert_allclose(E, Eo, rtol=0, atol=1e-11)
+        np.testing.assert_allclose(db, dbo, rtol=0, atol=1e-9)
+    # a smaller batch in the same workspace, and the un-captured path
+    gm, bt = W.qaoa_parameter_sets(p, 2, 9)
+    E, dg, db = eng.run(gm, bt)
+    eng.set_options(0, use_graphs=False)
+    E2, dg2, db2 = eng.run(gm, bt)
+    np.testing.assert_allclose(E2, E, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(dg2, dg, rtol=0, atol=1e-12)
+
+
+def test_qaoa_gradient_vs_finite_differences(gpu_lib):
+    n, p = 12, 3
+    edges = W.random_3regular_graph(n, 11)
+    gm, bt = W.qaoa_parameter_sets(p, 1, 12)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=2 * p)
+    E, dg, db = eng.run(gm, bt)
+    h = 1e-5
+    for which in ("g", "b"):
+        P = np.repeat(gm if which == "g" else bt, 2 * p, axis=0)
+        for k in range(p):
+            P[2 * k, k] += h
+            P[2 * k + 1, k] -= h
+        Ep = eng.run(P, np.repeat(bt, 2 * p, axis=0), grad=False) if which == "g" else \
+            eng.run(np.repeat(gm, 2 * p, axis=0), P, grad=False)
+        fd = (Ep[0::2] - Ep[1::2]) / (2 * h)
+        ref = dg[0] if which == "g" else db[0]
+        np.testing.assert_allclose(fd, ref, rtol=0, atol=1e-7)
+
+
+def test_qaoa_renormalisation_keeps_results(gpu_lib):
+    n, p = 12, 6
+    edges = W.random_3regular_graph(n, 13)
+    gm, bt = W.qaoa_parameter_sets(p, 2, 14)
+    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=2)
+    E0, dg0, db0 = eng.run(gm, bt)
+    eng.set_options(renorm_every=2)
+    E1, dg1, db1 = eng.run(gm, bt)
+    Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+    assert np.max(np.abs(E1 - Eo)) <= 1e-5
+    assert np.max(np.abs(dg1 - dgo)) <= 1e-4
+    assert np.max(np.abs(db1 - dbo)) <= 1e-4
+
+
+def test_qaoa_batch_items_equal_single_runs(gpu_lib):
+    n, p, B = 12, 2, 5
+    edges = W.random_3regular_graph(n, 15)
+    gm, bt = W.qaoa_parameter_sets(p, B, 16)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=B)
+    E, dg, db = eng.run(gm, bt)
+    for k in range(B):
+        e1, g1, b1 = eng.run(gm[k:k + 1], bt[k:k + 1])
+        np.testing.assert_allclose(E[k], e1[0], rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(dg[k], g1[0], rtol=1e-12, atol=1e-13)
+
+
+def test_qaoa_autograd_function(gpu_lib):
+    import torch
+    from paper_2001_10554_gb300.qaoa import QAOAEnergy
+    n, p = 10, 2
+    edges = W.random_3regular_graph(n, 17)
+    gm, bt = W.qaoa_parameter_sets(p, 3, 18)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=3)
+    g = torch.tensor(gm, requires_grad=True)
+    b = torch.tensor(bt, requires_grad=True)
+    E = QAOAEnergy.apply(g, b, eng)
+    w = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64)
+    (E * w).sum().backward()
+    Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+    np.testing.assert_allclose(E.detach().numpy(), Eo, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(g.grad.numpy(), w.numpy()[:, None] * dgo, rtol=0, atol=2e-9)
+    np.testing.assert_allclose(b.grad.numpy(), w.numpy()[:, None] * dbo, rtol=0, atol=2e-9)
+
+
+def test_qaoa_rejects_bad_arguments(gpu_lib):
+    from paper_2001_10554_gb300 import IQSError
+    with pytest.raises(IQSError):
+        gpu_lib.QAOA(6, [(0, 6)], "complex64")
+    with pytest.raises(IQSError):
+        gpu_lib.QAOA(6, [(1, 1)], "complex64")
+    eng = gpu_lib.QAOA(6, W.random_3regular_graph(6, 1), "complex64", batch_max=2)
+    with pytest.raises(IQSError):
+        eng.run(np.zeros((3, 1)), np.zeros((3, 1)))
+    with pytest.raises(IQSError):
+        eng.run(np.full((1, 1), np.nan), np.zeros((1, 1)))
