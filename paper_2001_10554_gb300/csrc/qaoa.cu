@@ -27,6 +27,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -50,6 +51,12 @@ struct T64 {
   using PH = float2;  // exp(-i gamma k)
   static constexpr int kTileBits = 12;  // 4096 x 8 B = 32 KiB per vector
   static constexpr int kRowBits = 4;    // 16 contiguous amplitudes (128 B) per tile row
+  static constexpr int kRegBits = 4;    // gates per register round (16 amplitudes per thread)
+  static constexpr int kSwzBits = 4;    // 16 elements of 8 B per 128-byte smem row
+  // Gradient terms of one register round (at most 32) are summed in FP32
+  // before the double-float accumulation: their rounding (<= 32 * 2^-24 of the
+  // terms) stays below the complex64 state's own error.
+  static constexpr bool kBlockSum = true;
   __device__ static W load(V v, unsigned&) { return v; }
   __device__ static V store(const W& w) { return w; }
   __device__ static RX rx_inv(RX k) { return make_float2(k.x, -k.y); }
@@ -65,6 +72,9 @@ struct T128 {
   using PH = qops::Ph;
   static constexpr int kTileBits = 11;  // 2048 x 16 B = 32 KiB per vector
   static constexpr int kRowBits = 3;    // 8 contiguous amplitudes (128 B) per tile row
+  static constexpr int kRegBits = 3;    // gates per register round (8 amplitudes per thread)
+  static constexpr int kSwzBits = 3;    // 8 elements of 16 B per 128-byte smem row
+  static constexpr bool kBlockSum = false;  // every gradient term goes to the double-float accumulator
   __device__ static W load(V v, unsigned& bad) { return qops::to_split(v, bad); }
   __device__ static V store(const W& w) { return qops::from_split(w); }
   __device__ static RX rx_inv(RX k) {
@@ -126,57 +136,228 @@ __global__ void k_cut_table(uint8_t* cut, uint64_t N, EdgesU8 E) {
     cut[i] = (uint8_t)cut_count((X)i, E);
 }
 
+// Shared-memory index of tile element l: XOR-swizzled within 128-byte rows so
+// that a warp reading a fixed offset of 32 consecutive register blocks (rows
+// of stride 2^kSwzBits elements) hits distinct banks.
+template <class TR>
+__device__ __forceinline__ unsigned swz(unsigned l) {
+  return l ^ ((l >> TR::kSwzBits) & ((1u << TR::kSwzBits) - 1u));
+}
+
 // Mixer pass: RX on the qubits [s, s+m) of every tile (or its inverse, with the
-// gradient term, on two vectors when ADJ).
+// gradient term, on two vectors when ADJ).  The tile is staged in shared
+// memory; the gate bits are processed in rounds of up to kRegBits bits, each
+// thread holding the 2^kRegBits amplitudes of one register block and applying
+// that round's gates in registers.
 template <class TR, bool ADJ>
 __global__ void __launch_bounds__(kThreads) k_mixer(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam,
                                                     uint64_t N, Geo g, const typename TR::RX* __restrict__ rx,
                                                     double* __restrict__ partials, int part_stride, unsigned* flag) {
   using W = typename TR::W;
+  constexpr int R = TR::kRegBits;
+  constexpr int RB = 1 << R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* sp = reinterpret_cast<W*>(smem_raw);
-  const unsigned T = 1u << (g.c + g.m);
+  const unsigned K = g.c + g.m;
+  const unsigned T = 1u << K;
   W* sl = sp + T;
   const unsigned b = blockIdx.y;
   typename TR::V* P = phi + (uint64_t)b * N;
   typename TR::V* L = ADJ ? lam + (uint64_t)b * N : nullptr;
   const typename TR::RX k = ADJ ? TR::rx_inv(rx[b]) : rx[b];
-  const uint64_t tiles = N >> (g.c + g.m);
+  const uint64_t tiles = N >> K;
   unsigned bad = 0;
   dfx::Acc acc;
   for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     for (unsigned l = threadIdx.x; l < T; l += blockDim.x) {
       const uint64_t x = tile_x(g, t, l);
-      sp[l] = TR::load(P[x], bad);
-      if (ADJ) sl[l] = TR::load(L[x], bad);
+      sp[swz<TR>(l)] = TR::load(P[x], bad);
+      if (ADJ) sl[swz<TR>(l)] = TR::load(L[x], bad);
     }
     __syncthreads();
-    for (int j = 0; j < g.m; ++j) {
-      const int lb = g.c + j;
-      for (unsigned pi = threadIdx.x; pi < (T >> 1); pi += blockDim.x) {
-        const unsigned i0 = (unsigned)insert_zero(pi, lb), i1 = i0 | (1u << lb);
-        W x0 = sp[i0], x1 = sp[i1];
-        if (ADJ) {
-          W y0 = sl[i0], y1 = sl[i1];
-          float p, e;
-          qops::im_conj_mul(y0, x1, p, e);
-          acc.add(p, e);
-          qops::im_conj_mul(y1, x0, p, e);
-          acc.add(p, e);
-          TR::rx(y0, y1, k);
-          sl[i0] = y0;
-          sl[i1] = y1;
+    for (int pos = g.c; pos < (int)K; pos += R) {
+      const int gb = min(R, (int)K - pos);
+      const unsigned nsub = T >> gb;
+      for (unsigned sb = threadIdx.x; sb < nsub; sb += blockDim.x) {
+        const unsigned base = ((sb >> pos) << (pos + gb)) | (sb & ((1u << pos) - 1u));
+        W a[RB];
+        W y[ADJ ? RB : 1];
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+          if (j < (1 << gb)) {
+            const unsigned idx = swz<TR>(base | ((unsigned)j << pos));
+            a[j] = sp[idx];
+            if (ADJ) y[j] = sl[idx];
+          }
         }
-        TR::rx(x0, x1, k);
-        sp[i0] = x0;
-        sp[i1] = x1;
+        float rsum = 0.f;  // FP32 block sum of this round's gradient terms (complex64)
+#pragma unroll
+        for (int bit = 0; bit < R; ++bit) {
+          if (bit < gb) {
+#pragma unroll
+            for (int j = 0; j < RB; ++j) {
+              if (!(j & (1 << bit)) && j < (1 << gb)) {
+                const int j1 = j | (1 << bit);
+                if (ADJ) {
+                  if constexpr (TR::kBlockSum) {
+                    rsum = qops::im_conj_mul_fma(y[j], a[j1], rsum);
+                    rsum = qops::im_conj_mul_fma(y[j1], a[j], rsum);
+                  } else {
+                    float p, e;
+                    qops::im_conj_mul(y[j], a[j1], p, e);
+                    acc.add(p, e);
+                    qops::im_conj_mul(y[j1], a[j], p, e);
+                    acc.add(p, e);
+                  }
+                  TR::rx(y[j], y[j1], k);
+                }
+                TR::rx(a[j], a[j1], k);
+              }
+            }
+          }
+        }
+        if (ADJ && TR::kBlockSum) acc.add(rsum, 0.f);
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+          if (j < (1 << gb)) {
+            const unsigned idx = swz<TR>(base | ((unsigned)j << pos));
+            sp[idx] = a[j];
+            if (ADJ) sl[idx] = y[j];
+          }
+        }
       }
       __syncthreads();
     }
     for (unsigned l = threadIdx.x; l < T; l += blockDim.x) {
       const uint64_t x = tile_x(g, t, l);
-      P[x] = TR::store(sp[l]);
-      if (ADJ) L[x] = TR::store(sl[l]);
+      P[x] = TR::store(sp[swz<TR>(l)]);
+      if (ADJ) L[x] = TR::store(sl[swz<TR>(l)]);
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(flag, 1u);
+  if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+}
+
+// The same pass for the two common tile shapes with everything but the tile
+// placement known at compile time: C row bits, then M gate bits, K = C + M =
+// kTileBits.  C = 0 is the low pass (tile = 2^K contiguous amplitudes); C > 0
+// is a high pass whose gate bits start at s.  Since swz() is linear over
+// GF(2), the shared-memory index of (base | j << POS) is swz(base) ^ swz(j << POS),
+// one XOR with a compile-time constant per element.
+template <class TR, bool ADJ, int C, int POS, int GB>
+__device__ __forceinline__ void mixer_round(typename TR::W* sp, typename TR::W* sl, const typename TR::RX& k,
+                                            float& rsum_out, dfx::Acc& acc) {
+  using W = typename TR::W;
+  constexpr int K = TR::kTileBits;
+  constexpr unsigned NSUB = 1u << (K - GB);
+  constexpr int RB = 1 << GB;
+  for (unsigned sb = threadIdx.x; sb < NSUB; sb += blockDim.x) {
+    const unsigned base = ((sb >> POS) << (POS + GB)) | (sb & ((1u << POS) - 1u));
+    const unsigned sbase = swz<TR>(base);
+    W a[RB];
+    W y[ADJ ? RB : 1];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      const unsigned idx = sbase ^ swz<TR>((unsigned)j << POS);
+      a[j] = sp[idx];
+      if (ADJ) y[j] = sl[idx];
+    }
+    float rsum = 0.f;
+#pragma unroll
+    for (int bit = 0; bit < GB; ++bit) {
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        if (!(j & (1 << bit))) {
+          const int j1 = j | (1 << bit);
+          if (ADJ) {
+            if constexpr (TR::kBlockSum) {
+              rsum = qops::im_conj_mul_fma(y[j], a[j1], rsum);
+              rsum = qops::im_conj_mul_fma(y[j1], a[j], rsum);
+            } else {
+              float p, e;
+              qops::im_conj_mul(y[j], a[j1], p, e);
+              acc.add(p, e);
+              qops::im_conj_mul(y[j1], a[j], p, e);
+              acc.add(p, e);
+            }
+            TR::rx(y[j], y[j1], k);
+          }
+          TR::rx(a[j], a[j1], k);
+        }
+      }
+    }
+    if (ADJ && TR::kBlockSum) acc.add(rsum, 0.f);
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      const unsigned idx = sbase ^ swz<TR>((unsigned)j << POS);
+      sp[idx] = a[j];
+      if (ADJ) sl[idx] = y[j];
+    }
+  }
+  (void)rsum_out;
+}
+
+template <class TR, bool ADJ, int C, int POS>
+__device__ __forceinline__ void mixer_rounds(typename TR::W* sp, typename TR::W* sl, const typename TR::RX& k,
+                                             dfx::Acc& acc) {
+  constexpr int K = TR::kTileBits;
+  if constexpr (POS < K) {
+    constexpr int GB = (K - POS) < TR::kRegBits ? (K - POS) : TR::kRegBits;
+    float dummy = 0.f;
+    mixer_round<TR, ADJ, C, POS, GB>(sp, sl, k, dummy, acc);
+    __syncthreads();
+    mixer_rounds<TR, ADJ, C, POS + GB>(sp, sl, k, acc);
+  }
+}
+
+template <class TR, bool ADJ, int C>
+__global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restrict__ phi,
+                                                         typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
+                                                         const typename TR::RX* __restrict__ rx,
+                                                         double* __restrict__ partials, int part_stride, unsigned* flag) {
+  using W = typename TR::W;
+  constexpr int K = TR::kTileBits;
+  constexpr int M = K - C;
+  constexpr unsigned T = 1u << K;
+  constexpr unsigned PER = T / kThreads;  // elements per thread in the load/store phases
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* sp = reinterpret_cast<W*>(smem_raw);
+  W* sl = sp + T;
+  const unsigned b = blockIdx.y;
+  typename TR::V* P = phi + (uint64_t)b * N;
+  typename TR::V* L = ADJ ? lam + (uint64_t)b * N : nullptr;
+  const typename TR::RX k = ADJ ? TR::rx_inv(rx[b]) : rx[b];
+  const uint64_t tiles = N >> K;
+  const unsigned tid = threadIdx.x;
+  // element l = tid + kThreads * i sits at (l >> C) << s | (l & (2^C - 1)) inside the tile
+  // footprint; for C <= 8 that is off0 + i * step (kThreads = 2^8 carries no bit into the row).
+  const int s = C == 0 ? 0 : s_bits;
+  const uint64_t off0 = C == 0 ? tid : ((uint64_t)(tid >> C) << s) | (tid & ((1u << C) - 1u));
+  const uint64_t step = C == 0 ? kThreads : ((uint64_t)(kThreads >> (C <= 8 ? C : 8)) << s);
+  const unsigned sw0 = swz<TR>(tid);
+  const int mid = s - C;
+  unsigned bad = 0;
+  dfx::Acc acc;
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
+#pragma unroll
+    for (unsigned i = 0; i < PER; ++i) {
+      const unsigned l = tid + kThreads * i;
+      const uint64_t x = C <= 8 ? tbase + off0 + step * i : tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
+      const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
+      sp[idx] = TR::load(P[x], bad);
+      if (ADJ) sl[idx] = TR::load(L[x], bad);
+    }
+    __syncthreads();
+    mixer_rounds<TR, ADJ, C, C>(sp, sl, k, acc);
+#pragma unroll
+    for (unsigned i = 0; i < PER; ++i) {
+      const unsigned l = tid + kThreads * i;
+      const uint64_t x = C <= 8 ? tbase + off0 + step * i : tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
+      const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
+      P[x] = TR::store(sp[idx]);
+      if (ADJ) L[x] = TR::store(sl[idx]);
     }
     __syncthreads();
   }
@@ -336,15 +517,24 @@ int blocks_per_state(const iqs_qaoa* q, int B) {
   return (int)std::min<uint64_t>(by_size, (uint64_t)std::min(by_batch, 2432));
 }
 
+// Mixer passes for n qubits: a low pass over the first min(n, K) qubits
+// (contiguous tile), then the remaining qubits spread evenly over high passes
+// of at most K - row_bits gate bits each; every high pass fills its tile to
+// 2^K amplitudes with K - m contiguous row bits.
 std::vector<Geo> plan_mixer(int n, int tile_bits, int row_bits) {
   std::vector<Geo> out;
   const int m0 = std::min(n, tile_bits);
   out.push_back(Geo{0, 0, m0});
-  int q0 = m0;
-  while (q0 < n) {
-    const int mm = std::min(n - q0, tile_bits - row_bits);
-    out.push_back(Geo{row_bits, q0, mm});
-    q0 += mm;
+  const int rem = n - m0;
+  if (rem > 0) {
+    const int maxm = tile_bits - row_bits;
+    const int np = (rem + maxm - 1) / maxm;
+    int q0 = m0;
+    for (int i = 0; i < np; ++i) {
+      const int mm = rem / np + (i < rem % np ? 1 : 0);
+      out.push_back(Geo{tile_bits - mm, q0, mm});
+      q0 += mm;
+    }
   }
   return out;
 }
@@ -354,12 +544,67 @@ size_t tile_smem(const Geo& g, int nvec) {
   return (size_t)nvec * ((size_t)1 << (g.c + g.m)) * sizeof(typename TR::W);
 }
 
+template <class TR, bool ADJ, int C>
+void launch_fast(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N, int sb,
+                 const typename TR::RX* rx, double* partials, int ps, unsigned* flag) {
+  k_mixer_fast<TR, ADJ, C><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag);
+}
+
+template <class TR, int C>
+cudaError_t set_attr_c(int bytes) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C>, a, bytes);
+  return e;
+}
+
+template <class TR, int... Cs>
+cudaError_t set_attr_all(int bytes, std::integer_sequence<int, Cs...>) {
+  cudaError_t e = cudaSuccess;
+  ((e = (e == cudaSuccess ? set_attr_c<TR, Cs>(bytes) : e)), ...);
+  return e;
+}
+
 template <class TR>
 cudaError_t set_smem_attrs() {
   const int bytes = 2 * (1 << TR::kTileBits) * (int)sizeof(typename TR::W);
-  cudaError_t e = cudaFuncSetAttribute(k_mixer<TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_mixer<TR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_mixer<TR, false>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer<TR, true>, a, bytes);
+  if (e == cudaSuccess) e = set_attr_c<TR, 0>(bytes);
+  if (e == cudaSuccess) e = set_attr_all<TR>(bytes, std::make_integer_sequence<int, TR::kTileBits>{});
+  return e;
+}
+
+template <class TR, bool ADJ, int... Cs>
+bool dispatch_fast(int c, dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam,
+                   uint64_t N, int sb, const typename TR::RX* rx, double* partials, int ps, unsigned* flag,
+                   std::integer_sequence<int, Cs...>) {
+  bool done = false;
+  ((c == Cs && Cs >= TR::kRowBits && !done
+        ? (launch_fast<TR, ADJ, (Cs >= TR::kRowBits ? Cs : TR::kRowBits)>(grid, smem, s, phi, lam, N, sb, rx, partials,
+                                                                          ps, flag),
+           done = true)
+        : false),
+   ...);
+  return done;
+}
+
+// One mixer pass: a kernel specialised for the tile shape when the tile is
+// full (2^kTileBits amplitudes), the generic one otherwise (tiny states).
+template <class TR, bool ADJ>
+void launch_mixer(const Geo& g, dim3 grid, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N,
+                  const typename TR::RX* rx, double* partials, int ps, unsigned* flag) {
+  const size_t smem = tile_smem<TR>(g, ADJ ? 2 : 1);
+  if (g.c + g.m == TR::kTileBits && g.c == 0 && g.s == 0) {
+    launch_fast<TR, ADJ, 0>(grid, smem, s, phi, lam, N, 0, rx, partials, ps, flag);
+    return;
+  }
+  if (g.c + g.m == TR::kTileBits &&
+      dispatch_fast<TR, ADJ>(g.c, grid, smem, s, phi, lam, N, g.s, rx, partials, ps, flag,
+                             std::make_integer_sequence<int, TR::kTileBits>{}))
+    return;
+  k_mixer<TR, ADJ><<<grid, kThreads, smem, s>>>(phi, lam, N, g, rx, partials, ps, flag);
 }
 
 // Enqueue one full evaluation (forward, energy, optional backward) for B states and depth p.
@@ -393,8 +638,7 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
     for (const Geo& g : q->passes) {
       const uint64_t tiles = N >> (g.c + g.m);
       const dim3 grid((unsigned)std::min<uint64_t>(tiles, (uint64_t)PB), B);
-      k_mixer<TR, false><<<grid, kThreads, tile_smem<TR>(g, 1), s>>>(phi, nullptr, N, g, rx + (uint64_t)l * q->bmax,
-                                                                     nullptr, 0, q->flag);
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)l * q->bmax, nullptr, 0, q->flag);
       ++launches;
     }
   }
@@ -414,8 +658,7 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
         const uint64_t tiles = N >> (g.c + g.m);
         const unsigned gx = (unsigned)std::min<uint64_t>(tiles, (uint64_t)PB);
         const dim3 grid(gx, B);
-        k_mixer<TR, true><<<grid, kThreads, tile_smem<TR>(g, 2), s>>>(phi, lam, N, g, rx + (uint64_t)l * q->bmax,
-                                                                      q->partials + col, ps, q->flag);
+        launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx + (uint64_t)l * q->bmax, q->partials + col, ps, q->flag);
         col += gx;
         ++launches;
       }

@@ -121,6 +121,12 @@ __device__ __forceinline__ void im_conj_mul(const S2& l, const S2& f, float& p, 
   e = e1 - e2 + t;
 }
 
+// acc + Im(conj(l) * f) in plain FP32 (two FMAs; complex64 block sums)
+__device__ __forceinline__ float im_conj_mul_fma(float2 l, float2 f, float acc) {
+  return fmaf(-l.y, f.x, fmaf(l.x, f.y, acc));
+}
+__device__ __forceinline__ float im_conj_mul_fma(const S2&, const S2&, float acc) { return acc; }  // unused for complex128
+
 // |x|^2
 __device__ __forceinline__ void abs2(float2 x, float& p, float& e) { dfx::abs2_c64(x.x, x.y, p, e); }
 __device__ __forceinline__ void abs2(const S2& x, float& p, float& e) {
