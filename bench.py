@@ -52,6 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the complex64 32q sweep and the QAOA sections")
     return ap.parse_args(argv)
 
 
@@ -200,6 +201,118 @@ def kernel_traffic(kernel_key: str):
     return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
 
 
+# ---------------------------------------------------------------- extra sections (same JSON line)
+def sweep_c64(iqs, torch, dev, n: int, steps: int, warmup: int):
+    """The same sweep on an n-qubit complex64 state (FP32 gate arithmetic);
+    returns GB/s over the gates and the one-qubit kernel's average launch."""
+    from paper_2001_10554_gb300 import _lib
+    from paper_2001_10554_gb300.register import mat8
+    N = 1 << n
+    Us, pairs, _ = sweep_ops(n)
+    U8 = [mat8(U) for U in Us]
+    X8 = mat8(np.array([[0, 1], [1, 0]]))
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(SEED_STATE)
+        st = torch.empty(N, dtype=torch.complex64, device=dev)
+        st.view(torch.float32).normal_(generator=gen)
+        st.div_(torch.linalg.vector_norm(st.view(torch.float32)))
+    stream.synchronize()
+    reg = iqs.Register.wrap(st, stream=stream)
+    L, h = _lib.lib, reg.handle
+    ev = []
+
+    def one(rec):
+        for q in range(n):
+            if rec:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            _lib.check(L.iqs_apply_1q(h, q, U8[q]), "iqs_apply_1q")
+            if rec:
+                b.record(stream)
+                ev.append((a, b))
+        for c, t in pairs:
+            _lib.check(L.iqs_apply_c1q(h, int(c), int(t), X8), "iqs_apply_c1q")
+
+    for _ in range(warmup):
+        one(False)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t0.record(stream)
+    for _ in range(steps):
+        one(True)
+    t1.record(stream)
+    t1.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    avg1q = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    byt = n * 2 * 8 * N + N_CNOT * 2 * 8 * (N // 2)
+    reg.close()
+    del st
+    torch.cuda.empty_cache()
+    return {"workload": f"{n}-qubit complex64 sweep ({N * 8 / 2**30:.0f} GiB): apply_1q on q=0..{n-1} + {N_CNOT} CNOT",
+            "value": round(byt / (ms * 1e-3) / 1e9, 1), "unit": "GB/s", "ms_per_step": round(ms, 3),
+            "avg_1q_launch_ms": round(avg1q, 4), "avg_1q_GBs": round(2 * 8 * N / (avg1q * 1e-3) / 1e9, 1),
+            "error_bound": "FP32 gate arithmetic: <= 8 * 2^-24 per gate on unit-norm states (tests/test_gpu_parity.py)"}
+
+
+def qaoa_section(iqs, torch):
+    """Batched complex64 QAOA energy + adjoint gradient (256 parameter sets per
+    graph, one engine call) against the plain complex128 path (one parameter
+    set per call), on seeded random 3-regular graphs; plus the 28-qubit
+    large-adjoint configuration."""
+    import workloads as W
+    out = {"workload": "QAOA Max-Cut on random 3-regular graphs, p=4, 256 (gamma, beta) sets per graph; "
+                       "energy <C> + adjoint gradient", "rows": []}
+    p, B = 4, 256
+    for n in (16, 20, 24):
+        edges = W.random_3regular_graph(n, 1000 + n)
+        gm, bt = W.qaoa_parameter_sets(p, B, 2000 + n)
+        eng = iqs.QAOA(n, edges, "complex64", batch_max=B)
+        eng.run(gm, bt)  # capture the graph
+        reps = 2
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            E64, _, _ = eng.run(gm, bt)
+        dt = (time.perf_counter() - t0) / reps
+        eng.close()
+        plain = iqs.QAOA(n, edges, "complex128", batch_max=1)
+        k = 8
+        plain.run(gm[:1], bt[:1])
+        E128 = np.empty(k)
+        t0 = time.perf_counter()
+        for i in range(k):
+            E128[i] = plain.run(gm[i:i + 1], bt[i:i + 1])[0][0]
+        dtp = (time.perf_counter() - t0) / k
+        plain.close()
+        torch.cuda.empty_cache()
+        model = (12 * p + 2) * 8 * (1 << n) * B
+        out["rows"].append({"n": n, "p": p, "batch": B,
+                            "batched_c64_evals_per_s": round(B / dt, 1),
+                            "plain_c128_evals_per_s": round(1 / dtp, 1),
+                            "ratio": round((B / dt) * dtp, 2),
+                            "energy_err_c64_vs_c128_max": float(np.max(np.abs(E64[:k] - E128))),
+                            "batched_model_GBs": round(model / dt / 1e9, 1)})
+    # large adjoint: 28 qubits, p = 4, one parameter set, complex64 with FP64 reductions
+    n = 28
+    edges = W.random_3regular_graph(n, 28)
+    gm, bt = W.qaoa_parameter_sets(4, 1, 29)
+    eng = iqs.QAOA(n, edges, "complex64", batch_max=1, renorm_every=2)
+    eng.run(gm, bt)
+    t0 = time.perf_counter()
+    E, dg, db = eng.run(gm, bt)
+    dt = time.perf_counter() - t0
+    eng.close()
+    torch.cuda.empty_cache()
+    out["adjoint_28q"] = {"n": 28, "p": 4, "dtype": "complex64 storage, FP64-equivalent reductions",
+                          "ms_per_energy_and_gradient": round(dt * 1e3, 2), "energy": float(E[0]),
+                          "model_GBs": round((12 * 4 + 2) * 8 * 2 ** 28 / dt / 1e9, 1)}
+    best = out["rows"][1]
+    out["headline"] = {"n": best["n"], "p": best["p"], "batched_c64_evals_per_s": best["batched_c64_evals_per_s"],
+                       "plain_c128_evals_per_s": best["plain_c128_evals_per_s"], "ratio": best["ratio"]}
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main(argv=None):
     args = parse_args(argv)
@@ -327,6 +440,14 @@ def main(argv=None):
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args)
 
+    reg.close()
+    del state
+    torch.cuda.empty_cache()
+    extra = {}
+    if not args.no_extra:
+        extra["c64_32q"] = sweep_c64(iqs, torch, dev, 32, steps=3, warmup=2)
+        extra["qaoa"] = qaoa_section(iqs, torch)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -347,8 +468,8 @@ def main(argv=None):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "check": {"norm2": nn, "expectation": ex, "p_mean": float(np.mean(probs))},
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
-    reg.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

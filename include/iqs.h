@@ -195,6 +195,11 @@ iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs);
 /* Evaluate ``batch`` parameter sets of depth p (1..64).  Host arrays,
  * row-major [batch][p]: gammas, betas.  Outputs (host): energies[batch] and,
  * when both are non-NULL, grad_gammas[batch][p] and grad_betas[batch][p].
+ * Energies and gradients are divided by the computed state's squared norm
+ * (FP64), i.e. Rayleigh quotients <phi|C|phi>/<phi|phi>: this removes the
+ * norm drift that FP32-rounded gate coefficients leave in complex64 (the norm
+ * is 1 in exact arithmetic).  With renorm_every > 0, phi is restored to that
+ * norm and lambda to its initial norm.
  * Synchronous.  IQS_ERANGE if a complex128 amplitude left the emulated range. */
 iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, const double* betas,
                         double* energies, double* grad_gammas, double* grad_betas);

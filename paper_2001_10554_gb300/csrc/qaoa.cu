@@ -403,7 +403,8 @@ __global__ void __launch_bounds__(kThreads) k_phase(typename TR::V* __restrict__
   if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
 }
 
-// Energy sum C |phi|^2, and lambda = C phi when lam != nullptr.
+// Energy sum C |phi|^2 and squared norm sum |phi|^2 (partials at [blockIdx.x]
+// and [gridDim.x + blockIdx.x]), and lambda = C phi when lam != nullptr.
 template <class TR>
 __global__ void __launch_bounds__(kThreads) k_energy_lambda(const typename TR::V* __restrict__ phi,
                                                             typename TR::V* __restrict__ lam, uint64_t N,
@@ -414,18 +415,29 @@ __global__ void __launch_bounds__(kThreads) k_energy_lambda(const typename TR::V
   const typename TR::V* P = phi + (uint64_t)b * N;
   typename TR::V* L = lam ? lam + (uint64_t)b * N : nullptr;
   unsigned bad = 0;
-  dfx::Acc acc;
+  dfx::Acc acc, accn;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
     const float cf = (float)cut[i];
     const typename TR::W x = TR::load(P[i], bad);
     float p, e;
     qops::abs2(x, p, e);
+    accn.add(p, e);
     const float q = cf * p;
     acc.add(q, fmaf(cf, p, -q) + cf * e);
     if (L) L[i] = TR::store(qops::scale_int(x, cf));
   }
   if (bad) atomicOr(flag, 1u);
   block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+  block_partial(accn.value(), partials + (uint64_t)b * part_stride + gridDim.x + blockIdx.x);
+}
+
+// results[b][0..count) /= norm[b]: energies and gradients become Rayleigh
+// quotients of the computed state, which removes the norm drift that rounded
+// (not exactly unitary) gate coefficients leave in complex64.
+__global__ void k_divide_results(double* __restrict__ results, int stride, int count, const double* __restrict__ norm) {
+  const unsigned b = blockIdx.x;
+  const double nb = norm[b];
+  for (int j = threadIdx.x; j < count; j += blockDim.x) results[(uint64_t)b * stride + j] /= nb;
 }
 
 // Squared norm of each state (for renormalisation).
@@ -495,7 +507,7 @@ struct iqs_qaoa {
   void* tables = nullptr;      // [kMaxP][bmax][n_edges + 1] phase factors
   double* partials = nullptr;  // [bmax][part_stride]
   double* results = nullptr;   // [bmax][1 + 2 kMaxP]
-  double* norms = nullptr;     // [2][bmax]: current norm, lambda target
+  double* norms = nullptr;     // [3][bmax]: current norm, lambda target, phi norm after the forward pass
   unsigned* flag = nullptr;
   unsigned char* host_params = nullptr;  // pinned staging of rx + tables
   double* host_results = nullptr;        // pinned
@@ -642,9 +654,11 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
       ++launches;
     }
   }
+  double* phi_norm = q->norms + 2 * q->bmax;  // |phi|^2 after the forward pass
   k_energy_lambda<TR><<<g_stream, kThreads, 0, s>>>(phi, grad ? lam : nullptr, N, q->cut, q->partials, ps, q->flag);
   k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->results, out_stride, 0);
-  launches += 2;
+  k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + PB, PB, ps, 1.0, phi_norm, 1, 0);
+  launches += 3;
   if (grad) {
     const int R = q->renorm_every;
     if (R > 0) {  // record |lambda|^2 as the target of later rescaling
@@ -670,7 +684,7 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
       if (R > 0 && l > 0 && ((p - l) % R) == 0) {
         k_norm_batch<TR><<<g_stream, kThreads, 0, s>>>(phi, N, q->partials, ps, q->flag);
         k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms, 1, 0);
-        k_rescale<V><<<g_stream, kThreads, 0, s>>>(phi, N, q->norms, nullptr);
+        k_rescale<V><<<g_stream, kThreads, 0, s>>>(phi, N, q->norms, phi_norm);
         k_norm_batch<TR><<<g_stream, kThreads, 0, s>>>(lam, N, q->partials, ps, q->flag);
         k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms, 1, 0);
         k_rescale<V><<<g_stream, kThreads, 0, s>>>(lam, N, q->norms, q->norms + q->bmax);
@@ -678,6 +692,8 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
       }
     }
   }
+  k_divide_results<<<B, 32, 0, s>>>(q->results, out_stride, grad ? 1 + 2 * p : 1, phi_norm);
+  ++launches;
   *n_launches = launches;
   return cudaGetLastError();
 }
@@ -782,7 +798,7 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
             cudaMalloc(&q->tables, q->table_bytes) == cudaSuccess &&
             cudaMalloc(&q->partials, sizeof(double) * (size_t)ps * batch_max) == cudaSuccess &&
             cudaMalloc(&q->results, sizeof(double) * (size_t)batch_max * (1 + 2 * kMaxP)) == cudaSuccess &&
-            cudaMalloc(&q->norms, sizeof(double) * 2 * (size_t)batch_max) == cudaSuccess &&
+            cudaMalloc(&q->norms, sizeof(double) * 3 * (size_t)batch_max) == cudaSuccess &&
             cudaMalloc(&q->flag, sizeof(unsigned)) == cudaSuccess &&
             cudaMallocHost(&q->host_params, q->rx_bytes + q->table_bytes) == cudaSuccess &&
             cudaMallocHost(&q->host_results, sizeof(double) * ((size_t)batch_max * (1 + 2 * kMaxP) + 1)) == cudaSuccess;

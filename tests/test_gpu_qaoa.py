@@ -4,9 +4,10 @@ oracle (plain forward, stored-state adjoint) and central finite differences.
 Tolerances:
 * complex128 (double-float emulation): energy 1e-11, gradient 1e-9 absolute
   (a gradient sums ~2^n * (n + |E|) products per parameter).
-* complex64: the stated bound of the benchmark spec, energy error <= 1e-5
-  absolute against the FP64 oracle on the original parameters; gradients
-  within 1e-4.
+* complex64: energies are Rayleigh quotients of the computed state, which
+  removes the norm drift of FP32-rounded gate coefficients; the energy error
+  against the FP64 oracle on the original parameters is held to 2e-6
+  (target 1e-5), gradients to 1e-4.
 """
 import numpy as np
 import pytest
@@ -50,7 +51,7 @@ def test_qaoa_c64_error_bound(gpu_lib, n, p, batch):
     eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=batch)
     E, dg, db = eng.run(gm, bt)
     Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
-    assert np.max(np.abs(E - Eo)) <= 1e-5
+    assert np.max(np.abs(E - Eo)) <= 2e-6
     assert np.max(np.abs(dg - dgo)) <= 1e-4
     assert np.max(np.abs(db - dbo)) <= 1e-4
     eng.close()
@@ -118,7 +119,7 @@ def test_qaoa_renormalisation_keeps_results(gpu_lib):
     eng.set_options(renorm_every=2)
     E1, dg1, db1 = eng.run(gm, bt)
     Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
-    assert np.max(np.abs(E1 - Eo)) <= 1e-5
+    assert np.max(np.abs(E1 - Eo)) <= 2e-6
     assert np.max(np.abs(dg1 - dgo)) <= 1e-4
     assert np.max(np.abs(db1 - dbo)) <= 1e-4
 
