@@ -208,6 +208,42 @@ iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, con
  * pass, or after the uncompute when a gradient was computed) to host memory. */
 iqs_status iqs_qaoa_download_state(iqs_qaoa* q, int index, void* host, size_t bytes);
 
+/* ------------------------------------------------------------ pool of noisy trajectories */
+
+/* Section 2 "Pool of multiple states" and the pool-of-states appendix: a pool
+ * of states runs the same circuit, each with its own stochastic noise
+ * rotations, and a probability is averaged incoherently over the pool (sum
+ * over the pool's states divided by their number).
+ * Circuit family ("brick"): layer l applies U[l][q] to every qubit q, then
+ * CNOT(i, i+1) for i = o, o + 2, ... (o = l mod 2, i + 1 < n).  With noise,
+ * each gate is followed, on every qubit it touched (the target of a one-qubit
+ * gate; control then target of a CNOT), by RX(tx) then RZ(tz),
+ * R(t) = exp(-i t sigma / 2), with angles that differ per trajectory. */
+typedef struct iqs_pool iqs_pool;
+
+/* Workspace for up to ``batch_max`` trajectories of n qubits (2..24) and
+ * circuits of up to ``depth_max`` layers, on the current device. */
+iqs_status iqs_pool_create(int n, int dtype, int batch_max, int depth_max, void* stream, iqs_pool** out);
+iqs_status iqs_pool_destroy(iqs_pool* p);
+
+/* Number of noise rotations (angle pairs) per trajectory of a depth-layer
+ * brick circuit on n qubits: sum over layers of n + 2 x (CNOTs in the layer). */
+int iqs_pool_noise_count(int n, int depth);
+
+/* Run ``batch`` trajectories from |0...0>.  ``unitaries``: host doubles
+ * [depth][n][8] (each U row-major as (re, im) pairs).  ``angles``: host
+ * doubles [batch][iqs_pool_noise_count(n, depth)][2] = (tx, tz) in the order
+ * the rotations occur (layer by layer: the one-qubit gates q = 0..n-1, then
+ * each CNOT's control and target), or NULL for the noiseless circuit.
+ * Outputs (host): probs[batch][n] = P(q = 1) of each trajectory (divided by
+ * the computed state's squared norm, FP64) or NULL; mean[n] = pool average.
+ * Synchronous. */
+iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* unitaries, const double* angles,
+                              double* probs, double* mean);
+
+/* Copy trajectory ``index``'s final state to host memory. */
+iqs_status iqs_pool_download_state(iqs_pool* p, int index, void* host, size_t bytes);
+
 /* ------------------------------------------------------------ allocation-free variant */
 
 /* The paper has no counterpart to this call: it is an interface for callers

@@ -35,6 +35,7 @@
 #include "df64.cuh"
 #include "internal.h"
 #include "qaoa_ops.cuh"
+#include "tile.cuh"
 
 namespace iqs {
 namespace {
@@ -93,36 +94,6 @@ struct T128 {
   __device__ static W mul(const PH& t, const W& x) { return qops::cmul(t, x); }
 };
 
-// ---------------------------------------------------------------- tile geometry
-// Tile bits: [0, c) and [s, s + m), s >= c.  Local index l = (h << c) | low.
-struct Geo {
-  int c, s, m;
-};
-
-__device__ __forceinline__ uint64_t tile_x(const Geo& g, uint64_t t, unsigned l) {
-  const uint64_t low = l & ((1u << g.c) - 1u);
-  const uint64_t h = l >> g.c;
-  const int mid = g.s - g.c;
-  const uint64_t tlo = t & ((1ull << mid) - 1ull);
-  const uint64_t thi = t >> mid;
-  return (thi << (g.s + g.m)) | (h << g.s) | (tlo << g.c) | low;
-}
-
-// ---------------------------------------------------------------- block reduction of one FP64 value
-__device__ __forceinline__ void block_partial(double v, double* out) {
-  __shared__ double red[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    *out = s;
-  }
-  __syncthreads();
-}
-
 // ---------------------------------------------------------------- kernels
 template <class V>
 __global__ void k_fill_uniform(V* a, uint64_t total, V v) {
@@ -134,14 +105,6 @@ template <class X>
 __global__ void k_cut_table(uint8_t* cut, uint64_t N, EdgesU8 E) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
     cut[i] = (uint8_t)cut_count((X)i, E);
-}
-
-// Shared-memory index of tile element l: XOR-swizzled within 128-byte rows so
-// that a warp reading a fixed offset of 32 consecutive register blocks (rows
-// of stride 2^kSwzBits elements) hits distinct banks.
-template <class TR>
-__device__ __forceinline__ unsigned swz(unsigned l) {
-  return l ^ ((l >> TR::kSwzBits) & ((1u << TR::kSwzBits) - 1u));
 }
 
 // Mixer pass: RX on the qubits [s, s+m) of every tile (or its inverse, with the

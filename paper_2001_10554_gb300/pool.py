@@ -1,0 +1,81 @@
+"""Pool of noisy trajectories of a brick circuit (C ABI ``iqs_pool_*``)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import call, lib
+from .register import _dtype_code, _stream_handle
+
+_dp = C.POINTER(C.c_double)
+
+
+def noise_count(n: int, depth: int) -> int:
+    """Noise rotations per trajectory of a depth-layer brick circuit on n qubits."""
+    return int(lib.iqs_pool_noise_count(int(n), int(depth)))
+
+
+class Pool:
+    """Workspace for ``batch_max`` trajectories of ``n`` qubits, circuits of up to ``depth_max`` layers.
+
+    ``run_brick(unitaries, angles)`` takes the layer unitaries as a complex
+    array (depth, n, 2, 2) and the noise angles as (batch, noise_count, 2) (or
+    None for the noiseless circuit) and returns (probs[batch, n], mean[n]).
+    """
+
+    def __init__(self, n: int, dtype="complex64", batch_max: int = 1, depth_max: int = 128, stream=None):
+        self.n, self.batch_max, self.depth_max = int(n), int(batch_max), int(depth_max)
+        self.dtype_code = _dtype_code(dtype)
+        h = C.c_void_p()
+        call("iqs_pool_create", self.n, self.dtype_code, self.batch_max, self.depth_max, _stream_handle(stream),
+             C.byref(h))
+        self._h = h
+
+    def run_brick(self, unitaries, angles=None):
+        U = np.asarray(unitaries, dtype=np.complex128).reshape(-1, self.n, 2, 2)
+        depth = U.shape[0]
+        flat = np.ascontiguousarray(U.reshape(depth, self.n, 4).view(np.float64).reshape(depth, self.n, 8))
+        if angles is None:
+            batch, ap = 1, None
+        else:
+            a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64))
+            batch = a.shape[0]
+            if a.shape[1:] != (noise_count(self.n, depth), 2):
+                raise ValueError(f"angles must have shape (batch, {noise_count(self.n, depth)}, 2)")
+            ap = a.ctypes.data_as(_dp)
+        probs = np.empty((batch, self.n))
+        mean = np.empty(self.n)
+        call("iqs_pool_run_brick", self._h, batch, depth, flat.ctypes.data_as(_dp), ap,
+             probs.ctypes.data_as(_dp), mean.ctypes.data_as(_dp))
+        return probs, mean
+
+    def state(self, index: int = 0) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.complex128 if self.dtype_code == _lib.IQS_C128 else np.complex64)
+        call("iqs_pool_download_state", self._h, int(index), C.c_void_p(out.ctypes.data), C.c_size_t(out.nbytes))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.iqs_pool_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def brick_unitaries(ops, n: int):
+    """(depth, n, 2, 2) unitaries from a layered op list (("1q", q, U) / ("cx", c, t))."""
+    layers = []
+    cur = None
+    for op in ops:
+        if op[0] == "1q":
+            if op[1] == 0:
+                cur = [None] * n
+                layers.append(cur)
+            cur[op[1]] = op[2]
+    return np.array(layers, dtype=np.complex128)

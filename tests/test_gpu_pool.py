@@ -1,0 +1,96 @@
+"""Pool engine (iqs_pool_*): noiseless and noisy brick circuits against the
+FP64 oracle, trajectory by trajectory (same angles), and the pool average.
+
+Tolerances: complex128 1e-12 on amplitudes and probabilities; complex64 the
+per-gate FP32 bound 8 * 2^-24 times the number of fused gates a qubit sees
+(two per layer: the fused one-qubit gate and the CNOT, which is exact).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ensemble as oe
+from oracle import statevector as sv
+from paper_2001_10554_gb300.pool import brick_unitaries, noise_count
+
+pytestmark = pytest.mark.gpu
+
+
+def c64_tol(depth):
+    return 8 * 2.0 ** -24 * (depth + 1) * 2
+
+
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+@pytest.mark.parametrize("n,depth", [(2, 3), (5, 4), (12, 20), (13, 6), (16, 5)])
+def test_noiseless_brick_matches_oracle(gpu_lib, dtype, n, depth):
+    ops = W.random_circuit_layers(n, depth, seed=40 + n)
+    U = brick_unitaries(ops, n)
+    pool = gpu_lib.Pool(n, dtype, batch_max=1, depth_max=depth)
+    probs, mean = pool.run_brick(U)
+    ref = oe.run_ops(n, ops)
+    got = pool.state(0).astype(np.complex128)
+    tol = 1e-12 if dtype == "complex128" else c64_tol(depth)
+    assert np.max(np.abs(got - ref)) <= tol
+    pref = oe.all_probabilities(ref)
+    assert np.max(np.abs(probs[0] - pref)) <= (1e-12 if dtype == "complex128" else 4 * tol)
+    np.testing.assert_array_equal(mean, probs[0])
+    pool.close()
+
+
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+@pytest.mark.parametrize("n,depth,batch,sigma", [(4, 3, 3, 0.3), (8, 5, 4, 0.02), (13, 4, 2, 0.2), (16, 3, 3, 0.02)])
+def test_noisy_trajectories_match_oracle(gpu_lib, dtype, n, depth, batch, sigma):
+    g = W.rng(70 + n)
+    ops = W.random_circuit_layers(n, depth, seed=50 + n)
+    U = brick_unitaries(ops, n)
+    k = noise_count(n, depth)
+    assert k == sum(1 if op[0] == "1q" else 2 for op in ops)
+    angles = g.normal(0.0, sigma, size=(batch, k, 2))
+    pool = gpu_lib.Pool(n, dtype, batch_max=batch, depth_max=depth)
+    probs, mean = pool.run_brick(U, angles)
+    tol = 1e-12 if dtype == "complex128" else c64_tol(depth)
+    per = []
+    for b in range(batch):
+        ref = oe.run_ops(n, oe.noisy_trajectory_ops(ops, angles[b]))
+        got = pool.state(b).astype(np.complex128)
+        assert np.max(np.abs(got - ref)) <= tol, b
+        pref = oe.all_probabilities(ref)
+        assert np.max(np.abs(probs[b] - pref)) <= (1e-12 if dtype == "complex128" else 4 * tol)
+        per.append(pref)
+    np.testing.assert_allclose(mean, oe.pool_average(per), rtol=0, atol=1e-12 if dtype == "complex128" else 4 * tol)
+    pool.close()
+
+
+def test_uneven_depth_circuits_share_a_workspace(gpu_lib):
+    """Circuits of different depths run one after another in one pool."""
+    n = 10
+    pool = gpu_lib.Pool(n, "complex128", batch_max=3, depth_max=9)
+    for depth, seed in ((4, 1), (9, 2), (6, 3)):
+        ops = W.random_circuit_layers(n, depth, seed=seed)
+        angles = W.rng(seed).normal(0, 0.1, size=(3, noise_count(n, depth), 2))
+        probs, mean = pool.run_brick(brick_unitaries(ops, n), angles)
+        ref = oe.ensemble_probabilities(n, ops, angles)
+        np.testing.assert_allclose(mean, ref, rtol=0, atol=1e-12)
+
+
+def test_noise_ensemble_workload_shape(gpu_lib):
+    """The seeded ensemble generator's circuits and angles run unchanged (2 trajectories checked)."""
+    ens = W.noise_ensemble(n=8, circuits=2, trajectories=3, depth_lo=3, depth_hi=6, seed=11)
+    for c in ens:
+        U = brick_unitaries(c["ops"], 8)
+        pool = gpu_lib.Pool(8, "complex128", batch_max=3, depth_max=c["depth"])
+        probs, mean = pool.run_brick(U, c["angles"])
+        ref = oe.ensemble_probabilities(8, c["ops"], c["angles"])
+        np.testing.assert_allclose(mean, ref, rtol=0, atol=1e-12)
+        pool.close()
+
+
+def test_pool_rejects_bad_arguments(gpu_lib):
+    from paper_2001_10554_gb300 import IQSError
+    with pytest.raises(IQSError):
+        gpu_lib.Pool(25, "complex64")
+    pool = gpu_lib.Pool(6, "complex64", batch_max=2, depth_max=3)
+    with pytest.raises(IQSError):
+        pool.run_brick(np.tile(np.eye(2), (4, 6, 1, 1)))           # depth 4 > depth_max 3
+    with pytest.raises(ValueError):
+        pool.run_brick(np.tile(np.eye(2), (2, 6, 1, 1)), np.zeros((1, 3, 2)))
