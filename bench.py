@@ -313,6 +313,47 @@ def qaoa_section(iqs, torch):
     return out
 
 
+def ensemble_section(iqs, torch):
+    """Noise ensemble: 8 circuits of 16 qubits, depth uniform in [40, 120],
+    one-qubit Haar layers + CNOT brick, X/Z noise rotations N(0, 0.02^2) after
+    every gate, 500 trajectories per circuit; ensemble-averaged P(1) per qubit.
+    complex64 and complex128, plus the FP64 oracle on a bounded sample."""
+    import workloads as W
+    from paper_2001_10554_gb300.pool import brick_unitaries
+    n, circuits, traj = 16, 8, 500
+    ens = W.noise_ensemble(n=n, circuits=circuits, trajectories=traj, seed=4242)
+    depths = [c["depth"] for c in ens]
+    Us = [brick_unitaries(c["ops"], n) for c in ens]
+    out = {"workload": f"{circuits} circuits x {traj} trajectories, {n} qubits, depth {min(depths)}..{max(depths)} "
+                       f"(uniform 40..120), noise RX.RZ N(0, 0.02^2) after every gate",
+           "depths": depths}
+    means = {}
+    for dtype in ("complex64", "complex128"):
+        pool = iqs.Pool(n, dtype, batch_max=traj, depth_max=max(depths))
+        pool.run_brick(Us[0][:2], ens[0]["angles"][:, :iqs.pool.noise_count(n, 2)])  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = [pool.run_brick(Us[i], ens[i]["angles"])[1] for i in range(circuits)]
+        dt = time.perf_counter() - t0
+        pool.close()
+        torch.cuda.empty_cache()
+        means[dtype] = np.array(m)
+        layers = sum(depths) * traj
+        out[dtype] = {"trajectories_per_s": round(circuits * traj / dt, 1), "seconds": round(dt, 3),
+                      "layer_updates_per_s": round(layers / dt, 1)}
+    out["mean_p1_diff_c64_vs_c128_max"] = float(np.max(np.abs(means["complex64"] - means["complex128"])))
+    # FP64 oracle on a bounded sample: 2 trajectories of the first circuit
+    from oracle import ensemble as oe
+    t0 = time.perf_counter()
+    k = 2
+    for t in range(k):
+        oe.all_probabilities(oe.run_ops(n, oe.noisy_trajectory_ops(ens[0]["ops"], ens[0]["angles"][t])))
+    dt = time.perf_counter() - t0
+    out["cpu_oracle"] = {"trajectories_per_s": round(k / dt, 4), "cores": 1,
+                         "sample": f"{k} trajectories of circuit 0 (depth {depths[0]}), numpy FP64"}
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main(argv=None):
     args = parse_args(argv)
@@ -447,6 +488,7 @@ def main(argv=None):
     if not args.no_extra:
         extra["c64_32q"] = sweep_c64(iqs, torch, dev, 32, steps=3, warmup=2)
         extra["qaoa"] = qaoa_section(iqs, torch)
+        extra["noise_ensemble"] = ensemble_section(iqs, torch)
 
     if rank == 0:
         line = {
