@@ -178,6 +178,23 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": float(max(power))}
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest ``value`` over all ranks of the default process group
+    (the step time a multi-rank job reports is the slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, bytes_per_rank_step: float, steps: int, elapsed_ms: float) -> float:
+    """Whole-job GB/s: every replica's algorithmic bytes over the slowest rank's time."""
+    return world * bytes_per_rank_step * steps / (elapsed_ms * 1e-3) / 1e9
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -438,15 +455,11 @@ def main(argv=None):
     launches = _lib.kernel_launches() - launches0
     clk = clocks.stop() if clocks else None
     reg.synchronize()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
 
     sb = step_bytes(n)
     bytes_step = sum(sb.values())
-    value = world * bytes_step * args.steps / (elapsed_ms * 1e-3) / 1e9
+    value = job_throughput(world, bytes_step, args.steps, elapsed_ms)
     g1 = [a.elapsed_time(b) for a, b in ev_pairs]
     avg_1q_ms = float(np.mean(g1))
     per_q = np.array(g1).reshape(args.steps, n).mean(axis=0)

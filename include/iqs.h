@@ -278,6 +278,15 @@ const char* iqs_version(void);
  * registers, all threads); for launch accounting in benchmarks. */
 uint64_t iqs_kernel_launches(void);
 
+/* Host-side fault injection, for testing error paths without any GPU fault.
+ * kind 1: the (after + 1)-th next device allocation of iqs_create, iqs_wrap,
+ * iqs_qaoa_create or iqs_pool_create fails with IQS_ENOMEM; kind 2: the
+ * (after + 1)-th next kernel-launching call fails with IQS_ECUDA before
+ * anything is queued (the state is untouched); kind 0 disarms.  One fault is
+ * armed at a time and fires once.  The environment variable IQS_FAULT =
+ * "alloc[:after]" or "launch[:after]" arms the same when the library loads. */
+iqs_status iqs_inject_fault(int kind, int after);
+
 #ifdef __cplusplus
 }
 #endif

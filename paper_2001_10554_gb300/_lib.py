@@ -60,6 +60,7 @@ SIGNATURES = {
     "iqs_last_error": ([], C.c_char_p),
     "iqs_version": ([], C.c_char_p),
     "iqs_kernel_launches": ([], C.c_uint64),
+    "iqs_inject_fault": ([C.c_int, C.c_int], C.c_int),
     "iqs_qaoa_create": ([C.c_int, C.c_int, C.c_int, C.c_int, _i32p, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "iqs_qaoa_destroy": ([C.c_void_p], C.c_int),
     "iqs_qaoa_set_options": ([C.c_void_p, C.c_int, C.c_int], C.c_int),

@@ -8,12 +8,31 @@
 #include <new>
 
 #include <atomic>
+#include <cstdlib>
 
 #include "internal.h"
 
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
+
+// Host-side fault injection (iqs_inject_fault / IQS_FAULT): kind 1 = allocation,
+// 2 = kernel launch; the fault fires on the (countdown + 1)-th event of that kind.
+std::atomic<int> g_fault_kind{0};
+std::atomic<int> g_fault_countdown{0};
+
+struct FaultEnv {
+  FaultEnv() {
+    const char* v = std::getenv("IQS_FAULT");
+    if (v == nullptr) return;
+    int kind = 0;
+    if (std::strncmp(v, "alloc", 5) == 0) kind = 1;
+    else if (std::strncmp(v, "launch", 6) == 0) kind = 2;
+    const char* colon = std::strchr(v, ':');
+    g_fault_countdown = colon ? std::atoi(colon + 1) : 0;
+    g_fault_kind = kind;
+  }
+} g_fault_env;
 
 thread_local char g_err[512] = "";
 
@@ -33,6 +52,14 @@ iqs_status cuda_fail(cudaError_t e, const char* what) {
 #define CHECK_REG(r)                                                  \
   do {                                                                \
     if ((r) == nullptr) return fail(IQS_EINVAL, "register is NULL");  \
+  } while (0)
+
+// A kernel-launching call: an armed launch fault fails it before anything is queued.
+#define LAUNCH_TRY(expr, what)                                                              \
+  do {                                                                                      \
+    if (iqs::fault_now(2)) return fail(IQS_ECUDA, "%s: injected launch failure", what);    \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);                                      \
   } while (0)
 
 #define CUDA_TRY(expr, what)                         \
@@ -88,6 +115,10 @@ iqs_status new_reg(int n, int dtype, void* ptr, bool owns, void* stream, iqs_reg
   r->dtype = dtype;
   r->stream = (cudaStream_t)stream;
   cudaGetDevice(&r->device);
+  if (iqs::fault_now(1)) {
+    delete r;
+    return fail(IQS_ENOMEM, "injected allocation failure");
+  }
   if (owns) {
     const size_t bytes = (size_t)iqs::num_amps(r) * iqs::amp_bytes(r);
     if (cudaMalloc(&r->data, bytes) != cudaSuccess) {
@@ -161,6 +192,14 @@ iqs_status check_edges(const iqs_reg* r, int n_edges, const int32_t* edges) {
 
 void iqs::note_launches(int k) { g_launches.fetch_add((uint64_t)k); }
 
+bool iqs::fault_now(int kind) {
+  if (g_fault_kind.load() != kind) return false;
+  if (g_fault_countdown.fetch_sub(1) > 0) return false;
+  g_fault_kind = 0;
+  g_fault_countdown = 0;
+  return true;
+}
+
 iqs_status iqs::report(iqs_status s, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -220,13 +259,13 @@ iqs_status iqs_synchronize(iqs_reg* reg) {
 iqs_status iqs_init_basis(iqs_reg* reg, uint64_t index) {
   CHECK_REG(reg);
   if (index >= iqs::num_amps(reg)) return fail(IQS_EINVAL, "basis index out of range");
-  CUDA_TRY(iqs::launch_init_basis(reg, index), "init_basis");
+  LAUNCH_TRY(iqs::launch_init_basis(reg, index), "init_basis");
   return IQS_OK;
 }
 
 iqs_status iqs_init_uniform(iqs_reg* reg) {
   CHECK_REG(reg);
-  CUDA_TRY(iqs::launch_init_uniform(reg), "init_uniform");
+  LAUNCH_TRY(iqs::launch_init_uniform(reg), "init_uniform");
   return IQS_OK;
 }
 
@@ -252,7 +291,7 @@ iqs_status iqs_apply_1q(iqs_reg* reg, int q, const double U[8]) {
   CHECK_REG(reg);
   if (U == nullptr) return fail(IQS_EINVAL, "U is NULL");
   if (q < 0 || q >= reg->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, reg->n);
-  CUDA_TRY(iqs::launch_1q(reg, q, to_mat(U)), "apply_1q");
+  LAUNCH_TRY(iqs::launch_1q(reg, q, to_mat(U)), "apply_1q");
   return IQS_OK;
 }
 
@@ -262,7 +301,7 @@ iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]) {
   if (c < 0 || c >= reg->n || t < 0 || t >= reg->n) return fail(IQS_EINVAL, "control/target outside [0, %d)", reg->n);
   if (c == t) return fail(IQS_EINVAL, "control and target are the same qubit (%d)", c);
   if (reg->n < 2) return fail(IQS_EINVAL, "a controlled gate needs 2 qubits");
-  CUDA_TRY(iqs::launch_c1q(reg, c, t, to_mat(U)), "apply_c1q");
+  LAUNCH_TRY(iqs::launch_c1q(reg, c, t, to_mat(U)), "apply_c1q");
   return IQS_OK;
 }
 
@@ -274,14 +313,14 @@ iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges, c
   if (weights)
     for (int e = 0; e < n_edges; ++e)
       if (!std::isfinite(weights[e])) return fail(IQS_EINVAL, "weight %d is not finite", e);
-  CUDA_TRY(iqs::launch_zz_phase(reg, n_edges, edges, weights, gamma), "apply_zz_phase");
+  LAUNCH_TRY(iqs::launch_zz_phase(reg, n_edges, edges, weights, gamma), "apply_zz_phase");
   return IQS_OK;
 }
 
 iqs_status iqs_norm2(iqs_reg* reg, double* out) {
   CHECK_REG(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
-  CUDA_TRY(iqs::launch_norm2(reg), "norm2");
+  LAUNCH_TRY(iqs::launch_norm2(reg), "norm2");
   iqs_status s = read_results(reg, 1, out);
   return s != IQS_OK ? s : check_flag(reg);
 }
@@ -290,7 +329,7 @@ iqs_status iqs_probability(iqs_reg* reg, int q, double* out) {
   CHECK_REG(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
   if (q < 0 || q >= reg->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, reg->n);
-  CUDA_TRY(iqs::launch_probability(reg, q), "probability");
+  LAUNCH_TRY(iqs::launch_probability(reg, q), "probability");
   iqs_status s = read_results(reg, 1, out);
   return s != IQS_OK ? s : check_flag(reg);
 }
@@ -298,7 +337,7 @@ iqs_status iqs_probability(iqs_reg* reg, int q, double* out) {
 iqs_status iqs_probabilities(iqs_reg* reg, double* out) {
   CHECK_REG(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
-  CUDA_TRY(iqs::launch_probabilities(reg), "probabilities");
+  LAUNCH_TRY(iqs::launch_probabilities(reg), "probabilities");
   iqs_status s = read_results(reg, reg->n, out);
   return s != IQS_OK ? s : check_flag(reg);
 }
@@ -308,7 +347,7 @@ iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, d
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
   const uint64_t all = reg->n >= 64 ? ~0ull : ((1ull << reg->n) - 1ull);
   if ((xmask | zmask) & ~all) return fail(IQS_EINVAL, "mask bits at or above n = %d", reg->n);
-  CUDA_TRY(iqs::launch_expectation(reg, xmask, zmask), "expectation");
+  LAUNCH_TRY(iqs::launch_expectation(reg, xmask, zmask), "expectation");
   double v;
   iqs_status s = read_results(reg, 1, &v);
   if (s != IQS_OK) return s;
@@ -346,7 +385,7 @@ iqs_status iqs_renormalize(iqs_reg* reg) {
   iqs_status s = iqs_norm2(reg, &nn);
   if (s != IQS_OK) return s;
   if (!(nn > 0.0) || !std::isfinite(nn)) return fail(IQS_EINVAL, "cannot renormalise a state of squared norm %g", nn);
-  CUDA_TRY(iqs::launch_scale(reg, 1.0 / std::sqrt(nn)), "renormalize");
+  LAUNCH_TRY(iqs::launch_scale(reg, 1.0 / std::sqrt(nn)), "renormalize");
   return IQS_OK;
 }
 
@@ -358,7 +397,7 @@ iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges, co
   double total = 0.0;
   for (int base = 0; base < n_edges; base += 255) {
     const int m = n_edges - base < 255 ? n_edges - base : 255;
-    CUDA_TRY(iqs::launch_energy(reg, m, edges + 2 * base, weights ? weights + base : nullptr), "energy");
+    LAUNCH_TRY(iqs::launch_energy(reg, m, edges + 2 * base, weights ? weights + base : nullptr), "energy");
     double v;
     if ((s = read_results(reg, 1, &v)) != IQS_OK) return s;
     total += v;
@@ -372,5 +411,12 @@ const char* iqs_last_error(void) { return g_err; }
 const char* iqs_version(void) { return "iqs-gb300 0.1.0 (sm_103a)"; }
 
 uint64_t iqs_kernel_launches(void) { return g_launches.load(); }
+
+iqs_status iqs_inject_fault(int kind, int after) {
+  if (kind < 0 || kind > 2 || after < 0) return fail(IQS_EINVAL, "fault kind must be 0, 1 or 2 and after >= 0");
+  g_fault_countdown = after;
+  g_fault_kind = kind;
+  return IQS_OK;
+}
 
 }  // extern "C"

@@ -82,5 +82,7 @@ cudaError_t launch_probabilities_raw(const void* data, int n, int dtype, cudaStr
 
 // ---- abi.cu: record a failure message for iqs_last_error() and return ``s``.
 iqs_status report(iqs_status s, const char* fmt, ...);
+// True (once) when an injected fault of ``kind`` (1 allocation, 2 launch) fires.
+bool fault_now(int kind);
 
 }  // namespace iqs

@@ -461,6 +461,7 @@ iqs_status iqs_pool_create(int n, int dtype, int batch_max, int depth_max, void*
   if (dtype != IQS_C64 && dtype != IQS_C128) return report(IQS_EINVAL, "dtype must be IQS_C64 or IQS_C128");
   if (batch_max < 1 || batch_max > 65535) return report(IQS_EINVAL, "batch_max %d outside [1, 65535]", batch_max);
   if (depth_max < 1 || depth_max > 100000) return report(IQS_EINVAL, "depth_max %d outside [1, 100000]", depth_max);
+  if (fault_now(1)) return report(IQS_ENOMEM, "injected allocation failure");
   iqs_pool* p = new (std::nothrow) iqs_pool();
   if (p == nullptr) return report(IQS_ENOMEM, "host allocation failed");
   p->n = n;
@@ -520,6 +521,7 @@ iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* u
   if (batch < 1 || batch > p->bmax) return report(IQS_EINVAL, "batch %d outside [1, %d]", batch, p->bmax);
   if (depth < 1 || depth > p->depth_max) return report(IQS_EINVAL, "depth %d outside [1, %d]", depth, p->depth_max);
   if (unitaries == nullptr || mean == nullptr) return report(IQS_EINVAL, "unitaries and mean must not be NULL");
+  if (fault_now(2)) return report(IQS_ECUDA, "iqs_pool_run_brick: injected launch failure");
   const int nn = n_noise_ops(p->n, depth);
   std::vector<int> base(depth);
   for (int l = 0, k = 0; l < depth; ++l) {

@@ -733,6 +733,7 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
     if (u < 0 || u >= n || v < 0 || v >= n || u == v)
       return report(IQS_EINVAL, "edge %d = (%d, %d) invalid for %d qubits", e, u, v, n);
   }
+  if (fault_now(1)) return report(IQS_ENOMEM, "injected allocation failure");
   iqs_qaoa* q = new (std::nothrow) iqs_qaoa();
   if (q == nullptr) return report(IQS_ENOMEM, "host allocation failed");
   q->n = n;
@@ -821,6 +822,7 @@ iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, con
   if (grad && (!grad_gammas || !grad_betas)) return report(IQS_EINVAL, "give both gradient outputs or neither");
   for (int i = 0; i < batch * p; ++i)
     if (!std::isfinite(gammas[i]) || !std::isfinite(betas[i])) return report(IQS_EINVAL, "non-finite parameter");
+  if (fault_now(2)) return report(IQS_ECUDA, "iqs_qaoa_run: injected launch failure");
   if (q->dtype == IQS_C128) fill_params_c128(q, batch, p, gammas, betas);
   else fill_params_c64(q, batch, p, gammas, betas);
   cudaStream_t s = q->stream;
