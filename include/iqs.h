@@ -244,6 +244,36 @@ iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* u
 /* Copy trajectory ``index``'s final state to host memory. */
 iqs_status iqs_pool_download_state(iqs_pool* p, int index, void* host, size_t bytes);
 
+/* A pool of brick circuits of uneven qubit counts, depths and trajectory
+ * counts, run in ONE persistent kernel launch (Section 2 "Pool of multiple
+ * states"; same circuit family and noise model as iqs_pool_run_brick). */
+typedef struct iqs_circuit_desc {
+  int n;                    /* qubits, 2..24 */
+  int depth;                /* brick layers, >= 1 */
+  int trajectories;         /* pool states of this circuit (1 when angles is NULL) */
+  const double* unitaries;  /* host [depth][n][8] */
+  const double* angles;     /* host [trajectories][iqs_pool_noise_count(n, depth)][2], or NULL */
+} iqs_circuit_desc;
+
+typedef struct iqs_pool_many iqs_pool_many;
+
+/* Workspace; device memory is allocated (and kept, growing) by the runs. */
+iqs_status iqs_pool_many_create(int dtype, void* stream, iqs_pool_many** out);
+iqs_status iqs_pool_many_destroy(iqs_pool_many* w);
+
+/* Every wait inside the persistent kernel gives up after ``seconds`` (default
+ * 2): the kernel then stops all its blocks and the run returns IQS_ETIMEOUT
+ * with the GPU context intact.  ``debug_never`` != 0 is a test mode in which
+ * the first job's first wait can never be satisfied, so the timeout path runs. */
+iqs_status iqs_pool_many_set_wait_limit(iqs_pool_many* w, double seconds, int debug_never);
+
+/* Run all circuits (at most 8 distinct qubit counts per call) from |0...0>.
+ * Outputs (host): probs = per-trajectory P(q = 1) (divided by the state's FP64
+ * squared norm), concatenated circuit by circuit as [trajectories][n], or NULL;
+ * means = per-circuit pool averages, concatenated as [n].  Synchronous. */
+iqs_status iqs_pool_many_run(iqs_pool_many* w, int n_circuits, const iqs_circuit_desc* circuits, double* probs,
+                             double* means);
+
 /* ------------------------------------------------------------ allocation-free variant */
 
 /* The paper has no counterpart to this call: it is an interface for callers

@@ -68,6 +68,69 @@ class Pool:
             pass
 
 
+class _Desc(C.Structure):
+    _fields_ = [("n", C.c_int), ("depth", C.c_int), ("trajectories", C.c_int),
+                ("unitaries", C.c_void_p), ("angles", C.c_void_p)]
+
+
+class PoolMany:
+    """Brick circuits of uneven qubit counts, depths and trajectory counts in
+    one persistent kernel launch (``iqs_pool_many_*``).
+
+    ``run([(unitaries, angles_or_None), ...])`` returns, per circuit,
+    (probs[trajectories, n], mean[n]).
+    """
+
+    def __init__(self, dtype="complex64", stream=None):
+        self.dtype_code = _dtype_code(dtype)
+        h = C.c_void_p()
+        call("iqs_pool_many_create", self.dtype_code, _stream_handle(stream), C.byref(h))
+        self._h = h
+
+    def set_wait_limit(self, seconds: float, debug_never: bool = False) -> None:
+        call("iqs_pool_many_set_wait_limit", self._h, C.c_double(seconds), int(bool(debug_never)))
+
+    def run(self, circuits):
+        keep, descs, shapes = [], [], []
+        for U, ang in circuits:
+            U = np.asarray(U, dtype=np.complex128)
+            depth, n = U.shape[0], U.shape[1]
+            flat = np.ascontiguousarray(U.reshape(depth, n, 4).view(np.float64).reshape(depth, n, 8))
+            keep.append(flat)
+            if ang is None:
+                traj, ap = 1, None
+            else:
+                a = np.ascontiguousarray(np.asarray(ang, dtype=np.float64))
+                if a.shape[1:] != (noise_count(n, depth), 2):
+                    raise ValueError(f"angles must have shape (trajectories, {noise_count(n, depth)}, 2)")
+                keep.append(a)
+                traj, ap = a.shape[0], a.ctypes.data
+            descs.append(_Desc(n, depth, traj, flat.ctypes.data, ap))
+            shapes.append((traj, n))
+        arr = (_Desc * len(descs))(*descs)
+        probs = np.empty(sum(t * n for t, n in shapes))
+        means = np.empty(sum(n for _, n in shapes))
+        call("iqs_pool_many_run", self._h, len(descs), C.cast(arr, C.c_void_p), probs.ctypes.data_as(_dp),
+             means.ctypes.data_as(_dp))
+        out, po, mo = [], 0, 0
+        for t, n in shapes:
+            out.append((probs[po:po + t * n].reshape(t, n), means[mo:mo + n]))
+            po += t * n
+            mo += n
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.iqs_pool_many_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def brick_unitaries(ops, n: int):
     """(depth, n, 2, 2) unitaries from a layered op list (("1q", q, U) / ("cx", c, t))."""
     layers = []

@@ -94,3 +94,66 @@ def test_pool_rejects_bad_arguments(gpu_lib):
         pool.run_brick(np.tile(np.eye(2), (4, 6, 1, 1)))           # depth 4 > depth_max 3
     with pytest.raises(ValueError):
         pool.run_brick(np.tile(np.eye(2), (2, 6, 1, 1)), np.zeros((1, 3, 2)))
+
+
+# ---------------------------------------------------------------- one persistent launch
+def _mixed_workload():
+    specs = [(5, 3, 4, 0.3), (9, 7, 1, None), (13, 2, 3, 0.1), (16, 5, 2, 0.02), (9, 4, 3, 0.2)]
+    out = []
+    for k, (n, depth, traj, sigma) in enumerate(specs):
+        ops = W.random_circuit_layers(n, depth, seed=900 + k)
+        ang = None if sigma is None else W.rng(950 + k).normal(0, sigma, size=(traj, noise_count(n, depth), 2))
+        out.append((n, ops, ang))
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+def test_persistent_mixed_pool_matches_oracle(gpu_lib, dtype):
+    work = _mixed_workload()
+    pm = gpu_lib.PoolMany(dtype)
+    res = pm.run([(brick_unitaries(ops, n), ang) for n, ops, ang in work])
+    for (n, ops, ang), (probs, mean) in zip(work, res):
+        depth = len(brick_unitaries(ops, n))
+        tol = 1e-12 if dtype == "complex128" else 4 * c64_tol(depth)
+        per = []
+        for b in range(probs.shape[0]):
+            tops = ops if ang is None else oe.noisy_trajectory_ops(ops, ang[b])
+            pref = oe.all_probabilities(oe.run_ops(n, tops))
+            assert np.max(np.abs(probs[b] - pref)) <= tol, (n, b)
+            per.append(pref)
+        assert np.max(np.abs(mean - oe.pool_average(per))) <= tol
+    pm.close()
+
+
+def test_persistent_pool_equals_per_circuit_engine(gpu_lib):
+    work = _mixed_workload()
+    pm = gpu_lib.PoolMany("complex128")
+    res = pm.run([(brick_unitaries(ops, n), ang) for n, ops, ang in work])
+    for (n, ops, ang), (probs, mean) in zip(work, res):
+        U = brick_unitaries(ops, n)
+        pool = gpu_lib.Pool(n, "complex128", batch_max=1 if ang is None else ang.shape[0], depth_max=len(U))
+        p2, m2 = pool.run_brick(U, ang)
+        np.testing.assert_allclose(probs, p2, rtol=0, atol=1e-13)
+        pool.close()
+    # a second run in the same (already grown) workspace
+    res2 = pm.run([(brick_unitaries(ops, n), ang) for n, ops, ang in work])
+    for (pa, ma), (pb, mb) in zip(res, res2):
+        np.testing.assert_array_equal(ma, mb)
+
+
+def test_persistent_wait_limit_reports_timeout_and_recovers(gpu_lib):
+    """A wait that nothing satisfies gives up after its limit: the run returns
+    IQS_ETIMEOUT, all blocks stop, and the next run succeeds."""
+    from paper_2001_10554_gb300 import IQSError
+    work = _mixed_workload()
+    circuits = [(brick_unitaries(ops, n), ang) for n, ops, ang in work]
+    pm = gpu_lib.PoolMany("complex64")
+    pm.set_wait_limit(0.05, debug_never=True)
+    with pytest.raises(IQSError) as ei:
+        pm.run(circuits)
+    assert ei.value.status == 4
+    pm.set_wait_limit(2.0, debug_never=False)
+    res = pm.run(circuits)
+    n, ops, ang = work[1]
+    ref = oe.all_probabilities(oe.run_ops(n, ops))
+    assert np.max(np.abs(res[1][0][0] - ref)) <= 1e-5
