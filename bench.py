@@ -359,6 +359,20 @@ def ensemble_section(iqs, torch):
         out[dtype] = {"trajectories_per_s": round(circuits * traj / dt, 1), "seconds": round(dt, 3),
                       "layer_updates_per_s": round(layers / dt, 1)}
     out["mean_p1_diff_c64_vs_c128_max"] = float(np.max(np.abs(means["complex64"] - means["complex128"])))
+    # the whole ensemble (8 circuits, uneven depths) in one persistent launch
+    for dtype in ("complex64", "complex128"):
+        pm = iqs.PoolMany(dtype)
+        circs = [(Us[i], ens[i]["angles"]) for i in range(circuits)]
+        pm.run(circs)  # warm-up (grows the workspace to its full size)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = pm.run(circs)
+        dt = time.perf_counter() - t0
+        pm.close()
+        torch.cuda.empty_cache()
+        m = np.array([r[1] for r in res])
+        out[dtype]["one_launch"] = {"trajectories_per_s": round(circuits * traj / dt, 1), "seconds": round(dt, 3),
+                                    "mean_diff_vs_per_circuit_max": float(np.max(np.abs(m - means[dtype])))}
     # FP64 oracle on a bounded sample: 2 trajectories of the first circuit
     from oracle import ensemble as oe
     t0 = time.perf_counter()
