@@ -286,6 +286,7 @@ def qaoa_section(iqs, torch):
         edges = W.random_3regular_graph(n, 1000 + n)
         gm, bt = W.qaoa_parameter_sets(p, B, 2000 + n)
         eng = iqs.QAOA(n, edges, "complex64", batch_max=B)
+        tuned = eng.autotune(B, p)  # project autotuner picks the tile shape (untimed)
         eng.run(gm, bt)  # capture the graph
         reps = 2
         t0 = time.perf_counter()
@@ -304,7 +305,7 @@ def qaoa_section(iqs, torch):
         plain.close()
         torch.cuda.empty_cache()
         model = (12 * p + 2) * 8 * (1 << n) * B
-        out["rows"].append({"n": n, "p": p, "batch": B,
+        out["rows"].append({"n": n, "p": p, "batch": B, "tile_choice": {k: tuned[k] for k in ("row_bits", "grid_mult")},
                             "batched_c64_evals_per_s": round(B / dt, 1),
                             "plain_c128_evals_per_s": round(1 / dtp, 1),
                             "ratio": round((B / dt) * dtp, 2),

@@ -204,6 +204,19 @@ iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs);
 iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, const double* betas,
                         double* energies, double* grad_gammas, double* grad_betas);
 
+/* Project autotuner: times the candidate mixer tile shapes (the row width of
+ * the high passes, hence gate bits per pass: 4..6 row bits for complex64, 3..5
+ * for complex128) and grid sizes (1x, 2x blocks per state) on this workspace
+ * for ``batch`` parameter sets of depth p, and keeps the fastest (every shape
+ * gives the same results up to rounding).  With IQS_AUTOTUNE_CACHE=<file> the
+ * choice is appended to that file, and later workspaces of the same dtype, n
+ * and batch_max start from it.  ``best_ms`` (may be NULL): time of one
+ * evaluation of the batch with the chosen shape. */
+iqs_status iqs_qaoa_autotune(iqs_qaoa* q, int batch, int p, double* best_ms);
+
+/* Current tile-shape choice: high-pass row bits and grid multiplier. */
+iqs_status iqs_qaoa_tuning(const iqs_qaoa* q, int* row_bits, int* grid_mult);
+
 /* Copy the final state phi of parameter set ``index`` (after the last forward
  * pass, or after the uncompute when a gradient was computed) to host memory. */
 iqs_status iqs_qaoa_download_state(iqs_qaoa* q, int index, void* host, size_t bytes);

@@ -22,6 +22,8 @@
 //           to its initial value (both invariant under the exact uncompute).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -479,6 +481,9 @@ struct iqs_qaoa {
   std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int>> graphs;  // (B, p, grad, renorm) -> graph, kernels
   bool use_graphs = true;
   bool own_stream = false;
+  // tile-shape choice (autotuner): high-pass row bits (-1: default) and grid multiplier
+  int row_bits = -1;
+  int grid_mult = 1;
 };
 
 namespace iqs {
@@ -488,7 +493,7 @@ int part_stride_for(const iqs_qaoa* q) { return 2432 * 4; }  // partial slots pe
 
 int blocks_per_state(const iqs_qaoa* q, int B) {
   const uint64_t by_size = std::max<uint64_t>(1, q->N / 4096);
-  const int by_batch = std::max(1, 2432 / std::max(B, 1));
+  const int by_batch = std::max(1, q->grid_mult * 2432 / std::max(B, 1));
   return (int)std::min<uint64_t>(by_size, (uint64_t)std::min(by_batch, 2432));
 }
 
@@ -513,6 +518,8 @@ std::vector<Geo> plan_mixer(int n, int tile_bits, int row_bits) {
   }
   return out;
 }
+
+void replan(iqs_qaoa* q);
 
 template <class TR>
 size_t tile_smem(const Geo& g, int nvec) {
@@ -696,6 +703,44 @@ void fill_params_c128(iqs_qaoa* q, int B, int p, const double* gam, const double
     }
 }
 
+void replan(iqs_qaoa* q) {
+  const int K = q->dtype == IQS_C128 ? T128::kTileBits : T64::kTileBits;
+  const int rows0 = q->dtype == IQS_C128 ? T128::kRowBits : T64::kRowBits;
+  const int rows = q->row_bits < 0 ? rows0 : std::max(rows0, std::min(K - 1, q->row_bits));
+  q->passes = plan_mixer(q->n, K, rows);
+  for (auto& kv : q->graphs) cudaGraphExecDestroy(kv.second.first);
+  q->graphs.clear();
+}
+
+const char* dtype_name(int dtype) { return dtype == IQS_C128 ? "c128" : "c64"; }
+
+// Tile-shape choices persisted by the autotuner: lines "qaoa <dtype> <n> <batch_max> <row_bits> <grid_mult>".
+void load_tuning(iqs_qaoa* q) {
+  const char* path = std::getenv("IQS_AUTOTUNE_CACHE");
+  if (path == nullptr) return;
+  FILE* f = std::fopen(path, "r");
+  if (f == nullptr) return;
+  char kind[16], dt[8];
+  int n, bm, rows, mult;
+  while (std::fscanf(f, "%15s %7s %d %d %d %d", kind, dt, &n, &bm, &rows, &mult) == 6) {
+    if (std::strcmp(kind, "qaoa") == 0 && std::strcmp(dt, dtype_name(q->dtype)) == 0 && n == q->n && bm == q->bmax &&
+        mult >= 1 && mult <= 4) {
+      q->row_bits = rows;
+      q->grid_mult = mult;  // the last matching line wins
+    }
+  }
+  std::fclose(f);
+}
+
+void save_tuning(const iqs_qaoa* q) {
+  const char* path = std::getenv("IQS_AUTOTUNE_CACHE");
+  if (path == nullptr) return;
+  FILE* f = std::fopen(path, "a");
+  if (f == nullptr) return;
+  std::fprintf(f, "qaoa %s %d %d %d %d\n", dtype_name(q->dtype), q->n, q->bmax, q->row_bits, q->grid_mult);
+  std::fclose(f);
+}
+
 void free_qaoa(iqs_qaoa* q) {
   for (auto& kv : q->graphs) cudaGraphExecDestroy(kv.second.first);
   if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
@@ -790,8 +835,8 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
     free_qaoa(q);
     return report(IQS_ECUDA, "QAOA set-up: %s", cudaGetErrorString(e));
   }
-  q->passes = dtype == IQS_C128 ? plan_mixer(n, T128::kTileBits, T128::kRowBits)
-                                : plan_mixer(n, T64::kTileBits, T64::kRowBits);
+  load_tuning(q);
+  replan(q);
   *out = q;
   return IQS_OK;
 }
@@ -880,6 +925,61 @@ iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, con
     cudaMemsetAsync(q->flag, 0, sizeof(unsigned), s);
     return report(IQS_ERANGE, "an amplitude outside the emulated-FP64 range was met");
   }
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_autotune(iqs_qaoa* q, int batch, int p, double* best_ms) {
+  using namespace iqs;
+  if (q == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (batch < 1 || batch > q->bmax || p < 1 || p > kMaxP) return report(IQS_EINVAL, "bad batch or depth");
+  std::vector<double> g((size_t)batch * p, 0.3), b((size_t)batch * p, 0.2), E(batch), dg((size_t)batch * p),
+      db((size_t)batch * p);
+  const int rows0 = q->dtype == IQS_C128 ? T128::kRowBits : T64::kRowBits;
+  const bool graphs = q->use_graphs;
+  q->use_graphs = false;
+  double best = 1e300;
+  int best_rows = rows0, best_mult = 1;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return report(IQS_ECUDA, "autotune events");
+  iqs_status st = IQS_OK;
+  for (int rows = rows0; rows <= rows0 + 2 && st == IQS_OK; ++rows) {
+    for (int mult = 1; mult <= 2 && st == IQS_OK; ++mult) {
+      q->row_bits = rows;
+      q->grid_mult = mult;
+      replan(q);
+      st = iqs_qaoa_run(q, batch, p, g.data(), b.data(), E.data(), dg.data(), db.data());  // warm
+      if (st != IQS_OK) break;
+      cudaEventRecord(e0, q->stream);
+      st = iqs_qaoa_run(q, batch, p, g.data(), b.data(), E.data(), dg.data(), db.data());
+      cudaEventRecord(e1, q->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st == IQS_OK && ms < best) {
+        best = ms;
+        best_rows = rows;
+        best_mult = mult;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  q->row_bits = best_rows;
+  q->grid_mult = best_mult;
+  replan(q);
+  q->use_graphs = graphs;
+  if (st != IQS_OK) return st;
+  save_tuning(q);
+  if (best_ms) *best_ms = best;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_tuning(const iqs_qaoa* q, int* row_bits, int* grid_mult) {
+  if (q == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  const int rows0 = q->dtype == IQS_C128 ? iqs::T128::kRowBits : iqs::T64::kRowBits;
+  if (row_bits) *row_bits = q->row_bits < 0 ? rows0 : q->row_bits;
+  if (grid_mult) *grid_mult = q->grid_mult;
   return IQS_OK;
 }
 

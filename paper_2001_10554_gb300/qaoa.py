@@ -58,6 +58,17 @@ class QAOA:
         call("iqs_qaoa_run", self._h, batch, p, _ptr(g), _ptr(b), _ptr(E), None, None)
         return E
 
+    def autotune(self, batch: int | None = None, p: int = 4) -> dict:
+        """Pick the fastest mixer tile shape and grid size for (batch, p); returns the choice."""
+        ms = C.c_double()
+        call("iqs_qaoa_autotune", self._h, int(batch or self.batch_max), int(p), C.byref(ms))
+        return dict(self.tuning(), best_ms=ms.value)
+
+    def tuning(self) -> dict:
+        rows, mult = C.c_int(), C.c_int()
+        call("iqs_qaoa_tuning", self._h, C.byref(rows), C.byref(mult))
+        return {"row_bits": rows.value, "grid_mult": mult.value}
+
     def state(self, index: int = 0) -> np.ndarray:
         out = np.empty(1 << self.n, dtype=np.complex128 if self.dtype_code == _lib.IQS_C128 else np.complex64)
         call("iqs_qaoa_download_state", self._h, int(index), C.c_void_p(out.ctypes.data), C.c_size_t(out.nbytes))

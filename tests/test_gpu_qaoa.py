@@ -165,3 +165,36 @@ def test_qaoa_rejects_bad_arguments(gpu_lib):
         eng.run(np.zeros((3, 1)), np.zeros((3, 1)))
     with pytest.raises(IQSError):
         eng.run(np.full((1, 1), np.nan), np.zeros((1, 1)))
+
+
+def test_autotuner_keeps_results_and_persists_choice(gpu_lib, tmp_path):
+    import os
+    import subprocess
+    import sys
+    n, p, B = 14, 2, 8
+    edges = W.random_3regular_graph(n, 19)
+    gm, bt = W.qaoa_parameter_sets(p, B, 20)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=B)
+    E0, dg0, db0 = eng.run(gm, bt)
+    choice = eng.autotune(B, p)
+    assert 3 <= choice["row_bits"] <= 5 and choice["grid_mult"] in (1, 2) and choice["best_ms"] > 0
+    E1, dg1, db1 = eng.run(gm, bt)
+    np.testing.assert_allclose(E1, E0, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(dg1, dg0, rtol=0, atol=1e-11)
+    # the choice persists through IQS_AUTOTUNE_CACHE
+    cache = tmp_path / "tune.txt"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys, json; sys.path.insert(0, %r)\n"
+            "import paper_2001_10554_gb300 as iqs, workloads as W\n"
+            "e = iqs.QAOA(12, W.random_3regular_graph(12, 3), 'complex64', batch_max=4)\n"
+            "print(json.dumps(e.autotune(4, 2) if sys.argv[1] == 'tune' else e.tuning()))\n") % root
+    env = dict(os.environ, IQS_AUTOTUNE_CACHE=str(cache))
+    import json
+    r1 = subprocess.run([sys.executable, "-c", code, "tune"], env=env, capture_output=True, text=True, timeout=300)
+    assert r1.returncode == 0, r1.stderr
+    tuned = json.loads(r1.stdout.strip().splitlines()[-1])
+    assert cache.read_text().startswith("qaoa c64 12 4 ")
+    r2 = subprocess.run([sys.executable, "-c", code, "read"], env=env, capture_output=True, text=True, timeout=300)
+    assert r2.returncode == 0, r2.stderr
+    loaded = json.loads(r2.stdout.strip().splitlines()[-1])
+    assert loaded == {"row_bits": tuned["row_bits"], "grid_mult": tuned["grid_mult"]}
