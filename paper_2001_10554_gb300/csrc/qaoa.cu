@@ -276,12 +276,29 @@ __device__ __forceinline__ void mixer_rounds(typename TR::W* sp, typename TR::W*
   }
 }
 
-template <class TR, bool ADJ, int C>
+// PH = 1 (forward, low pass): the layer's cost phase T_b[C(x)] is applied to
+// each amplitude as the tile is loaded.  PH = 2 (adjoint, last pass): after the
+// mixer uncompute, each amplitude contributes C(x) Im(conj(lambda) phi) to the
+// phase gradient (partials_g) and both vectors are multiplied by
+// conj(T_b[C(x)]) as they are stored.  Either way one full pass per layer is saved.
+template <class TR, bool ADJ, int C, int PH>
 __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restrict__ phi,
                                                          typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
                                                          const typename TR::RX* __restrict__ rx,
-                                                         double* __restrict__ partials, int part_stride, unsigned* flag) {
+                                                         double* __restrict__ partials, int part_stride, unsigned* flag,
+                                                         const uint8_t* __restrict__ cut,
+                                                         const typename TR::PH* __restrict__ tables, int tsize,
+                                                         double* __restrict__ partials_g) {
   using W = typename TR::W;
+  using PHT = typename TR::PH;
+  __shared__ PHT st[PH ? kEdgeChunk + 1 : 1];
+  if (PH) {
+    for (int i = threadIdx.x; i < tsize; i += blockDim.x) {
+      const PHT tt = tables[(uint64_t)blockIdx.y * tsize + i];
+      st[i] = PH == 2 ? TR::conj(tt) : tt;
+    }
+    __syncthreads();
+  }
   constexpr int K = TR::kTileBits;
   constexpr int M = K - C;
   constexpr unsigned T = 1u << K;
@@ -303,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restr
   const unsigned sw0 = swz<TR>(tid);
   const int mid = s - C;
   unsigned bad = 0;
-  dfx::Acc acc;
+  dfx::Acc acc, accg;
   for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
 #pragma unroll
@@ -311,23 +328,43 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restr
       const unsigned l = tid + kThreads * i;
       const uint64_t x = C <= 8 ? tbase + off0 + step * i : tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
       const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
-      sp[idx] = TR::load(P[x], bad);
+      if (PH == 1) sp[idx] = TR::mul(st[cut[x]], TR::load(P[x], bad));
+      else sp[idx] = TR::load(P[x], bad);
       if (ADJ) sl[idx] = TR::load(L[x], bad);
     }
     __syncthreads();
     mixer_rounds<TR, ADJ, C, C>(sp, sl, k, acc);
+    float gsum = 0.f;
 #pragma unroll
     for (unsigned i = 0; i < PER; ++i) {
       const unsigned l = tid + kThreads * i;
       const uint64_t x = C <= 8 ? tbase + off0 + step * i : tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
       const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
-      P[x] = TR::store(sp[idx]);
-      if (ADJ) L[x] = TR::store(sl[idx]);
+      if (PH == 2) {
+        const int c = cut[x];
+        const W xv = sp[idx], yv = sl[idx];
+        const float cf = (float)c;
+        if constexpr (TR::kBlockSum) {
+          gsum = fmaf(cf, qops::im_conj_mul_fma(yv, xv, 0.f), gsum);
+        } else {
+          float pp, ee;
+          qops::im_conj_mul(yv, xv, pp, ee);
+          const float qq = cf * pp;
+          accg.add(qq, fmaf(cf, pp, -qq) + cf * ee);
+        }
+        P[x] = TR::store(TR::mul(st[c], xv));
+        L[x] = TR::store(TR::mul(st[c], yv));
+      } else {
+        P[x] = TR::store(sp[idx]);
+        if (ADJ) L[x] = TR::store(sl[idx]);
+      }
     }
+    if (PH == 2 && TR::kBlockSum) accg.add(gsum, 0.f);
     __syncthreads();
   }
   if (bad) atomicOr(flag, 1u);
   if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+  if (PH == 2) block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
 }
 
 // Cost phase: psi_x <- T_b[C(x)] psi_x.  When ADJ: accumulate Im conj(lambda) C phi
@@ -489,7 +526,10 @@ struct iqs_qaoa {
 namespace iqs {
 namespace {
 
-int part_stride_for(const iqs_qaoa* q) { return 2432 * 4; }  // partial slots per state: passes x blocks
+// Partial slots per state: mixer passes x blocks (<= 4 x 2432), then the fused
+// phase-gradient partials at kGammaCol.
+constexpr int kGammaCol = 2432 * 4;
+int part_stride_for(const iqs_qaoa* q) { return 2432 * 5; }
 
 int blocks_per_state(const iqs_qaoa* q, int B) {
   const uint64_t by_size = std::max<uint64_t>(1, q->N / 4096);
@@ -526,24 +566,44 @@ size_t tile_smem(const Geo& g, int nvec) {
   return (size_t)nvec * ((size_t)1 << (g.c + g.m)) * sizeof(typename TR::W);
 }
 
+// Optional fused cost phase of a mixer pass (see k_mixer_fast).
+template <class TR>
+struct PhaseFuse {
+  int mode = 0;  // 0 none, 1 forward on load, 2 adjoint on store
+  const uint8_t* cut = nullptr;
+  const typename TR::PH* tables = nullptr;
+  int tsize = 0;
+  double* partials_g = nullptr;
+};
+
 template <class TR, bool ADJ, int C>
 void launch_fast(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N, int sb,
-                 const typename TR::RX* rx, double* partials, int ps, unsigned* flag) {
-  k_mixer_fast<TR, ADJ, C><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag);
+                 const typename TR::RX* rx, double* partials, int ps, unsigned* flag, const PhaseFuse<TR>& f) {
+  if (!ADJ && f.mode == 1)
+    k_mixer_fast<TR, ADJ, C, (ADJ ? 0 : 1)><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
+                                                                          f.cut, f.tables, f.tsize, f.partials_g);
+  else if (ADJ && f.mode == 2)
+    k_mixer_fast<TR, ADJ, C, (ADJ ? 2 : 0)><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
+                                                                          f.cut, f.tables, f.tsize, f.partials_g);
+  else
+    k_mixer_fast<TR, ADJ, C, 0><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag, nullptr, nullptr,
+                                                             0, nullptr);
 }
 
 template <class TR, int C>
 cudaError_t set_attr_c(int bytes) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C>, a, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C>, a, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C, 0>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C, 0>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C, 1>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C, 2>, a, bytes);
   return e;
 }
 
 template <class TR, int... Cs>
 cudaError_t set_attr_all(int bytes, std::integer_sequence<int, Cs...>) {
   cudaError_t e = cudaSuccess;
-  ((e = (e == cudaSuccess ? set_attr_c<TR, Cs>(bytes) : e)), ...);
+  ((e = (e == cudaSuccess ? set_attr_c<TR, Cs + TR::kRowBits>(bytes) : e)), ...);
   return e;
 }
 
@@ -554,18 +614,17 @@ cudaError_t set_smem_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_mixer<TR, false>, a, bytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer<TR, true>, a, bytes);
   if (e == cudaSuccess) e = set_attr_c<TR, 0>(bytes);
-  if (e == cudaSuccess) e = set_attr_all<TR>(bytes, std::make_integer_sequence<int, TR::kTileBits>{});
+  if (e == cudaSuccess) e = set_attr_all<TR>(bytes, std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{});
   return e;
 }
 
 template <class TR, bool ADJ, int... Cs>
 bool dispatch_fast(int c, dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam,
                    uint64_t N, int sb, const typename TR::RX* rx, double* partials, int ps, unsigned* flag,
-                   std::integer_sequence<int, Cs...>) {
+                   const PhaseFuse<TR>& f, std::integer_sequence<int, Cs...>) {
   bool done = false;
-  ((c == Cs && Cs >= TR::kRowBits && !done
-        ? (launch_fast<TR, ADJ, (Cs >= TR::kRowBits ? Cs : TR::kRowBits)>(grid, smem, s, phi, lam, N, sb, rx, partials,
-                                                                          ps, flag),
+  ((c == Cs + TR::kRowBits && !done
+        ? (launch_fast<TR, ADJ, Cs + TR::kRowBits>(grid, smem, s, phi, lam, N, sb, rx, partials, ps, flag, f),
            done = true)
         : false),
    ...);
@@ -574,17 +633,27 @@ bool dispatch_fast(int c, dim3 grid, size_t smem, cudaStream_t s, typename TR::V
 
 // One mixer pass: a kernel specialised for the tile shape when the tile is
 // full (2^kTileBits amplitudes), the generic one otherwise (tiny states).
+// True when a pass runs on the shape-specialised kernels (full 2^K tile),
+// which are the ones that can carry the fused cost phase.
+template <class TR>
+bool fast_shape(const Geo& g) {
+  return g.c + g.m == TR::kTileBits && (g.c == 0 ? g.s == 0 : g.c >= TR::kRowBits);
+}
+
+// One mixer pass: a kernel specialised for the tile shape when the tile is
+// full (2^kTileBits amplitudes), the generic one otherwise (tiny states).
 template <class TR, bool ADJ>
 void launch_mixer(const Geo& g, dim3 grid, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N,
-                  const typename TR::RX* rx, double* partials, int ps, unsigned* flag) {
+                  const typename TR::RX* rx, double* partials, int ps, unsigned* flag,
+                  const PhaseFuse<TR>& f = PhaseFuse<TR>()) {
   const size_t smem = tile_smem<TR>(g, ADJ ? 2 : 1);
   if (g.c + g.m == TR::kTileBits && g.c == 0 && g.s == 0) {
-    launch_fast<TR, ADJ, 0>(grid, smem, s, phi, lam, N, 0, rx, partials, ps, flag);
+    launch_fast<TR, ADJ, 0>(grid, smem, s, phi, lam, N, 0, rx, partials, ps, flag, f);
     return;
   }
   if (g.c + g.m == TR::kTileBits &&
-      dispatch_fast<TR, ADJ>(g.c, grid, smem, s, phi, lam, N, g.s, rx, partials, ps, flag,
-                             std::make_integer_sequence<int, TR::kTileBits>{}))
+      dispatch_fast<TR, ADJ>(g.c, grid, smem, s, phi, lam, N, g.s, rx, partials, ps, flag, f,
+                             std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{}))
     return;
   k_mixer<TR, ADJ><<<grid, kThreads, smem, s>>>(phi, lam, N, g, rx, partials, ps, flag);
 }
@@ -613,14 +682,26 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
   k_fill_uniform<V><<<grid_for(N * B, 1, 16), kThreads, 0, s>>>(phi, N * B, v0);
   ++launches;
   const dim3 g_stream(PB, B);
+  const bool fuse_in = fast_shape<TR>(q->passes.front());
+  const bool fuse_out = fast_shape<TR>(q->passes.back());
   for (int l = 0; l < p; ++l) {
-    k_phase<TR, false><<<g_stream, kThreads, 0, s>>>(phi, nullptr, N, q->cut, tab + (uint64_t)l * q->bmax * tsize,
-                                                     tsize, nullptr, 0, q->flag);
-    ++launches;
-    for (const Geo& g : q->passes) {
+    const typename TR::PH* tab_l = tab + (uint64_t)l * q->bmax * tsize;
+    if (!fuse_in) {
+      k_phase<TR, false><<<g_stream, kThreads, 0, s>>>(phi, nullptr, N, q->cut, tab_l, tsize, nullptr, 0, q->flag);
+      ++launches;
+    }
+    for (size_t i = 0; i < q->passes.size(); ++i) {
+      const Geo& g = q->passes[i];
       const uint64_t tiles = N >> (g.c + g.m);
       const dim3 grid((unsigned)std::min<uint64_t>(tiles, (uint64_t)PB), B);
-      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)l * q->bmax, nullptr, 0, q->flag);
+      PhaseFuse<TR> f;
+      if (i == 0 && fuse_in) {
+        f.mode = 1;
+        f.cut = q->cut;
+        f.tables = tab_l;
+        f.tsize = tsize;
+      }
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)l * q->bmax, nullptr, 0, q->flag, f);
       ++launches;
     }
   }
@@ -636,21 +717,39 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
       k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms + q->bmax, 1, 0);
       launches += 2;
     }
+    double* partials_g = q->partials + kGammaCol;  // phase-gradient partials of the fused last pass
     for (int l = p - 1; l >= 0; --l) {
+      const typename TR::PH* tab_l = tab + (uint64_t)l * q->bmax * tsize;
       int col = 0;
-      for (const Geo& g : q->passes) {
+      unsigned last_gx = 0;
+      for (size_t i = 0; i < q->passes.size(); ++i) {
+        const Geo& g = q->passes[i];
         const uint64_t tiles = N >> (g.c + g.m);
         const unsigned gx = (unsigned)std::min<uint64_t>(tiles, (uint64_t)PB);
         const dim3 grid(gx, B);
-        launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx + (uint64_t)l * q->bmax, q->partials + col, ps, q->flag);
+        PhaseFuse<TR> f;
+        if (i + 1 == q->passes.size() && fuse_out) {
+          f.mode = 2;
+          f.cut = q->cut;
+          f.tables = tab_l;
+          f.tsize = tsize;
+          f.partials_g = partials_g;
+        }
+        launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx + (uint64_t)l * q->bmax, q->partials + col, ps, q->flag, f);
         col += gx;
+        last_gx = gx;
         ++launches;
       }
       k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, col, ps, 2.0, q->results, out_stride, 1 + p + l);
-      k_phase<TR, true><<<g_stream, kThreads, 0, s>>>(phi, lam, N, q->cut, tab + (uint64_t)l * q->bmax * tsize, tsize,
-                                                      q->partials, ps, q->flag);
-      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 2.0, q->results, out_stride, 1 + l);
-      launches += 3;
+      ++launches;
+      if (fuse_out) {
+        k_finalize_batch<<<B, kThreads, 0, s>>>(partials_g, (int)last_gx, ps, 2.0, q->results, out_stride, 1 + l);
+        ++launches;
+      } else {
+        k_phase<TR, true><<<g_stream, kThreads, 0, s>>>(phi, lam, N, q->cut, tab_l, tsize, q->partials, ps, q->flag);
+        k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 2.0, q->results, out_stride, 1 + l);
+        launches += 2;
+      }
       if (R > 0 && l > 0 && ((p - l) % R) == 0) {
         k_norm_batch<TR><<<g_stream, kThreads, 0, s>>>(phi, N, q->partials, ps, q->flag);
         k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms, 1, 0);
