@@ -53,6 +53,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the complex64 32q sweep and the QAOA sections")
+    ap.add_argument("--profile-qaoa", default=None, metavar="N,P,BATCH",
+                    help="run one complex64 QAOA energy + gradient evaluation of BATCH parameter sets and exit "
+                         "(a small, fixed launch sequence for profilers)")
     return ap.parse_args(argv)
 
 
@@ -387,10 +390,25 @@ def ensemble_section(iqs, torch):
 
 
 # ---------------------------------------------------------------- GPU arm
+def profile_qaoa(spec: str) -> int:
+    import paper_2001_10554_gb300 as iqs
+    import workloads as W
+    n, p, batch = (int(v) for v in spec.split(","))
+    edges = W.random_3regular_graph(n, 1000 + n)
+    gm, bt = W.qaoa_parameter_sets(p, batch, 7)
+    eng = iqs.QAOA(n, edges, "complex64", batch_max=batch)
+    E, _, _ = eng.run(gm, bt)
+    print(json.dumps({"profile_qaoa": [n, p, batch], "energy0": float(E[0])}))
+    eng.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_qaoa:
+        return profile_qaoa(args.profile_qaoa)
 
     import torch
     import torch.distributed as dist
