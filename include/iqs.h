@@ -204,9 +204,10 @@ iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs);
 iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, const double* betas,
                         double* energies, double* grad_gammas, double* grad_betas);
 
-/* Project autotuner: times the candidate mixer tile shapes (the row width of
- * the high passes, hence gate bits per pass: 4..6 row bits for complex64, 3..5
- * for complex128) and grid sizes (1x, 2x blocks per state) on this workspace
+/* Project autotuner: times TMA staging (off / forward / forward + adjoint),
+ * then the candidate mixer tile shapes (the row width of the high passes,
+ * hence gate bits per pass: 4..6 row bits for complex64, 3..5 for complex128)
+ * and grid sizes (1x, 2x blocks per state) on this workspace
  * for ``batch`` parameter sets of depth p, and keeps the fastest (every shape
  * gives the same results up to rounding).  With IQS_AUTOTUNE_CACHE=<file> the
  * choice is appended to that file, and later workspaces of the same dtype, n
@@ -216,6 +217,14 @@ iqs_status iqs_qaoa_autotune(iqs_qaoa* q, int batch, int p, double* best_ms);
 
 /* Current tile-shape choice: high-pass row bits and grid multiplier. */
 iqs_status iqs_qaoa_tuning(const iqs_qaoa* q, int* row_bits, int* grid_mult);
+
+/* Mixer-tile staging by the Tensor Memory Accelerator (cp.async.bulk.tensor
+ * loads and stores, double-buffered): mode 0 off, 1 forward passes, 2 forward
+ * and adjoint passes.  It applies to full 2^K-amplitude tiles (n >= 12 for
+ * complex64, 11 for complex128); ``available`` reports whether the tensor maps
+ * of the current plan could be built.  The autotuner also chooses this mode. */
+iqs_status iqs_qaoa_set_tma(iqs_qaoa* q, int mode);
+iqs_status iqs_qaoa_get_tma(const iqs_qaoa* q, int* mode, int* available);
 
 /* Copy the final state phi of parameter set ``index`` (after the last forward
  * pass, or after the uncompute when a gradient was computed) to host memory. */

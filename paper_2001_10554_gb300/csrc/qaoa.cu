@@ -27,6 +27,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <tuple>
 #include <utility>
@@ -38,6 +39,9 @@
 #include "internal.h"
 #include "qaoa_ops.cuh"
 #include "tile.cuh"
+
+#include <cuda.h>
+#include <type_traits>
 
 namespace iqs {
 namespace {
@@ -60,6 +64,7 @@ struct T64 {
   // before the double-float accumulation: their rounding (<= 32 * 2^-24 of the
   // terms) stays below the complex64 state's own error.
   static constexpr bool kBlockSum = true;
+  static constexpr bool kTmaSwizzle = false;
   __device__ static W load(V v, unsigned&) { return v; }
   __device__ static V store(const W& w) { return w; }
   __device__ static RX rx_inv(RX k) { return make_float2(k.x, -k.y); }
@@ -78,6 +83,7 @@ struct T128 {
   static constexpr int kRegBits = 3;    // gates per register round (8 amplitudes per thread)
   static constexpr int kSwzBits = 3;    // 8 elements of 16 B per 128-byte smem row
   static constexpr bool kBlockSum = false;  // every gradient term goes to the double-float accumulator
+  static constexpr bool kTmaSwizzle = false;
   __device__ static W load(V v, unsigned& bad) { return qops::to_split(v, bad); }
   __device__ static V store(const W& w) { return qops::from_split(w); }
   __device__ static RX rx_inv(RX k) {
@@ -367,6 +373,212 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restr
   if (PH == 2) block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
 }
 
+// ---------------------------------------------------------------- TMA-staged mixer pass
+// The same pass with its tiles moved by the Tensor Memory Accelerator: one
+// thread issues cp.async.bulk.tensor loads (completion counted on an
+// mbarrier) and stores (bulk groups); two tile buffers per vector let the next
+// tile stream in while the current one is computed.  The tensor maps use the
+// hardware 128-byte swizzle, which the register rounds index directly
+// (kTmaSwizzle).  x coordinates are always 0, so every copy starts on a
+// 128-byte row.
+template <class TR>
+struct TmaTraits : TR {
+  static constexpr bool kTmaSwizzle = true;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int rank, const int* c, uint64_t* bar) {
+  if (rank == 3)
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(smem_u32(bar))
+        : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+        "[%7];" ::"r"(smem_u32(dst)), "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store(const CUtensorMap* map, int rank, const int* c, const void* src) {
+  if (rank == 3)
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(smem_u32(src))
+                 : "memory");
+  else
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(map),
+                 "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr uint32_t kMbarSpinLimit = 1u << 26;  // try_wait rounds before a wait is declared failed
+
+template <class TR, bool ADJ, int C, int PH>
+__global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ CUtensorMap tm_phi,
+                                                        const __grid_constant__ CUtensorMap tm_lam, uint64_t N,
+                                                        int s_bits, int hi_bits, const typename TR::RX* __restrict__ rx,
+                                                        double* __restrict__ partials, int part_stride, unsigned* flag,
+                                                        const uint8_t* __restrict__ cut,
+                                                        const typename TR::PH* __restrict__ tables, int tsize,
+                                                        double* __restrict__ partials_g, unsigned* err) {
+  using TT = TmaTraits<TR>;
+  using V = typename TR::V;
+  using W = typename TR::W;
+  using PHT = typename TR::PH;
+  constexpr int K = TR::kTileBits;
+  constexpr int M = K - C;
+  constexpr unsigned T = 1u << K;
+  constexpr unsigned PER = T / kThreads;
+  constexpr unsigned TILE = T * sizeof(V);
+  constexpr int NV = ADJ ? 2 : 1;
+  constexpr bool CONVERT = !std::is_same<V, W>::value;  // complex128: split in place after the load
+  constexpr int RANK = C == 0 ? 3 : 5;
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  // the 128-byte TMA swizzle needs 1024-byte aligned tiles (1 KiB of slack is allocated)
+  unsigned char* smem_raw = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ PHT st[PH ? kEdgeChunk + 1 : 1];
+  const unsigned tid = threadIdx.x;
+  const unsigned b = blockIdx.y;
+  if (PH) {
+    for (int i = tid; i < tsize; i += blockDim.x) {
+      const PHT tt = tables[(uint64_t)b * tsize + i];
+      st[i] = PH == 2 ? TR::conj(tt) : tt;
+    }
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const typename TR::RX k = ADJ ? TR::rx_inv(rx[b]) : rx[b];
+  const uint64_t tiles = N >> K;
+  const int s = C == 0 ? 0 : s_bits;
+  const int mid = s - C;
+  auto vbuf = [&](int buf, int vec) { return smem_raw + (size_t)(buf * NV + vec) * TILE; };
+  auto coords = [&](uint64_t t, int* c) {
+    if (C == 0) {
+      c[0] = 0; c[1] = 0; c[2] = (int)(b * tiles + t);
+    } else {
+      c[0] = 0; c[1] = 0; c[2] = (int)(t & ((1ull << mid) - 1ull)); c[3] = 0;
+      c[4] = (int)((t >> mid) + ((uint64_t)b << hi_bits));
+    }
+  };
+  auto issue = [&](uint64_t t, int buf) {
+    int c[5];
+    coords(t, c);
+    mbar_expect_tx(&mbar[buf], TILE * NV);
+    tma_load(vbuf(buf, 0), &tm_phi, RANK, c, &mbar[buf]);
+    if (ADJ) tma_load(vbuf(buf, 1), &tm_lam, RANK, c, &mbar[buf]);
+  };
+  unsigned phase0 = 0, phase1 = 0;
+  unsigned bad = 0;
+  dfx::Acc acc, accg;
+  uint64_t t = blockIdx.x;
+  if (t < tiles && tid == 0) issue(t, 0);
+  for (int it = 0; t < tiles; ++it, t += gridDim.x) {
+    const int buf = it & 1;
+    const uint64_t tn = t + gridDim.x;
+    if (tid == 0 && tn < tiles) {
+      bulk_wait_read0();  // the other buffer's previous store has read its shared memory
+      fence_proxy_async();
+      issue(tn, buf ^ 1);
+    }
+    unsigned& ph = buf ? phase1 : phase0;
+    bool ok = false;
+    for (uint32_t spin = 0; spin < kMbarSpinLimit; ++spin)
+      if (mbar_try_wait(&mbar[buf], ph)) { ok = true; break; }
+    ph ^= 1u;
+    if (__syncthreads_or(!ok)) {  // a tile never arrived: report and leave
+      if (tid == 0) atomicOr(err, 1u);
+      break;
+    }
+    W* sp = reinterpret_cast<W*>(vbuf(buf, 0));
+    W* sl = ADJ ? reinterpret_cast<W*>(vbuf(buf, 1)) : nullptr;
+    const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
+    if (CONVERT || PH == 1) {
+#pragma unroll
+      for (unsigned i = 0; i < PER; ++i) {
+        const unsigned l = tid + kThreads * i;
+        const unsigned idx = swz<TT>(l);
+        W w = TR::load(reinterpret_cast<const V*>(sp)[idx], bad);
+        if (PH == 1) {
+          const uint64_t x = tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
+          w = TR::mul(st[cut[x]], w);
+        }
+        sp[idx] = w;
+        if (ADJ && CONVERT) sl[idx] = TR::load(reinterpret_cast<const V*>(sl)[idx], bad);
+      }
+      __syncthreads();
+    }
+    mixer_rounds<TT, ADJ, C, C>(sp, sl, k, acc);
+    if (CONVERT || PH == 2) {
+      float gsum = 0.f;
+#pragma unroll
+      for (unsigned i = 0; i < PER; ++i) {
+        const unsigned l = tid + kThreads * i;
+        const unsigned idx = swz<TT>(l);
+        W xv = sp[idx];
+        W yv = ADJ ? sl[idx] : xv;
+        if (PH == 2) {
+          const uint64_t x = tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
+          const int c = cut[x];
+          const float cf = (float)c;
+          if constexpr (TR::kBlockSum) {
+            gsum = fmaf(cf, qops::im_conj_mul_fma(yv, xv, 0.f), gsum);
+          } else {
+            float pp, ee;
+            qops::im_conj_mul(yv, xv, pp, ee);
+            const float qq = cf * pp;
+            accg.add(qq, fmaf(cf, pp, -qq) + cf * ee);
+          }
+          xv = TR::mul(st[c], xv);
+          yv = TR::mul(st[c], yv);
+        }
+        reinterpret_cast<V*>(sp)[idx] = TR::store(xv);
+        if (ADJ) reinterpret_cast<V*>(sl)[idx] = TR::store(yv);
+      }
+      if (PH == 2 && TR::kBlockSum) accg.add(gsum, 0.f);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      int c[5];
+      coords(t, c);
+      tma_store(&tm_phi, RANK, c, vbuf(buf, 0));
+      if (ADJ) tma_store(&tm_lam, RANK, c, vbuf(buf, 1));
+      bulk_commit();
+    }
+  }
+  if (tid == 0) bulk_wait0();
+  __syncthreads();
+  if (bad) atomicOr(flag, 1u);
+  if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+  if (PH == 2) block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
+}
+
 // Cost phase: psi_x <- T_b[C(x)] psi_x.  When ADJ: accumulate Im conj(lambda) C phi
 // first, then multiply both vectors by conj(T_b[C(x)]).
 template <class TR, bool ADJ>
@@ -521,6 +733,11 @@ struct iqs_qaoa {
   // tile-shape choice (autotuner): high-pass row bits (-1: default) and grid multiplier
   int row_bits = -1;
   int grid_mult = 1;
+  // TMA-staged mixer passes: 0 off, 1 forward passes, 2 forward and adjoint passes
+  int tma_mode = 0;
+  std::vector<CUtensorMap> tm_phi, tm_lam;  // one per mixer pass (valid when tma_ok)
+  bool tma_ok = false;
+  unsigned* tma_err = nullptr;              // device word: a TMA wait gave up
 };
 
 namespace iqs {
@@ -640,12 +857,88 @@ bool fast_shape(const Geo& g) {
   return g.c + g.m == TR::kTileBits && (g.c == 0 ? g.s == 0 : g.c >= TR::kRowBits);
 }
 
-// One mixer pass: a kernel specialised for the tile shape when the tile is
-// full (2^kTileBits amplitudes), the generic one otherwise (tiny states).
+// TMA staging of one pass (tensor maps built by replan()).
+struct TmaArgs {
+  bool use = false;
+  const CUtensorMap* phi = nullptr;
+  const CUtensorMap* lam = nullptr;
+  int hi_bits = 0;
+  unsigned* err = nullptr;
+};
+
+template <class TR>
+size_t tma_smem(bool adj) {
+  return (size_t)2 * (adj ? 2 : 1) * ((size_t)1 << TR::kTileBits) * sizeof(typename TR::V) + 1024;
+}
+
+template <class TR, bool ADJ, int C, int PH>
+void launch_tma1(dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename TR::RX* rx, double* partials, int ps,
+                 unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta) {
+  k_mixer_tma<TR, ADJ, C, PH><<<grid, kThreads, tma_smem<TR>(ADJ), s>>>(
+      *ta.phi, ADJ ? *ta.lam : *ta.phi, N, sb, ta.hi_bits, rx, partials, ps, flag, f.cut, f.tables, f.tsize,
+      f.partials_g, ta.err);
+}
+
+template <class TR, bool ADJ, int C>
+void launch_tma_c(dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename TR::RX* rx, double* partials, int ps,
+                  unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta) {
+  if (!ADJ && f.mode == 1 && C == 0)
+    launch_tma1<TR, ADJ, C, (!ADJ && C == 0) ? 1 : 0>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
+  else if (ADJ && f.mode == 2)
+    launch_tma1<TR, ADJ, C, ADJ ? 2 : 0>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
+  else
+    launch_tma1<TR, ADJ, C, 0>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
+}
+
+template <class TR, bool ADJ, int... Cs>
+void dispatch_tma(int c, dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename TR::RX* rx, double* partials,
+                  int ps, unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta,
+                  std::integer_sequence<int, Cs...>) {
+  bool done = false;
+  ((c == Cs + TR::kRowBits && !done
+        ? (launch_tma_c<TR, ADJ, Cs + TR::kRowBits>(grid, s, N, sb, rx, partials, ps, flag, f, ta), done = true)
+        : false),
+   ...);
+}
+
+template <class TR, bool ADJ, int... Cs>
+cudaError_t set_tma_attrs_c(std::integer_sequence<int, Cs...>) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const int bytes = (int)tma_smem<TR>(ADJ);
+  cudaError_t e = cudaSuccess;
+  ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, 0>, a, bytes) : e), ...);
+  if (ADJ) ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, ADJ ? 2 : 0>, a, bytes) : e), ...);
+  return e;
+}
+
+template <class TR>
+cudaError_t set_tma_attrs() {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 0>, a, (int)tma_smem<TR>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 1>, a, (int)tma_smem<TR>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, true, 0, 0>, a, (int)tma_smem<TR>(true));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, true, 0, 2>, a, (int)tma_smem<TR>(true));
+  const auto seq = std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{};
+  if (e == cudaSuccess) e = set_tma_attrs_c<TR, false>(seq);
+  if (e == cudaSuccess) e = set_tma_attrs_c<TR, true>(seq);
+  return e;
+}
+
+// One mixer pass: TMA-staged when requested and possible, else the kernel
+// specialised for the tile shape when the tile is full (2^kTileBits
+// amplitudes), else the generic one (tiny states).
 template <class TR, bool ADJ>
 void launch_mixer(const Geo& g, dim3 grid, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N,
                   const typename TR::RX* rx, double* partials, int ps, unsigned* flag,
-                  const PhaseFuse<TR>& f = PhaseFuse<TR>()) {
+                  const PhaseFuse<TR>& f = PhaseFuse<TR>(), const TmaArgs& ta = TmaArgs()) {
+  if (ta.use && fast_shape<TR>(g)) {
+    if (g.c == 0)
+      launch_tma_c<TR, ADJ, 0>(grid, s, N, 0, rx, partials, ps, flag, f, ta);
+    else
+      dispatch_tma<TR, ADJ>(g.c, grid, s, N, g.s, rx, partials, ps, flag, f, ta,
+                            std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{});
+    return;
+  }
   const size_t smem = tile_smem<TR>(g, ADJ ? 2 : 1);
   if (g.c + g.m == TR::kTileBits && g.c == 0 && g.s == 0) {
     launch_fast<TR, ADJ, 0>(grid, smem, s, phi, lam, N, 0, rx, partials, ps, flag, f);
@@ -701,7 +994,13 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
         f.tables = tab_l;
         f.tsize = tsize;
       }
-      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)l * q->bmax, nullptr, 0, q->flag, f);
+      TmaArgs ta;
+      ta.use = q->tma_ok && q->tma_mode >= 1;
+      ta.phi = &q->tm_phi[i];
+      ta.lam = &q->tm_lam[i];
+      ta.hi_bits = q->n - g.s - g.m;
+      ta.err = q->tma_err;
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)l * q->bmax, nullptr, 0, q->flag, f, ta);
       ++launches;
     }
   }
@@ -735,7 +1034,14 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
           f.tsize = tsize;
           f.partials_g = partials_g;
         }
-        launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx + (uint64_t)l * q->bmax, q->partials + col, ps, q->flag, f);
+        TmaArgs ta;
+        ta.use = q->tma_ok && q->tma_mode >= 2;
+        ta.phi = &q->tm_phi[i];
+        ta.lam = &q->tm_lam[i];
+        ta.hi_bits = q->n - g.s - g.m;
+        ta.err = q->tma_err;
+        launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx + (uint64_t)l * q->bmax, q->partials + col, ps, q->flag, f,
+                               ta);
         col += gx;
         last_gx = gx;
         ++launches;
@@ -802,6 +1108,51 @@ void fill_params_c128(iqs_qaoa* q, int B, int p, const double* gam, const double
     }
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult res;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &res) ==
+            cudaSuccess &&
+        res == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of one mixer pass over ``bmax`` states of 2^n amplitudes at ``base``
+// (8-byte units: a complex128 amplitude is two).  Low pass: [row, rows, tiles x B];
+// high pass: [row, row blocks, mid bits, gate bits, high bits x B], box = one tile.
+bool make_tile_map(CUtensorMap* m, void* base, const Geo& g, int n, int bmax, int amp_bytes, int K, int r0) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  const cuuint64_t eb = (cuuint64_t)amp_bytes, upa = (cuuint64_t)amp_bytes / 8;
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  if (g.c == 0) {
+    const cuuint64_t dims[3] = {(1ull << r0) * upa, 1ull << (K - r0), ((1ull << n) >> K) * (cuuint64_t)bmax};
+    const cuuint64_t strides[2] = {(1ull << r0) * eb, (1ull << K) * eb};
+    const cuuint32_t box[3] = {(cuuint32_t)((1u << r0) * upa), 1u << (K - r0), 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  const cuuint64_t dims[5] = {(1ull << r0) * upa, 1ull << (g.c - r0), 1ull << (g.s - g.c), 1ull << g.m,
+                              (1ull << (n - g.s - g.m)) * (cuuint64_t)bmax};
+  const cuuint64_t strides[4] = {(1ull << r0) * eb, (1ull << g.c) * eb, (1ull << g.s) * eb,
+                                 (1ull << (g.s + g.m)) * eb};
+  const cuuint32_t box[5] = {(cuuint32_t)((1u << r0) * upa), 1u << (g.c - r0), 1u, 1u << g.m, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void replan(iqs_qaoa* q) {
   const int K = q->dtype == IQS_C128 ? T128::kTileBits : T64::kTileBits;
   const int rows0 = q->dtype == IQS_C128 ? T128::kRowBits : T64::kRowBits;
@@ -809,23 +1160,39 @@ void replan(iqs_qaoa* q) {
   q->passes = plan_mixer(q->n, K, rows);
   for (auto& kv : q->graphs) cudaGraphExecDestroy(kv.second.first);
   q->graphs.clear();
+  // tensor maps for the TMA-staged passes (full tiles only)
+  const int amp = q->dtype == IQS_C128 ? 16 : 8;
+  q->tm_phi.assign(q->passes.size(), CUtensorMap{});
+  q->tm_lam.assign(q->passes.size(), CUtensorMap{});
+  q->tma_ok = tensor_map_encoder() != nullptr;
+  for (size_t i = 0; i < q->passes.size() && q->tma_ok; ++i) {
+    const Geo& g = q->passes[i];
+    if (g.c + g.m != K || (g.c != 0 && g.c < rows0)) {
+      q->tma_ok = false;
+      break;
+    }
+    q->tma_ok = make_tile_map(&q->tm_phi[i], q->phi, g, q->n, q->bmax, amp, K, rows0) &&
+                make_tile_map(&q->tm_lam[i], q->lam, g, q->n, q->bmax, amp, K, rows0);
+  }
 }
 
 const char* dtype_name(int dtype) { return dtype == IQS_C128 ? "c128" : "c64"; }
 
-// Tile-shape choices persisted by the autotuner: lines "qaoa <dtype> <n> <batch_max> <row_bits> <grid_mult>".
+// Tile-shape choices persisted by the autotuner:
+// lines "qaoa <dtype> <n> <batch_max> <row_bits> <grid_mult> <tma_mode>".
 void load_tuning(iqs_qaoa* q) {
   const char* path = std::getenv("IQS_AUTOTUNE_CACHE");
   if (path == nullptr) return;
   FILE* f = std::fopen(path, "r");
   if (f == nullptr) return;
   char kind[16], dt[8];
-  int n, bm, rows, mult;
-  while (std::fscanf(f, "%15s %7s %d %d %d %d", kind, dt, &n, &bm, &rows, &mult) == 6) {
+  int n, bm, rows, mult, tma;
+  while (std::fscanf(f, "%15s %7s %d %d %d %d %d", kind, dt, &n, &bm, &rows, &mult, &tma) == 7) {
     if (std::strcmp(kind, "qaoa") == 0 && std::strcmp(dt, dtype_name(q->dtype)) == 0 && n == q->n && bm == q->bmax &&
-        mult >= 1 && mult <= 4) {
+        mult >= 1 && mult <= 4 && tma >= 0 && tma <= 2) {
       q->row_bits = rows;
       q->grid_mult = mult;  // the last matching line wins
+      q->tma_mode = tma;
     }
   }
   std::fclose(f);
@@ -836,7 +1203,8 @@ void save_tuning(const iqs_qaoa* q) {
   if (path == nullptr) return;
   FILE* f = std::fopen(path, "a");
   if (f == nullptr) return;
-  std::fprintf(f, "qaoa %s %d %d %d %d\n", dtype_name(q->dtype), q->n, q->bmax, q->row_bits, q->grid_mult);
+  std::fprintf(f, "qaoa %s %d %d %d %d %d\n", dtype_name(q->dtype), q->n, q->bmax, q->row_bits, q->grid_mult,
+               q->tma_mode);
   std::fclose(f);
 }
 
@@ -852,6 +1220,7 @@ void free_qaoa(iqs_qaoa* q) {
   cudaFree(q->results);
   cudaFree(q->norms);
   cudaFree(q->flag);
+  cudaFree(q->tma_err);
   if (q->host_params) cudaFreeHost(q->host_params);
   if (q->host_results) cudaFreeHost(q->host_results);
   delete q;
@@ -908,6 +1277,7 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
             cudaMalloc(&q->results, sizeof(double) * (size_t)batch_max * (1 + 2 * kMaxP)) == cudaSuccess &&
             cudaMalloc(&q->norms, sizeof(double) * 3 * (size_t)batch_max) == cudaSuccess &&
             cudaMalloc(&q->flag, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&q->tma_err, sizeof(unsigned)) == cudaSuccess &&
             cudaMallocHost(&q->host_params, q->rx_bytes + q->table_bytes) == cudaSuccess &&
             cudaMallocHost(&q->host_results, sizeof(double) * ((size_t)batch_max * (1 + 2 * kMaxP) + 1)) == cudaSuccess;
   if (!ok) {
@@ -929,6 +1299,8 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
   if (e == cudaSuccess) note_launches(1);
   if (e == cudaSuccess) e = cudaMemsetAsync(q->flag, 0, sizeof(unsigned), q->stream);
   if (e == cudaSuccess) e = dtype == IQS_C128 ? set_smem_attrs<T128>() : set_smem_attrs<T64>();
+  if (e == cudaSuccess) e = dtype == IQS_C128 ? set_tma_attrs<T128>() : set_tma_attrs<T64>();
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->tma_err, 0, sizeof(unsigned), q->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
   if (e != cudaSuccess) {
     free_qaoa(q);
@@ -1005,12 +1377,20 @@ iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, con
   note_launches(kernels);
   const int stride = 1 + 2 * kMaxP;
   e = cudaMemcpyAsync(q->host_results, q->results, sizeof(double) * (size_t)batch * stride, cudaMemcpyDeviceToHost, s);
-  unsigned f = 0;
+  unsigned f = 0, terr = 0;
   double* flag_slot = q->host_results + (size_t)q->bmax * stride;
   if (e == cudaSuccess) e = cudaMemcpyAsync(flag_slot, q->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(reinterpret_cast<unsigned*>(flag_slot) + 1, q->tma_err, sizeof(unsigned),
+                        cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return report(IQS_ECUDA, "QAOA results: %s", cudaGetErrorString(e));
   std::memcpy(&f, flag_slot, sizeof(unsigned));
+  std::memcpy(&terr, reinterpret_cast<unsigned*>(flag_slot) + 1, sizeof(unsigned));
+  if (terr) {
+    cudaMemsetAsync(q->tma_err, 0, sizeof(unsigned), s);
+    return report(IQS_ETIMEOUT, "a TMA tile load did not complete within its wait limit; results are invalid");
+  }
   for (int b = 0; b < batch; ++b) {
     const double* r = q->host_results + (size_t)b * stride;
     energies[b] = r[0];
@@ -1042,19 +1422,40 @@ iqs_status iqs_qaoa_autotune(iqs_qaoa* q, int batch, int p, double* best_ms) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return report(IQS_ECUDA, "autotune events");
   iqs_status st = IQS_OK;
+  auto time_one = [&](float* ms) -> iqs_status {
+    replan(q);
+    iqs_status r = iqs_qaoa_run(q, batch, p, g.data(), b.data(), E.data(), dg.data(), db.data());  // warm
+    if (r != IQS_OK) return r;
+    cudaEventRecord(e0, q->stream);
+    r = iqs_qaoa_run(q, batch, p, g.data(), b.data(), E.data(), dg.data(), db.data());
+    cudaEventRecord(e1, q->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    return r;
+  };
+  // 1) TMA staging off / forward / forward + adjoint, at the default shape
+  int best_tma = 0;
+  q->row_bits = rows0;
+  q->grid_mult = 1;
+  for (int tma = 0; tma <= 2 && st == IQS_OK; ++tma) {
+    q->tma_mode = tma;
+    float ms = 0.f;
+    st = time_one(&ms);
+    if (st == IQS_OK && ms < best) {
+      best = ms;
+      best_tma = tma;
+    }
+    if (!q->tma_ok) break;  // no tensor maps here: staging unavailable
+  }
+  q->tma_mode = best_tma;
+  // 2) high-pass row width and grid size with that staging
   for (int rows = rows0; rows <= rows0 + 2 && st == IQS_OK; ++rows) {
     for (int mult = 1; mult <= 2 && st == IQS_OK; ++mult) {
+      if (rows == rows0 && mult == 1) continue;  // measured above
       q->row_bits = rows;
       q->grid_mult = mult;
-      replan(q);
-      st = iqs_qaoa_run(q, batch, p, g.data(), b.data(), E.data(), dg.data(), db.data());  // warm
-      if (st != IQS_OK) break;
-      cudaEventRecord(e0, q->stream);
-      st = iqs_qaoa_run(q, batch, p, g.data(), b.data(), E.data(), dg.data(), db.data());
-      cudaEventRecord(e1, q->stream);
-      cudaEventSynchronize(e1);
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      st = time_one(&ms);
       if (st == IQS_OK && ms < best) {
         best = ms;
         best_rows = rows;
@@ -1071,6 +1472,21 @@ iqs_status iqs_qaoa_autotune(iqs_qaoa* q, int batch, int p, double* best_ms) {
   if (st != IQS_OK) return st;
   save_tuning(q);
   if (best_ms) *best_ms = best;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_set_tma(iqs_qaoa* q, int mode) {
+  if (q == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (mode < 0 || mode > 2) return iqs::report(IQS_EINVAL, "TMA mode must be 0, 1 or 2");
+  q->tma_mode = mode;
+  iqs::replan(q);
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_get_tma(const iqs_qaoa* q, int* mode, int* available) {
+  if (q == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (mode) *mode = q->tma_mode;
+  if (available) *available = q->tma_ok ? 1 : 0;
   return IQS_OK;
 }
 

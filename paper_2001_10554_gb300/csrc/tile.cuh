@@ -38,10 +38,18 @@ __device__ __forceinline__ void block_partial(double v, double* out) {
 
 // Shared-memory index of tile element l: XOR-swizzled within 128-byte rows so
 // that a warp reading a fixed offset of 32 consecutive register blocks (rows
-// of stride 2^kSwzBits elements) hits distinct banks.
+// of stride 2^kSwzBits elements) hits distinct banks.  A traits type may
+// instead define kTmaSwizzle to use the layout of the TMA 128-byte swizzle
+// (16-byte chunk index XOR row index mod 8), so tiles written by TMA can be
+// indexed directly.  Both are linear over GF(2): swz(a ^ b) = swz(a) ^ swz(b).
 template <class TR>
 __device__ __forceinline__ unsigned swz(unsigned l) {
-  return l ^ ((l >> TR::kSwzBits) & ((1u << TR::kSwzBits) - 1u));
+  if constexpr (TR::kTmaSwizzle) {
+    if constexpr (sizeof(typename TR::V) == 8) return l ^ (((l >> 4) & 7u) << 1);  // 8-byte elements
+    else return l ^ ((l >> 3) & 7u);                                             // 16-byte elements
+  } else {
+    return l ^ ((l >> TR::kSwzBits) & ((1u << TR::kSwzBits) - 1u));
+  }
 }
 
 }  // namespace iqs

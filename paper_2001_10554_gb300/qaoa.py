@@ -65,9 +65,14 @@ class QAOA:
         return dict(self.tuning(), best_ms=ms.value)
 
     def tuning(self) -> dict:
-        rows, mult = C.c_int(), C.c_int()
+        rows, mult, tma, avail = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         call("iqs_qaoa_tuning", self._h, C.byref(rows), C.byref(mult))
-        return {"row_bits": rows.value, "grid_mult": mult.value}
+        call("iqs_qaoa_get_tma", self._h, C.byref(tma), C.byref(avail))
+        return {"row_bits": rows.value, "grid_mult": mult.value, "tma_mode": tma.value, "tma_available": bool(avail.value)}
+
+    def set_tma(self, mode: int) -> None:
+        """Stage mixer tiles with TMA: 0 off, 1 forward passes, 2 forward and adjoint passes."""
+        call("iqs_qaoa_set_tma", self._h, int(mode))
 
     def state(self, index: int = 0) -> np.ndarray:
         out = np.empty(1 << self.n, dtype=np.complex128 if self.dtype_code == _lib.IQS_C128 else np.complex64)

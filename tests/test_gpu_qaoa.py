@@ -178,6 +178,7 @@ def test_autotuner_keeps_results_and_persists_choice(gpu_lib, tmp_path):
     E0, dg0, db0 = eng.run(gm, bt)
     choice = eng.autotune(B, p)
     assert 3 <= choice["row_bits"] <= 5 and choice["grid_mult"] in (1, 2) and choice["best_ms"] > 0
+    assert choice["tma_mode"] in (0, 1, 2)
     E1, dg1, db1 = eng.run(gm, bt)
     np.testing.assert_allclose(E1, E0, rtol=0, atol=1e-12)
     np.testing.assert_allclose(dg1, dg0, rtol=0, atol=1e-11)
@@ -197,4 +198,31 @@ def test_autotuner_keeps_results_and_persists_choice(gpu_lib, tmp_path):
     r2 = subprocess.run([sys.executable, "-c", code, "read"], env=env, capture_output=True, text=True, timeout=300)
     assert r2.returncode == 0, r2.stderr
     loaded = json.loads(r2.stdout.strip().splitlines()[-1])
-    assert loaded == {"row_bits": tuned["row_bits"], "grid_mult": tuned["grid_mult"]}
+    assert {k: loaded[k] for k in ("row_bits", "grid_mult", "tma_mode")} == \
+        {k: tuned[k] for k in ("row_bits", "grid_mult", "tma_mode")}
+
+
+@pytest.mark.parametrize("dtype,n", [("complex64", 12), ("complex64", 16), ("complex64", 21),
+                                     ("complex128", 11), ("complex128", 13), ("complex128", 16)])
+def test_qaoa_tma_staged_passes_match(gpu_lib, dtype, n):
+    """TMA-staged mixer tiles (forward only, forward + adjoint) give the same
+    energies and gradients as the register-loaded tiles, and match the oracle."""
+    p, B = 3, 3
+    edges = W.random_3regular_graph(n if n % 2 == 0 else n - 1, 500 + n)
+    gm, bt = W.qaoa_parameter_sets(p, B, 600 + n)
+    eng = gpu_lib.QAOA(n, edges, dtype, batch_max=B)
+    eng.set_tma(0)
+    E0, dg0, db0 = eng.run(gm, bt)
+    for mode in (1, 2):
+        eng.set_tma(mode)
+        assert eng.tuning()["tma_available"] and eng.tuning()["tma_mode"] == mode
+        E, dg, db = eng.run(gm, bt)
+        np.testing.assert_allclose(E, E0, rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(dg, dg0, rtol=1e-9, atol=1e-11)
+        np.testing.assert_allclose(db, db0, rtol=1e-9, atol=1e-11)
+    if n <= 16:
+        Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+        tol_e, tol_g = (1e-11, 1e-9) if dtype == "complex128" else (2e-6, 1e-4)
+        assert np.max(np.abs(E - Eo)) <= tol_e
+        assert np.max(np.abs(dg - dgo)) <= tol_g and np.max(np.abs(db - dbo)) <= tol_g
+    eng.close()
