@@ -111,6 +111,33 @@ def apply_c1q(psi, c: int, t: int, U) -> np.ndarray:
     return out
 
 
+def apply_kq(psi, qubits, U) -> np.ndarray:
+    """A k-qubit gate: the dense 2^k x 2^k matrix U acts on the qubits listed
+    (Section 2, "Scope and basic use": custom multi-qubit gates).  Reading
+    (the paper gives no convention): bit j of U's row and column index is the
+    value of qubit ``qubits[j]``, matching the index convention of the state.
+
+    The state as an n-axis tensor (axis n-1-q holds bit q); the k target axes
+    are moved last, in the order qubits[k-1] .. qubits[0], so that the flattened
+    trailing block index equals U's index; then new = U @ block.
+    """
+    out = _as_state(psi)
+    n = num_qubits(out)
+    qubits = [int(q) for q in qubits]
+    k = len(qubits)
+    if k < 1 or len(set(qubits)) != k or any(not 0 <= q < n for q in qubits):
+        raise ValueError("qubits must be k distinct indices in [0, n)")
+    U = np.asarray(U, dtype=np.complex128).reshape(1 << k, 1 << k)
+    v = out.reshape((2,) * n)
+    axes = [n - 1 - q for q in reversed(qubits)]
+    moved = np.moveaxis(v, axes, list(range(n - k, n)))
+    shape = moved.shape
+    block = moved.reshape(-1, 1 << k)
+    new = block @ U.T
+    moved_new = new.reshape(shape)
+    return np.moveaxis(moved_new, list(range(n - k, n)), axes).reshape(-1).copy()
+
+
 def cut_values(n: int, edges, weights=None) -> np.ndarray:
     """Max-Cut cost diagonal C(x) for every basis state x (Section 4: H_MaxCut
     counts the edges cut by the bipartition; here with optional weights):
@@ -198,6 +225,35 @@ def masks_to_pauli(n: int, xmask: int, zmask: int) -> str:
         xb, zb = (xmask >> k) & 1, (zmask >> k) & 1
         s.append("Y" if xb and zb else "X" if xb else "Z" if zb else "I")
     return "".join(s)
+
+
+def marginal(psi, qubits) -> np.ndarray:
+    """Joint outcome probabilities of a group of qubits (Section 2, "Scope and
+    basic use": measuring qubits in larger groups gives the full statistics of
+    the outcomes): out[m] = sum of |alpha_i|^2 over the indices whose bits at
+    ``qubits[j]`` equal bit j of m."""
+    a = _as_state(psi)
+    n = num_qubits(a)
+    qubits = [int(q) for q in qubits]
+    w = a.real * a.real + a.imag * a.imag
+    out = np.zeros(1 << len(qubits))
+    idx = np.arange(1 << n, dtype=np.uint64)
+    m = np.zeros(1 << n, dtype=np.int64)
+    for j, q in enumerate(qubits):
+        m |= (((idx >> np.uint64(q)) & np.uint64(1)).astype(np.int64) << j)
+    np.add.at(out, m, w)
+    return out
+
+
+def sample(psi, uniforms) -> np.ndarray:
+    """Basis states drawn from |alpha_i|^2 by inverse transform: for each u in
+    [0, 1), the smallest i with u * sum_j |alpha_j|^2 < sum_{j <= i} |alpha_j|^2
+    (the sampling counterpart of measuring all qubits; the uniforms are inputs)."""
+    a = _as_state(psi)
+    w = a.real * a.real + a.imag * a.imag
+    cdf = np.cumsum(w)
+    u = np.asarray(uniforms, dtype=np.float64) * cdf[-1]
+    return np.minimum(np.searchsorted(cdf, u, side="right"), len(w) - 1)
 
 
 def norm2(psi) -> float:

@@ -407,3 +407,60 @@ def test_noise_ensemble_converges_to_channel():
 def test_pool_average_is_sum_over_count():
     v = np.array([[1.0, 2.0], [3.0, 6.0], [5.0, 1.0]])
     np.testing.assert_array_equal(oe.pool_average(v), np.array([3.0, 3.0]))
+
+
+# ---------------------------------------------------------------- k-qubit blocks, groups, sampling
+def test_apply_kq_equals_kronecker_of_one_qubit_gates():
+    """U = kron(U1, U0) on (q0, q1) (bit 0 of U's index = qubits[0]) equals
+    applying U0 on q0 and U1 on q1."""
+    g = W.rng(401)
+    n = 6
+    for q0, q1 in [(0, 1), (4, 2), (5, 0)]:
+        U0, U1 = W.haar_u2(g), W.haar_u2(g)
+        psi = rand_state(n, g)
+        ref = sv.apply_1q(sv.apply_1q(psi, q0, U0), q1, U1)
+        np.testing.assert_allclose(sv.apply_kq(psi, [q0, q1], np.kron(U1, U0)), ref, rtol=0, atol=1e-13)
+
+
+def test_apply_kq_controlled_gate_and_full_matrix():
+    g = W.rng(402)
+    n = 5
+    U = W.haar_u2(g)
+    psi = rand_state(n, g)
+    # controlled-U with control = qubits[0], target = qubits[1]: |0><0| x I + |1><1| x U in U's index order
+    CU = np.zeros((4, 4), dtype=np.complex128)
+    CU[0, 0] = CU[2, 2] = 1.0                    # control bit (bit 0) = 0
+    CU[np.ix_([1, 3], [1, 3])] = U               # control bit = 1, target bit (bit 1) indexes U
+    np.testing.assert_allclose(sv.apply_kq(psi, [3, 1], CU), sv.apply_c1q(psi, 3, 1, U), rtol=0, atol=1e-13)
+    # a random 3-qubit block against the dense operator built index by index
+    qs = [4, 0, 2]
+    M = np.linalg.qr(g.standard_normal((8, 8)) + 1j * g.standard_normal((8, 8)))[0]
+    full = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    for col in range(1 << n):
+        cb = sum(((col >> q) & 1) << j for j, q in enumerate(qs))
+        rest = col & ~sum(1 << q for q in qs)
+        for rb in range(8):
+            row = rest | sum(((rb >> j) & 1) << q for j, q in enumerate(qs))
+            full[row, col] = M[rb, cb]
+    np.testing.assert_allclose(sv.apply_kq(psi, qs, M), full @ psi, rtol=0, atol=1e-13)
+
+
+def test_marginal_and_sampling():
+    g = W.rng(403)
+    n = 7
+    psi = rand_state(n, g)
+    qs = [5, 1, 2]
+    m = sv.marginal(psi, qs)
+    assert abs(m.sum() - 1.0) < 1e-14
+    for q in range(n):                          # single-qubit marginals are GetProbability
+        assert abs(sv.marginal(psi, [q])[1] - sv.probability(psi, q)) < 1e-14
+    brute = np.zeros(8)
+    for i in range(1 << n):
+        brute[((i >> 5) & 1) | (((i >> 1) & 1) << 1) | (((i >> 2) & 1) << 2)] += abs(psi[i]) ** 2
+    np.testing.assert_allclose(m, brute, rtol=0, atol=1e-14)
+    # inverse-transform sampling: basis states sample themselves; frequencies follow |psi|^2
+    assert np.all(sv.sample(sv.basis_state(n, 37), g.uniform(size=50)) == 37)
+    u = g.uniform(size=200000)
+    counts = np.bincount(sv.sample(psi, u), minlength=1 << n) / len(u)
+    w = np.abs(psi) ** 2
+    assert np.all(np.abs(counts - w) < 5 * np.sqrt(w * (1 - w) / len(u)) + 1e-12)
