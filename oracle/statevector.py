@@ -248,12 +248,20 @@ def marginal(psi, qubits) -> np.ndarray:
 def sample(psi, uniforms) -> np.ndarray:
     """Basis states drawn from |alpha_i|^2 by inverse transform: for each u in
     [0, 1), the smallest i with u * sum_j |alpha_j|^2 < sum_{j <= i} |alpha_j|^2
-    (the sampling counterpart of measuring all qubits; the uniforms are inputs)."""
+    (the sampling counterpart of measuring all qubits; the uniforms are inputs).
+
+    Reading: an outcome of probability zero never occurs (Section 2: outcome i
+    has probability |alpha_i|^2), so where rounding puts u * total at or above
+    the last cumulative value the draw is the last index of nonzero weight."""
     a = _as_state(psi)
     w = a.real * a.real + a.imag * a.imag
     cdf = np.cumsum(w)
+    if not cdf[-1] > 0:
+        raise ValueError("a state of zero weight has no outcomes")
     u = np.asarray(uniforms, dtype=np.float64) * cdf[-1]
-    return np.minimum(np.searchsorted(cdf, u, side="right"), len(w) - 1)
+    idx = np.searchsorted(cdf, u, side="right")
+    last = int(np.flatnonzero(w)[-1])
+    return np.where(idx >= len(w), last, idx).astype(np.int64)
 
 
 def norm2(psi) -> float:

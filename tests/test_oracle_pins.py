@@ -464,3 +464,27 @@ def test_marginal_and_sampling():
     counts = np.bincount(sv.sample(psi, u), minlength=1 << n) / len(u)
     w = np.abs(psi) ** 2
     assert np.all(np.abs(counts - w) < 5 * np.sqrt(w * (1 - w) / len(u)) + 1e-12)
+
+
+def test_sampling_never_draws_zero_weight_outcomes():
+    """Outcome i occurs with probability |alpha_i|^2 (Section 2), so indices of
+    zero weight are never drawn: not inside the state, not in a zero tail
+    reached through rounding (u next to 1), and u = 0 gives the first nonzero."""
+    g = W.rng(404)
+    n = 9
+    psi = rand_state(n, g)
+    psi[g.uniform(size=1 << n) < 0.8] = 0           # sparse: most weights zero
+    psi[-37:] = 0                                    # zero tail
+    w = np.abs(psi) ** 2
+    u = np.concatenate([g.uniform(size=20000), [0.0, np.nextafter(1.0, 0.0)]])
+    s = sv.sample(psi, u)
+    assert np.all(w[s] > 0)
+    nz = np.flatnonzero(w)
+    assert s[-2] == nz[0] and s[-1] == nz[-1]
+    # inverse transform brute force: the draw is the i with cdf[i-1] <= u*S < cdf[i]
+    cdf = np.concatenate([[0.0], np.cumsum(w)])
+    t = u[:-1] * cdf[-1]
+    for ti, si in zip(t[:2000], s[:2000]):
+        assert cdf[si] <= ti < cdf[si + 1]
+    with pytest.raises(ValueError):
+        sv.sample(np.zeros(8, complex), [0.5])
