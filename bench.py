@@ -276,6 +276,64 @@ def sweep_c64(iqs, torch, dev, n: int, steps: int, warmup: int):
             "error_bound": "FP32 gate arithmetic: <= 8 * 2^-24 per gate on unit-norm states (tests/test_gpu_parity.py)"}
 
 
+def kq_measure_section(iqs, torch, dev):
+    """Dense k-qubit gates, qubit-group marginals and sampling at the sweep's
+    state sizes (30-qubit complex128, 32-qubit complex64): average launch time
+    by CUDA events on the register's stream over 3 calls after 1 warm-up, and
+    GB/s of the algorithmic bytes (a gate reads and writes the state once, a
+    marginal reads it once, a sampling call reads it once plus one run of 256
+    amplitudes per shot)."""
+    import workloads as W
+    out = {"workload": "apply_kq (Haar 2^k x 2^k) on the lowest and highest k qubits, "
+                       "10-qubit marginal, 2^20-shot sampling"}
+    g = W.rng(77)
+    for n, dt, name, ks in ((30, torch.complex128, "c128_30q", (2, 3, 4)), (32, torch.complex64, "c64_32q", (2, 3, 4, 5))):
+        N = 1 << n
+        amp = 16 if dt == torch.complex128 else 8
+        stream = torch.cuda.Stream(dev)
+        with torch.cuda.stream(stream):
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(SEED_STATE)
+            st = torch.empty(N, dtype=dt, device=dev)
+            st.view(torch.float64 if amp == 16 else torch.float32).normal_(generator=gen)
+            st.div_(torch.linalg.vector_norm(st))
+        stream.synchronize()
+        reg = iqs.Register.wrap(st, stream=stream)
+
+        def timed(fn, reps=3):
+            fn()
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b) / reps
+
+        rows = []
+        for k in ks:
+            U = np.linalg.qr(g.normal(size=(1 << k, 1 << k)) + 1j * g.normal(size=(1 << k, 1 << k)))[0]
+            for where, qs in (("low", list(range(k))), ("high", list(range(n - k, n)))):
+                ms = timed(lambda: reg.apply_kq(qs, U))
+                rows.append({"k": k, "targets": where, "ms": round(ms, 3),
+                             "GBs": round(2 * amp * N / (ms * 1e-3) / 1e9, 1)})
+        out[name] = {"apply_kq": rows}
+        qs10 = [0, 3, 7, 9, 12, 15, 20, 24, n - 2, n - 1]
+        ms = timed(lambda: reg.marginal(qs10))
+        out[name]["marginal_10q"] = {"ms": round(ms, 3), "GBs": round(amp * N / (ms * 1e-3) / 1e9, 1)}
+        shots = 1 << 20
+        u = g.uniform(size=shots)
+        ms = timed(lambda: reg.sample(u))
+        out[name]["sample_2p20"] = {"ms": round(ms, 3), "GBs_state_pass": round(amp * N / (ms * 1e-3) / 1e9, 1),
+                                    "shots_per_s": round(shots / (ms * 1e-3), 1),
+                                    "note": "includes the 8 MiB uniform upload and the 8 MiB index download"}
+        reg.close()
+        del st
+        torch.cuda.empty_cache()
+    return out
+
+
 def qaoa_section(iqs, torch):
     """Batched complex64 QAOA energy + adjoint gradient (256 parameter sets per
     graph, one engine call) against the plain complex128 path (one parameter
@@ -533,6 +591,7 @@ def main(argv=None):
     extra = {}
     if not args.no_extra:
         extra["c64_32q"] = sweep_c64(iqs, torch, dev, 32, steps=3, warmup=2)
+        extra["kq_measure"] = kq_measure_section(iqs, torch, dev)
         extra["qaoa"] = qaoa_section(iqs, torch)
         extra["noise_ensemble"] = ensemble_section(iqs, torch)
 

@@ -137,6 +137,15 @@ iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]);
 iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges,
                               const double* weights, double gamma);
 
+/* Section 2 "Scope and basic use": custom gates on several qubits.  A dense
+ * 2^k x 2^k matrix U acts on qubits[0..k); bit j of U's row and column index
+ * is the value of qubits[j].  ``U`` is row-major, (re, im) doubles: entry
+ * (row, col) at U[2 * (row * 2^k + col)].  k: 1..5 for IQS_C64 (computed in
+ * FP32), 1..4 for IQS_C128 (double-float emulation or native FP64 as for
+ * iqs_apply_1q).  The qubits must be distinct and in [0, n); U must be
+ * finite.  IQS_EINVAL otherwise, with the state untouched.  Asynchronous. */
+iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U);
+
 /* ------------------------------------------------------------ reductions (FP64 results, synchronous) */
 
 /* Section 2 "Scope and basic use", GetProbability(q): sum of |alpha_i|^2 over
@@ -154,6 +163,25 @@ iqs_status iqs_expectation(iqs_reg* reg, const char* pauli, double* out);
 /* The same by bit masks: bit k of ``xmask`` and ``zmask`` marks an X (x only),
  * Z (z only) or Y (both) on qubit k.  Bits at or above n must be zero. */
 iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, double* out);
+
+/* Section 2 "Scope and basic use": measuring qubits in groups gives the joint
+ * statistics of their outcomes.  out[m] (m in [0, 2^k)) = sum of |alpha_i|^2
+ * over the indices whose bit qubits[j] equals bit j of m; raw sums, not
+ * divided by the norm.  k: 1..min(n, 10), distinct qubits; ``out`` is a host
+ * array of 2^k doubles.  Temporary device memory (about 8 x 2^k x 608
+ * bytes) is taken from the stream-ordered allocator and returned. */
+iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out);
+
+/* Sampling counterpart of measuring all qubits: for each of ``shots`` host
+ * uniforms u in [0, 1), out[s] = the first index i whose cumulative weight
+ * sum_{j <= i} |alpha_j|^2 exceeds u times the total weight (a zero-weight
+ * index is never returned: where rounding leaves u * total at or above the
+ * last cumulative value, the last index of nonzero weight).  Cumulative
+ * weights are FP64; their rounding order (runs of 256 amplitudes, chunks of
+ * 256 runs) differs from a sequential sum only by rounding.  IQS_EINVAL for a
+ * u outside [0, 1), NULL arrays, or a state of zero weight.  Temporary
+ * device memory: N / 256 + 2 N / 65536 doubles plus 16 bytes per shot. */
+iqs_status iqs_sample(iqs_reg* reg, uint64_t shots, const double* uniforms, uint64_t* out);
 
 /* Squared norm sum_i |alpha_i|^2. */
 iqs_status iqs_norm2(iqs_reg* reg, double* out);

@@ -50,6 +50,9 @@ SIGNATURES = {
     "iqs_apply_1q": ([_reg, C.c_int, _dp], C.c_int),
     "iqs_apply_c1q": ([_reg, C.c_int, C.c_int, _dp], C.c_int),
     "iqs_apply_zz_phase": ([_reg, C.c_int, _i32p, _dp, C.c_double], C.c_int),
+    "iqs_apply_kq": ([_reg, C.c_int, C.POINTER(C.c_int), _dp], C.c_int),
+    "iqs_marginal": ([_reg, C.c_int, C.POINTER(C.c_int), _dp], C.c_int),
+    "iqs_sample": ([_reg, C.c_uint64, _dp, C.POINTER(C.c_uint64)], C.c_int),
     "iqs_probability": ([_reg, C.c_int, _dp], C.c_int),
     "iqs_probabilities": ([_reg, _dp], C.c_int),
     "iqs_expectation": ([_reg, C.c_char_p, _dp], C.c_int),

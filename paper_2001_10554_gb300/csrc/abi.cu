@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 
@@ -187,6 +188,44 @@ iqs_status check_edges(const iqs_reg* r, int n_edges, const int32_t* edges) {
   }
   return IQS_OK;
 }
+
+// k distinct qubits in [0, n).
+iqs_status check_qubit_set(const iqs_reg* r, int k, const int* qubits) {
+  uint64_t seen = 0;
+  for (int j = 0; j < k; ++j) {
+    const int q = qubits[j];
+    if (q < 0 || q >= r->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, r->n);
+    if ((seen >> q) & 1ull) return fail(IQS_EINVAL, "qubit %d listed twice", q);
+    seen |= 1ull << q;
+  }
+  return IQS_OK;
+}
+
+// Temporary device memory from the stream-ordered allocator, returned on the
+// same stream (release(), or the destructor on an early error return).
+struct DeviceScratch {
+  cudaStream_t stream;
+  void* ptr = nullptr;
+  explicit DeviceScratch(cudaStream_t s) : stream(s) {}
+  iqs_status get(size_t bytes) {
+    if (iqs::fault_now(1)) return fail(IQS_ENOMEM, "injected allocation failure");
+    if (cudaMallocAsync(&ptr, bytes < 16 ? 16 : bytes, stream) != cudaSuccess) {
+      cudaGetLastError();
+      ptr = nullptr;
+      return fail(IQS_ENOMEM, "cannot allocate %zu bytes of scratch", bytes);
+    }
+    return IQS_OK;
+  }
+  iqs_status release() {
+    if (ptr == nullptr) return IQS_OK;
+    const cudaError_t e = cudaFreeAsync(ptr, stream);
+    ptr = nullptr;
+    return e == cudaSuccess ? IQS_OK : cuda_fail(e, "free scratch");
+  }
+  ~DeviceScratch() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+  }
+};
 
 }  // namespace
 
@@ -404,6 +443,64 @@ iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges, co
   }
   *out = total;
   return check_flag(reg);
+}
+
+iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U) {
+  CHECK_REG(reg);
+  if (U == nullptr || qubits == nullptr) return fail(IQS_EINVAL, "qubits or U is NULL");
+  const int kmax = iqs::max_kq(reg->dtype);
+  if (k < 1 || k > kmax || k > reg->n) return fail(IQS_EINVAL, "k = %d outside [1, %d] for this register", k, kmax);
+  iqs_status s = check_qubit_set(reg, k, qubits);
+  if (s != IQS_OK) return s;
+  const int entries = 2 << (2 * k);
+  for (int i = 0; i < entries; ++i)
+    if (!std::isfinite(U[i])) return fail(IQS_EINVAL, "U entry %d is not finite", i / 2);
+  LAUNCH_TRY(iqs::launch_kq(reg, k, qubits, U), "apply_kq");
+  return IQS_OK;
+}
+
+iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out) {
+  CHECK_REG(reg);
+  if (qubits == nullptr || out == nullptr) return fail(IQS_EINVAL, "qubits or out is NULL");
+  const int kmax = std::min(reg->n, iqs::max_marginal_qubits());
+  if (k < 1 || k > kmax) return fail(IQS_EINVAL, "k = %d outside [1, %d]", k, kmax);
+  iqs_status s = check_qubit_set(reg, k, qubits);
+  if (s != IQS_OK) return s;
+  const size_t outs = (size_t)1 << k;
+  const size_t pbytes = iqs::marginal_scratch_bytes(reg, k, qubits);
+  DeviceScratch mem(reg->stream);
+  if ((s = mem.get(sizeof(double) * outs + pbytes)) != IQS_OK) return s;
+  double* out_dev = (double*)mem.ptr;
+  double* partials = out_dev + outs;
+  LAUNCH_TRY(iqs::launch_marginal(reg, k, qubits, out_dev, partials), "marginal");
+  CUDA_TRY(cudaMemcpyAsync(out, out_dev, sizeof(double) * outs, cudaMemcpyDeviceToHost, reg->stream), "copy marginal");
+  if ((s = mem.release()) != IQS_OK) return s;
+  CUDA_TRY(cudaStreamSynchronize(reg->stream), "synchronise");
+  return check_flag(reg);
+}
+
+iqs_status iqs_sample(iqs_reg* reg, uint64_t shots, const double* uniforms, uint64_t* out) {
+  CHECK_REG(reg);
+  if (shots == 0) return IQS_OK;
+  if (uniforms == nullptr || out == nullptr) return fail(IQS_EINVAL, "uniforms or out is NULL");
+  if (shots > (1ull << 32)) return fail(IQS_EINVAL, "at most 2^32 shots per call");
+  for (uint64_t s = 0; s < shots; ++s)
+    if (!(uniforms[s] >= 0.0 && uniforms[s] < 1.0)) return fail(IQS_EINVAL, "uniform %llu outside [0, 1)", (unsigned long long)s);
+  const size_t sbytes = iqs::sample_scratch_bytes(reg->n);
+  DeviceScratch mem(reg->stream);
+  iqs_status st = mem.get(sbytes + 16 * (size_t)shots);
+  if (st != IQS_OK) return st;
+  double* scratch = (double*)mem.ptr;
+  double* u_dev = (double*)((char*)mem.ptr + sbytes);
+  unsigned long long* out_dev = (unsigned long long*)(u_dev + shots);
+  CUDA_TRY(cudaMemcpyAsync(u_dev, uniforms, sizeof(double) * shots, cudaMemcpyHostToDevice, reg->stream), "copy uniforms");
+  LAUNCH_TRY(iqs::launch_sample(reg, shots, u_dev, out_dev, scratch), "sample");
+  CUDA_TRY(cudaMemcpyAsync(out, out_dev, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, reg->stream), "copy samples");
+  if ((st = mem.release()) != IQS_OK) return st;
+  CUDA_TRY(cudaStreamSynchronize(reg->stream), "synchronise");
+  if ((st = check_flag(reg)) != IQS_OK) return st;
+  if (out[0] == ~0ull) return fail(IQS_EINVAL, "cannot sample a state of zero weight");
+  return IQS_OK;
 }
 
 const char* iqs_last_error(void) { return g_err; }

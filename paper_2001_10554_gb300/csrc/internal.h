@@ -80,6 +80,18 @@ cudaError_t launch_energy(iqs_reg* r, int n_edges, const int32_t* edges, const d
 cudaError_t launch_probabilities_raw(const void* data, int n, int dtype, cudaStream_t s, double* partials,
                                      double* results, unsigned* flag);
 
+// ---- kgate.cu: dense k-qubit gates (k <= max_kq(dtype))
+int max_kq(int dtype);
+cudaError_t launch_kq(iqs_reg* r, int k, const int* qubits, const double* U);
+
+// ---- measure.cu: qubit-group marginals and sampling
+int max_marginal_qubits();
+size_t marginal_scratch_bytes(const iqs_reg* r, int k, const int* qubits);
+cudaError_t launch_marginal(iqs_reg* r, int k, const int* qubits, double* out_dev, double* partials);
+size_t sample_scratch_bytes(int n);
+cudaError_t launch_sample(iqs_reg* r, uint64_t shots, const double* u_dev, unsigned long long* out_dev,
+                          double* scratch);
+
 // ---- abi.cu: record a failure message for iqs_last_error() and return ``s``.
 iqs_status report(iqs_status s, const char* fmt, ...);
 // True (once) when an injected fault of ``kind`` (1 allocation, 2 launch) fires.

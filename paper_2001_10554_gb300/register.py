@@ -179,6 +179,14 @@ class Register:
         _e, _w, m, ep, wp = _edges(edges, weights)
         call("iqs_apply_zz_phase", self._h, m, ep, wp, C.c_double(float(gamma)))
 
+    def apply_kq(self, qubits, U) -> None:
+        """Dense 2^k x 2^k gate on ``qubits``; bit j of U's index = qubits[j]."""
+        qs = [int(q) for q in qubits]
+        k = len(qs)
+        u = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).reshape(1 << k, 1 << k))
+        buf = u.view(np.float64).reshape(-1)
+        call("iqs_apply_kq", self._h, k, (C.c_int * k)(*qs), buf.ctypes.data_as(C.POINTER(C.c_double)))
+
     # ------------------------------------------------------------ reductions
     def probability(self, q: int) -> float:
         out = C.c_double()
@@ -199,6 +207,22 @@ class Register:
         out = C.c_double()
         call("iqs_expectation_masks", self._h, C.c_uint64(xmask), C.c_uint64(zmask), C.byref(out))
         return out.value
+
+    def marginal(self, qubits) -> np.ndarray:
+        """Joint outcome probabilities of ``qubits``: out[m], bit j of m = qubits[j]."""
+        qs = [int(q) for q in qubits]
+        k = len(qs)
+        out = np.zeros(1 << k, dtype=np.float64)
+        call("iqs_marginal", self._h, k, (C.c_int * k)(*qs), out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def sample(self, uniforms) -> np.ndarray:
+        """Basis-state indices drawn by inverse transform with the given uniforms in [0, 1)."""
+        u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64).reshape(-1))
+        out = np.zeros(u.size, dtype=np.uint64)
+        call("iqs_sample", self._h, C.c_uint64(u.size), u.ctypes.data_as(C.POINTER(C.c_double)),
+             out.ctypes.data_as(C.POINTER(C.c_uint64)))
+        return out
 
     def norm2(self) -> float:
         out = C.c_double()

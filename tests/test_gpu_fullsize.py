@@ -1,0 +1,276 @@
+"""Full-size parity in the launch configuration the benchmark times.
+
+The 30-qubit complex128 state (16 GiB) is generated on the device from a
+seeded torch generator, normalised, and wrapped with Register.wrap on a side
+stream (math mode "auto", which is the double-float emulation at this size),
+exactly as the benchmark's gate sweep does.  Outputs too large for the oracle
+are checked on samples the oracle computes one by one:
+
+* gates: 4096 random pairs (one-qubit gates), index sets (CNOT) or 2^k-groups
+  (dense k-qubit gates) are gathered before and after the call, and the
+  oracle's pair update / k-qubit gate on the gathered amplitudes gives the
+  expected outputs (1e-12; CNOT bit-exact);
+* reductions: on a product state (Haar one-qubit gates on |0...0>) every
+  probability, qubit-group marginal, Pauli expectation and amplitude is a
+  product of one-qubit oracle results, so the full-size values are checked
+  against the oracle (1e-12); on the Gaussian state, properties that hold at
+  any size (norm conservation, marginals summing to the norm, marginal vs
+  GetProbability);
+* sampling: on the product state each draw's cumulative weight has a closed
+  form, so every draw is checked to bracket u * total (1e-12) with nonzero
+  weight;
+* the 32-qubit complex64 sweep state (32 GiB) on sampled pairs, with the FP32
+  bound of the other parity tests;
+* the QAOA rows (n = 24, p = 4, 256 sets; sampled sets against the oracle),
+  the 28-qubit adjoint (gradient against central differences of the
+  complex128 engine's energies) and the noise ensemble (16 qubits, sampled
+  trajectories against the oracle).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ensemble as oe
+from oracle import qaoa as oq
+from oracle import statevector as sv
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+C64_GATE = 8 * 2.0 ** -24
+
+
+def insert_zero(k, q):
+    k = np.asarray(k, dtype=np.int64)
+    return ((k >> q) << (q + 1)) | (k & ((1 << q) - 1))
+
+
+def device_state(n, seed, dtype, dev, stream):
+    with torch.cuda.stream(stream):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        st = torch.empty(1 << n, dtype=dtype, device=dev)
+        st.view(torch.float64 if dtype == torch.complex128 else torch.float32).normal_(generator=gen)
+        st.div_(torch.linalg.vector_norm(st))
+    stream.synchronize()
+    return st
+
+
+def gather(st, idx):
+    return st[torch.as_tensor(idx, device=st.device)].cpu().numpy().astype(np.complex128)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda", 0)
+
+
+def test_sweep_gates_30q_c128_sampled(gpu_lib, dev):
+    n, N = 30, 1 << 30
+    g = W.rng(5001)
+    stream = torch.cuda.Stream(dev)
+    st = device_state(n, 5002, torch.complex128, dev, stream)
+    reg = gpu_lib.Register.wrap(st, stream=stream)
+    norm0 = reg.norm2()
+    for q in (0, 1, 2, 13, 28, 29):
+        U = W.haar_u2(g)
+        k = g.integers(0, N // 2, size=4096)
+        i0 = insert_zero(k, q)
+        i1 = i0 | (1 << q)
+        a0, a1 = gather(st, i0), gather(st, i1)
+        reg.apply_1q(q, U)
+        reg.synchronize()
+        e0, e1 = sv.pair_update(a0, a1, U)
+        assert np.max(np.abs(gather(st, i0) - e0)) <= 1e-12, q
+        assert np.max(np.abs(gather(st, i1) - e1)) <= 1e-12, q
+    X = np.array([[0, 1], [1, 0]])
+    for c, t in ((0, 29), (29, 0), (5, 6), (17, 3)):
+        idx = g.integers(0, N, size=4096)
+        src = np.where((idx >> c) & 1, idx ^ (1 << t), idx)
+        before = gather(st, src)
+        reg.apply_c1q(c, t, X)
+        reg.synchronize()
+        np.testing.assert_array_equal(gather(st, idx), before)
+    for qs in ([0, 1, 2, 3], [29, 3, 17, 8], [5, 28]):
+        k = len(qs)
+        U = np.linalg.qr(g.normal(size=(1 << k, 1 << k)) + 1j * g.normal(size=(1 << k, 1 << k)))[0]
+        free = [q for q in range(n) if q not in qs]
+        gi = g.integers(0, 1 << (n - k), size=1024)
+        base = np.zeros_like(gi)
+        for j, q in enumerate(free):
+            base |= ((gi >> j) & 1) << q
+        off = np.array([sum(((c >> j) & 1) << q for j, q in enumerate(qs)) for c in range(1 << k)])
+        idx = (base[:, None] | off[None, :]).reshape(-1)
+        x = gather(st, idx).reshape(-1, 1 << k)
+        reg.apply_kq(qs, U)
+        reg.synchronize()
+        y = gather(st, idx).reshape(-1, 1 << k)
+        expect = np.array([sv.apply_kq(row, list(range(k)), U) for row in x])
+        assert np.max(np.abs(y - expect)) <= 1e-12, qs
+    # properties at full size
+    assert abs(reg.norm2() - norm0) <= 1e-12
+    P = reg.probabilities()
+    for q in (0, 9, 29):
+        m = reg.marginal([q])
+        assert abs(m[1] - P[q]) <= 1e-13
+    m10 = reg.marginal([29, 0, 7, 3, 18, 22, 1, 11, 26, 5])
+    assert abs(m10.sum() - reg.norm2()) <= 1e-12
+    reg.close()
+    del st
+    torch.cuda.empty_cache()
+
+
+def test_product_state_30q_c128_reductions_and_sampling(gpu_lib, dev):
+    n, N = 30, 1 << 30
+    g = W.rng(5101)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        st = torch.empty(N, dtype=torch.complex128, device=dev)
+    stream.synchronize()
+    reg = gpu_lib.Register.wrap(st, stream=stream)
+    reg.init_basis(0)
+    b = []
+    for q in range(n):
+        U = W.haar_u2(g)
+        reg.apply_1q(q, U)
+        b.append(sv.apply_1q(sv.basis_state(1, 0), 0, U))   # qubit q's one-qubit state
+    b = np.array(b)
+    w = np.abs(b) ** 2                                         # w[q, bit]
+    # probabilities
+    P = reg.probabilities()
+    np.testing.assert_allclose(P, w[:, 1], rtol=0, atol=1e-12)
+    # qubit-group marginals: kron of the one-qubit states in the group's order
+    for qs in ([3], [0, 29], [5, 1, 17], [29, 28, 27, 0, 1, 2, 14, 15, 9, 21]):
+        small = np.array([1.0 + 0j])
+        for q in qs:
+            small = np.kron(b[q], small)                     # bit j of the small index = qs[j]
+        ref = sv.marginal(small, list(range(len(qs))))
+        assert np.max(np.abs(reg.marginal(qs) - ref)) <= 1e-12, qs
+    # Pauli expectations: products of one-qubit expectations
+    for pauli in ("Z" * n, "XYZI" * 7 + "XY", "I" * 12 + "Y" + "I" * 17):
+        ref = 1.0
+        for q, ch in enumerate(pauli):
+            ref *= sv.expectation(b[q], ch).real
+        assert abs(reg.expectation(pauli) - ref) <= 1e-12, pauli
+    # sampled amplitudes
+    idx = g.integers(0, N, size=4096)
+    amp = np.ones(len(idx), dtype=np.complex128)
+    for q in range(n):
+        amp *= b[q][(idx >> q) & 1]
+    assert np.max(np.abs(gather(st, idx) - amp)) <= 1e-12
+    # sampling: F(i) = sum_{j <= i} w(j) for a product state, scanning bits from the top
+    u = g.uniform(size=20000)
+    s = reg.sample(u).astype(np.int64)
+    total = reg.norm2()
+
+    def cdf_incl(i):
+        acc, pre = 0.0, 1.0
+        for q in range(n - 1, -1, -1):
+            bit = (i >> q) & 1
+            if bit:
+                acc += pre * w[q, 0]
+            pre *= w[q, bit]
+        return acc + pre, pre
+
+    for ui, si in zip(u, s):
+        F, wi = cdf_incl(int(si))
+        assert wi > 0
+        assert F - wi - 1e-12 <= ui * total <= F + 1e-12
+    reg.close()
+    del st
+    torch.cuda.empty_cache()
+
+
+def test_sweep_gate_32q_c64_sampled(gpu_lib, dev):
+    n, N = 32, 1 << 32
+    g = W.rng(5201)
+    stream = torch.cuda.Stream(dev)
+    st = device_state(n, 5202, torch.complex64, dev, stream)
+    reg = gpu_lib.Register.wrap(st, stream=stream)
+    for q in (0, 1, 16, 31):
+        U = W.haar_u2(g)
+        k = g.integers(0, N // 2, size=4096)
+        i0 = insert_zero(k, q)
+        i1 = i0 | (1 << q)
+        a0, a1 = gather(st, i0), gather(st, i1)
+        reg.apply_1q(q, U)
+        reg.synchronize()
+        Ur = U.astype(np.complex64).astype(np.complex128)
+        e0, e1 = sv.pair_update(a0, a1, Ur)
+        scale = np.maximum(np.abs(a0), np.abs(a1))
+        assert np.all(np.abs(gather(st, i0) - e0) <= C64_GATE * 2 * scale + 1e-30), q
+        assert np.all(np.abs(gather(st, i1) - e1) <= C64_GATE * 2 * scale + 1e-30), q
+    m = reg.marginal([31, 0, 16])
+    assert abs(m.sum() - reg.norm2()) <= 1e-12
+    reg.close()
+    del st
+    torch.cuda.empty_cache()
+
+
+def test_qaoa_rows_full_size_sampled(gpu_lib):
+    """n = 24, p = 4, 256 parameter sets in one call (the benchmark's row); two
+    sampled sets against the oracle: energy within 2e-6 (complex64 engine with
+    FP64-equivalent reductions) and gradient within 1e-4 + 1e-4 |g|."""
+    n, p, B = 24, 4, 256
+    edges = W.random_3regular_graph(n, 1000 + n)
+    gm, bt = W.qaoa_parameter_sets(p, B, 2000 + n)
+    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=B)
+    E, dg, db = eng.run(gm, bt)
+    eng.close()
+    Eo = oq.qaoa_energy(n, edges, gm[0], bt[0])
+    assert abs(E[0] - Eo) <= 2e-6
+    Eo, go, bo = oq.qaoa_energy_grad_stored(n, edges, gm[173], bt[173])
+    assert abs(E[173] - Eo) <= 2e-6
+    assert np.all(np.abs(dg[173] - go) <= 1e-4 + 1e-4 * np.abs(go))
+    assert np.all(np.abs(db[173] - bo) <= 1e-4 + 1e-4 * np.abs(bo))
+    assert np.all((E >= -1e-9) & (E <= len(edges) + 1e-9))     # 0 <= <C> <= |E|
+    torch.cuda.empty_cache()
+
+
+def test_adjoint_28q_gradient_vs_central_differences(gpu_lib):
+    """The 28-qubit adjoint row (complex64, renormalised every 2 layers): its
+    gradient against central differences of the complex128 engine's energies."""
+    n = 28
+    edges = W.random_3regular_graph(n, 28)
+    gm, bt = W.qaoa_parameter_sets(4, 1, 29)
+    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=1, renorm_every=2)
+    E, dg, db = eng.run(gm, bt)
+    eng.close()
+    torch.cuda.empty_cache()
+    ref = gpu_lib.QAOA(n, edges, "complex128", batch_max=1)
+    E128 = ref.run(gm, bt)[0][0]
+    assert abs(E[0] - E128) <= 1e-5
+    h = 1e-4
+    for which, arr, grad in (("g", gm, dg), ("b", bt, db)):
+        for l in (0, 3):
+            plus, minus = arr.copy(), arr.copy()
+            plus[0, l] += h
+            minus[0, l] -= h
+            if which == "g":
+                fd = (ref.run(plus, bt)[0][0] - ref.run(minus, bt)[0][0]) / (2 * h)
+            else:
+                fd = (ref.run(gm, plus)[0][0] - ref.run(gm, minus)[0][0]) / (2 * h)
+            assert abs(grad[0, l] - fd) <= 1e-4 + 1e-4 * abs(fd), (which, l)
+    ref.close()
+    torch.cuda.empty_cache()
+
+
+def test_noise_ensemble_full_size_sampled(gpu_lib):
+    """The benchmark's ensemble (16 qubits, 500 trajectories per circuit, depth
+    40..120): sampled trajectories of two circuits against the oracle, and the
+    pool mean against the mean of the per-trajectory probabilities."""
+    from paper_2001_10554_gb300.pool import brick_unitaries
+    n, traj = 16, 500
+    ens = W.noise_ensemble(n=n, circuits=8, trajectories=traj, seed=4242)
+    for ci in (0, 5):
+        c = ens[ci]
+        U = brick_unitaries(c["ops"], n)
+        pool = gpu_lib.Pool(n, "complex128", batch_max=traj, depth_max=c["depth"])
+        probs, mean = pool.run_brick(U, c["angles"])
+        for t in (0, traj - 1):
+            ref = oe.all_probabilities(oe.run_ops(n, oe.noisy_trajectory_ops(c["ops"], c["angles"][t])))
+            assert np.max(np.abs(probs[t] - ref)) <= 1e-12
+        np.testing.assert_allclose(mean, probs.mean(axis=0), rtol=0, atol=1e-13)
+        pool.close()
+    torch.cuda.empty_cache()
