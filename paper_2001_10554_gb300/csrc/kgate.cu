@@ -4,12 +4,16 @@
 //
 // One thread owns one group of 2^k amplitudes (the other n - k bits fixed):
 // it loads the group into registers, forms every output as a dot product with
-// a row of U and stores it.  The loops are unrolled completely, so every
-// coefficient is a compile-time offset into the kernel's parameter block and
-// enters the FMAs as a constant-bank operand (no shared-memory traffic).
-// complex64 computes in FP32 (k <= 5); complex128 in the double-float
-// emulation (k <= 4) or, for small states or on request, in native FP64.
-// One read and one write of the state per gate.
+// a row of U and stores it.  For small k the loops are unrolled completely, so
+// every coefficient is a compile-time offset into the kernel's parameter block
+// and enters the FMAs as a constant-bank operand.  Where full unrolling would
+// make the loop body larger than the instruction cache (complex64 k >= 4,
+// double-float k >= 3, native k >= 4), the row loop stays rolled and the
+// coefficients are staged once per block in shared memory (all lanes read
+// the same address, so the reads broadcast).  complex64 computes in FP32
+// (k <= 5); complex128 in the double-float emulation (k <= 4) or, for small
+// states or on request, in native FP64.  One read and one write of the state
+// per gate.
 #include <algorithm>
 #include <cstring>
 
@@ -72,6 +76,36 @@ __global__ void __launch_bounds__(kThreads, min_blocks<K>()) k_kgate_c64(float2*
   }
 }
 
+// Rolled rows, U in shared memory (two coefficients per 16-byte read).
+template <int K>
+__global__ void __launch_bounds__(kThreads, 2) k_kgate_c64_rows(float2* __restrict__ a, uint64_t n_groups, Targets<K> T,
+                                                                UF32<K> U) {
+  constexpr int D = 1 << K;
+  __shared__ __align__(16) float2 su[D * D];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) su[i] = U.u[i];
+  __syncthreads();
+  const float4* su4 = reinterpret_cast<const float4*>(su);
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_groups; g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t base = group_base<K>(g, T);
+    float2 x[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = a[base + T.off[c]];
+#pragma unroll 1
+    for (int r = 0; r < D; ++r) {
+      float yr = 0.f, yi = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; c += 2) {
+        const float4 u = su4[(r * D + c) >> 1];
+        yr = fmaf(u.x, x[c].x, fmaf(-u.y, x[c].y, yr));
+        yi = fmaf(u.x, x[c].y, fmaf(u.y, x[c].x, yi));
+        yr = fmaf(u.z, x[c + 1].x, fmaf(-u.w, x[c + 1].y, yr));
+        yi = fmaf(u.z, x[c + 1].y, fmaf(u.w, x[c + 1].x, yi));
+      }
+      a[base + T.off[r]] = make_float2(yr, yi);
+    }
+  }
+}
+
 template <int K>
 struct UF64 {
   double2 u[1 << (2 * K)];
@@ -98,6 +132,186 @@ __global__ void __launch_bounds__(kThreads, min_blocks<K + 1>()) k_kgate_c128_na
       a[base + T.off[r]] = make_double2(yr, yi);
     }
   }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1) k_kgate_c128_native_rows(double2* __restrict__ a, uint64_t n_groups,
+                                                                        Targets<K> T, UF64<K> U) {
+  constexpr int D = 1 << K;
+  __shared__ double2 su[D * D];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) su[i] = U.u[i];
+  __syncthreads();
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_groups; g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t base = group_base<K>(g, T);
+    double2 x[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = a[base + T.off[c]];
+#pragma unroll 1
+    for (int r = 0; r < D; ++r) {
+      double yr = 0.0, yi = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const double2 u = su[r * D + c];
+        yr = fma(u.x, x[c].x, fma(-u.y, x[c].y, yr));
+        yi = fma(u.x, x[c].y, fma(u.y, x[c].x, yi));
+      }
+      a[base + T.off[r]] = make_double2(yr, yi);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- staged tiles (complex64, low targets)
+// When a target lies below bit 5, a thread's group is (partly) contiguous and
+// a warp's loads stride across 32 cache lines.  The tiled kernel instead
+// moves tiles of S = 2^s amplitudes, s = max(12, 8 + K): bits [0, t)
+// contiguous (t >= 8) and the kh targets at or above t, so that a tile holds
+// 2^(s - K) groups, a whole number of them per thread.  Tiles move between HBM and shared memory as coalesced
+// 16-byte accesses; inside shared memory the target bits below 4 (the bank
+// bits of a float2) are XORed with the lowest non-target bits at or above 4,
+// which spreads the lanes' reads over the banks and keeps every group on its
+// own 2^K positions.
+template <int K>
+__host__ __device__ constexpr int tile_bits() { return 8 + K > 12 ? 8 + K : 12; }
+
+template <int K>
+struct TilePlan {
+  int t;                       // contiguous low bits of a tile
+  int kh;                      // targets at or above t
+  int hpos[K];                 // their global positions, ascending
+  uint64_t hoff[1 << K];       // segment id -> global offset of the high targets
+  int tt[K];                   // all tile-local target positions, ascending
+  uint32_t toff[1 << K];       // element c -> tile-local offset (bit j of c <-> qubits[j])
+  int nsw;                     // swizzle: target bits below 4 ...
+  int sw_dst[4];               // ... their positions
+  int sw_src[4];               // ... the non-target bits that flip them
+};
+
+template <int K>
+__device__ __forceinline__ uint32_t tile_swz(uint32_t e, const TilePlan<K>& P) {
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < P.nsw) s |= ((e >> P.sw_src[i]) & 1u) << P.sw_dst[i];
+  return s;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_kgate_c64_tiled(float2* __restrict__ a, uint64_t n_tiles, TilePlan<K> P,
+                                                              UF32<K> U) {
+  constexpr int D = 1 << K;
+  constexpr int S = 1 << tile_bits<K>();
+  constexpr int GPT = (S >> K) / kThreads;  // groups per thread
+  extern __shared__ __align__(16) float2 tile[];
+  float2* su = tile + S;                                     // U, D * D values
+  uint64_t* hoff = reinterpret_cast<uint64_t*>(su + D * D);  // segment offsets
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) su[i] = U.u[i];
+#pragma unroll
+  for (int h = 0; h < D; ++h)
+    if (threadIdx.x == 0) hoff[h] = P.hoff[h];
+  const uint32_t tmask = (1u << P.t) - 1u;
+  for (uint64_t tau = blockIdx.x; tau < n_tiles; tau += gridDim.x) {
+    uint64_t gbase = tau << P.t;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j < P.kh) gbase = insert_zero(gbase, P.hpos[j]);
+    __syncthreads();  // the previous tile's stores have read the buffer
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < S / 2; i += kThreads) {
+      const uint32_t e = 2 * i;
+      const uint64_t gi = gbase | (e & tmask) | hoff[e >> P.t];
+      float4 v = *reinterpret_cast<const float4*>(a + gi);
+      const uint32_t sw = tile_swz<K>(e, P);
+      if (sw & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+      *reinterpret_cast<float4*>(tile + ((e ^ sw) & ~1u)) = v;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int j = 0; j < GPT; ++j) {
+      uint32_t gb = threadIdx.x + j * kThreads;
+#pragma unroll
+      for (int q = 0; q < K; ++q) gb = (uint32_t)insert_zero(gb, P.tt[q]);
+      const uint32_t gsw = tile_swz<K>(gb, P);
+      float2 x[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) x[c] = tile[gb | (P.toff[c] ^ gsw)];
+#pragma unroll(K <= 3 ? D : 1)
+      for (int r = 0; r < D; ++r) {
+        float yr = 0.f, yi = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const float2 u = su[r * D + c];
+          yr = fmaf(u.x, x[c].x, fmaf(-u.y, x[c].y, yr));
+          yi = fmaf(u.x, x[c].y, fmaf(u.y, x[c].x, yi));
+        }
+        tile[gb | (P.toff[r] ^ gsw)] = make_float2(yr, yi);
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < S / 2; i += kThreads) {
+      const uint32_t e = 2 * i;
+      const uint64_t gi = gbase | (e & tmask) | hoff[e >> P.t];
+      const uint32_t sw = tile_swz<K>(e, P);
+      float4 v = *reinterpret_cast<const float4*>(tile + ((e ^ sw) & ~1u));
+      if (sw & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+      *reinterpret_cast<float4*>(a + gi) = v;
+    }
+  }
+}
+
+// Tile geometry for qubits[0..K) on n qubits; false when the state is
+// smaller than a tile.
+template <int K>
+bool make_tile_plan(int n, const int* qubits, TilePlan<K>& P) {
+  constexpr int s = tile_bits<K>();
+  if (n < s) return false;
+  std::memset(&P, 0, sizeof(P));
+  int t = s, kh = 0;
+  for (int it = 0; it < 8; ++it) {  // t = s - (targets at or above t), a fixed point
+    kh = 0;
+    for (int j = 0; j < K; ++j) kh += qubits[j] >= t;
+    if (s - kh == t) break;
+    t = s - kh;
+  }
+  P.t = t;
+  P.kh = kh;
+  int hs[K], nh = 0;
+  for (int j = 0; j < K; ++j)
+    if (qubits[j] >= t) hs[nh++] = qubits[j];
+  std::sort(hs, hs + nh);
+  for (int j = 0; j < nh; ++j) P.hpos[j] = hs[j];
+  for (int h = 0; h < (1 << kh); ++h) {
+    uint64_t o = 0;
+    for (int j = 0; j < kh; ++j) o |= (uint64_t)((h >> j) & 1) << hs[j];
+    P.hoff[h] = o;
+  }
+  // tile-local position of each target: below t as is, else t + rank
+  int tl[K];
+  for (int j = 0; j < K; ++j) {
+    if (qubits[j] < t) tl[j] = qubits[j];
+    else tl[j] = t + (int)(std::lower_bound(hs, hs + nh, qubits[j]) - hs);
+  }
+  int srt[K];
+  for (int j = 0; j < K; ++j) srt[j] = tl[j];
+  std::sort(srt, srt + K);
+  for (int j = 0; j < K; ++j) P.tt[j] = srt[j];
+  for (int c = 0; c < (1 << K); ++c) {
+    uint32_t o = 0;
+    for (int j = 0; j < K; ++j) o |= (uint32_t)((c >> j) & 1) << tl[j];
+    P.toff[c] = o;
+  }
+  uint32_t tmask = 0;
+  for (int j = 0; j < K; ++j) tmask |= 1u << tl[j];
+  int src = 4;
+  for (int b = 0; b < 4; ++b) {
+    if (!((tmask >> b) & 1u)) continue;
+    while ((tmask >> src) & 1u) ++src;
+    P.sw_dst[P.nsw] = b;
+    P.sw_src[P.nsw] = src;
+    ++P.nsw;
+    ++src;
+  }
+  return true;
 }
 
 // Emulated complex128: output component (row r, re or im) is a real dot
@@ -134,6 +348,63 @@ __global__ void __launch_bounds__(kThreads, min_blocks<K + 2>()) k_kgate_c128_df
   if (bad) atomicOr(flag, 1u);
 }
 
+// The double-float dot product of dfx::dot with coefficients packed as
+// (h, l, h52, unused) float4 values in shared memory.
+template <int M>
+__device__ __forceinline__ void dot_smem(const float4* __restrict__ c, const float* xh, const float* xl, float& p,
+                                         float& e) {
+  float4 k = c[0];
+  p = k.x * xh[0];
+  e = fmaf(k.x, xh[0], -p);
+  e = fmaf(k.z, xl[0], e);
+  e = fmaf(k.y, xh[0], e);
+#pragma unroll
+  for (int j = 1; j < M; ++j) {
+    k = c[j];
+    const float q = k.x * xh[j];
+    const float eq = fmaf(k.x, xh[j], -q);
+    float s, t;
+    dfx::two_sum(p, q, s, t);
+    p = s;
+    e += eq + t;
+    e = fmaf(k.z, xl[j], e);
+    e = fmaf(k.y, xh[j], e);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1) k_kgate_c128_df_rows(double2* __restrict__ a, uint64_t n_groups,
+                                                                    Targets<K> T, UDF<K> U, unsigned* flag) {
+  constexpr int D = 1 << K;
+  constexpr int M = 2 * D;
+  __shared__ float4 sc[2 * D * M];
+  for (int i = threadIdx.x; i < 2 * D * M; i += blockDim.x) {
+    const dfx::Coef k = U.c[i];
+    sc[i] = make_float4(k.h, k.l, k.h52, 0.f);
+  }
+  __syncthreads();
+  unsigned bad = 0;
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_groups; g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t base = group_base<K>(g, T);
+    float xh[M], xl[M];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const double2 v = a[base + T.off[c]];
+      dfx::split(v.x, xh[2 * c], xl[2 * c], bad);
+      dfx::split(v.y, xh[2 * c + 1], xl[2 * c + 1], bad);
+    }
+#pragma unroll 1
+    for (int r = 0; r < D; ++r) {
+      float p, e;
+      dot_smem<M>(&sc[(2 * r) * M], xh, xl, p, e);
+      const double yr = dfx::join(p, e);
+      dot_smem<M>(&sc[(2 * r + 1) * M], xh, xl, p, e);
+      a[base + T.off[r]] = make_double2(yr, dfx::join(p, e));
+    }
+  }
+  if (bad) atomicOr(flag, 1u);
+}
+
 template <int K>
 Targets<K> make_targets(const int* qubits) {
   Targets<K> T;
@@ -159,14 +430,39 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
     if constexpr (K <= kMaxK64) {
       UF32<K> u;
       for (int i = 0; i < D * D; ++i) u.u[i] = make_float2((float)U[2 * i], (float)U[2 * i + 1]);
-      k_kgate_c64<K><<<grid, kThreads, 0, r->stream>>>((float2*)r->data, n_groups, T, u);
+      bool low = false;
+      for (int j = 0; j < K; ++j) low |= qubits[j] < 5;
+      TilePlan<K> P;
+      if (low && make_tile_plan<K>(r->n, qubits, P)) {
+        const size_t smem = sizeof(float2) * ((size_t)(1 << tile_bits<K>()) + (size_t)(D * D)) + sizeof(uint64_t) * D;
+        static int per_sm = 0;  // per K instantiation: resident blocks per SM
+        if (per_sm == 0) {
+          cudaError_t e = cudaFuncSetAttribute(k_kgate_c64_tiled<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+          if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kgate_c64_tiled<K>, kThreads, smem);
+          if (e != cudaSuccess) return e;
+          per_sm = std::max(per_sm, 1);
+        }
+        const uint64_t n_tiles = num_amps(r) >> tile_bits<K>();
+        const unsigned tg = (unsigned)std::min<uint64_t>(n_tiles, (uint64_t)per_sm * kSMs);
+        k_kgate_c64_tiled<K><<<tg, kThreads, smem, r->stream>>>((float2*)r->data, n_tiles, P, u);
+        return launched(1);
+      }
+      if constexpr (K >= 4)
+        k_kgate_c64_rows<K><<<grid, kThreads, 0, r->stream>>>((float2*)r->data, n_groups, T, u);
+      else
+        k_kgate_c64<K><<<grid, kThreads, 0, r->stream>>>((float2*)r->data, n_groups, T, u);
       return launched(1);
     }
   } else if (!use_emulated(r)) {
     if constexpr (K <= kMaxK128) {
       UF64<K> u;
       for (int i = 0; i < D * D; ++i) u.u[i] = make_double2(U[2 * i], U[2 * i + 1]);
-      k_kgate_c128_native<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u);
+      if constexpr (K >= 4)
+        k_kgate_c128_native_rows<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u);
+      else
+        k_kgate_c128_native<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u);
       return launched(1);
     }
   } else {
@@ -181,7 +477,10 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
           u.c[(2 * row + 1) * M + 2 * c] = dfx::make_coef(ui);       // im += Im(u) Re(x)
           u.c[(2 * row + 1) * M + 2 * c + 1] = dfx::make_coef(ur);   // im += Re(u) Im(x)
         }
-      k_kgate_c128_df<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
+      if constexpr (K >= 3)
+        k_kgate_c128_df_rows<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
+      else
+        k_kgate_c128_df<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
       return launched(1);
     }
   }
