@@ -488,3 +488,67 @@ def test_sampling_never_draws_zero_weight_outcomes():
         assert cdf[si] <= ti < cdf[si + 1]
     with pytest.raises(ValueError):
         sv.sample(np.zeros(8, complex), [0.5])
+
+
+# ---------------------------------------------------------------- particle swarm (Section 4)
+def test_swarm_without_attraction_moves_geometrically():
+    """phi_p = phi_g = 0: v_s = omega^s v_0, so theta_s = theta_0 + v_0 (omega + ... + omega^s)."""
+    from oracle import pso
+    g = W.rng(501)
+    R, D, steps, om = 5, 3, 7, 0.66
+    x0, v0 = g.uniform(size=(R, D)), g.uniform(size=(R, D))
+    _, _, _, hist = pso.swarm(lambda t: -float(np.sum(t * t)), x0, v0, g.uniform(size=(steps, R)),
+                              g.uniform(size=(steps, R)), om, 0.0, 0.0)
+    for s in range(steps + 1):
+        geo = sum(om ** j for j in range(1, s + 1))
+        np.testing.assert_allclose(hist[s], x0 + v0 * geo, rtol=0, atol=1e-13)
+
+
+def test_swarm_attraction_terms_by_hand():
+    """Two particles on L = cos(theta), omega = 0.  Step 1 (r_p = 0, r_g = 1/2,
+    phi_g = 1): the particle that is not the swarm's best moves halfway to it,
+    where L is worse, so its own best stays put.  Step 2 (r_p = 1, phi_p = 1,
+    r_g = 0): it returns exactly to its own best; the best particle never moves."""
+    from oracle import pso
+    a, b = 0.0, 2 * np.pi - 0.1
+    x0 = np.array([[a], [b]])
+    v0 = np.array([[0.7], [-0.3]])
+    rp = np.array([[0.0, 0.0], [1.0, 1.0]])
+    rg = np.array([[0.5, 0.5], [0.0, 0.0]])
+    trace, best_pos, best_val, hist = pso.swarm(lambda t: float(np.cos(t[0])), x0, v0, rp, rg, 0.0, 1.0, 1.0)
+    assert hist[1][0, 0] == a and hist[2][0, 0] == a
+    assert abs(hist[1][1, 0] - (a + b) / 2) < 1e-15
+    assert abs(hist[2][1, 0] - b) < 1e-15
+    assert best_val == 1.0 and best_pos[0] == a
+    np.testing.assert_array_equal(trace, [1.0] * 6)
+
+
+def test_swarm_trace_is_running_best_of_scored_positions():
+    from oracle import pso, qaoa as oq
+    n, p = 6, 2
+    edges = W.random_3regular_graph(n, 11)
+    pos, vel, rp, rg = W.pso_inputs(1, 4, 5, p, 12)
+    f = pso.qaoa_objective(n, edges, p)
+    trace, best_pos, best_val, hist = pso.swarm(f, pos[0], vel[0], rp[:, 0], rg[:, 0], 0.66, 1.6, 0.62)
+    assert trace.shape == (6 * 4,)
+    scores = [oq.qaoa_energy(n, edges, th[:p], th[p:]) for th in hist.reshape(-1, 2 * p)]
+    np.testing.assert_allclose(trace, np.maximum.accumulate(scores), rtol=0, atol=1e-14)
+    assert best_val == trace[-1]
+    assert abs(oq.qaoa_energy(n, edges, best_pos[:p], best_pos[p:]) - best_val) < 1e-14
+    assert best_val <= oq.maxcut_brute_force(n, edges) + 1e-12
+
+
+def test_swarm_converges_on_a_concave_quadratic():
+    """With the section's constants (omega 0.66, phi_p 1.6, phi_g 0.62) the
+    attracting swarm contracts onto the maximum of -|theta - c|^2; a sign error
+    in either attraction term makes it drift away instead."""
+    from oracle import pso
+    g = W.rng(503)
+    c = np.array([0.3, -1.2, 2.0, 0.7])
+    R, steps = 16, 150
+    x0 = g.uniform(-5, 5, size=(R, 4))
+    v0 = g.uniform(-1, 1, size=(R, 4))
+    _, best_pos, best_val, _ = pso.swarm(lambda t: -float(np.sum((t - c) ** 2)), x0, v0,
+                                         g.uniform(size=(steps, R)), g.uniform(size=(steps, R)), 0.66, 1.6, 0.62)
+    assert best_val > -1e-8
+    assert np.max(np.abs(best_pos - c)) < 1e-4

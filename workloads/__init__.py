@@ -198,3 +198,16 @@ def noise_ensemble(n: int = 16, circuits: int = 8, trajectories: int = 500,
             ang[t] = gt.normal(0.0, sigma, size=(n_noise, 2))
         out.append({"ops": ops, "angles": ang, "depth": depth})
     return out
+
+
+def pso_inputs(graphs: int, particles: int, steps: int, p: int, seed: int):
+    """Swarm inputs of Section 4: initial positions and velocities uniform in
+    [0, 2 pi) (graphs, particles, 2p), and the per-step uniform draws r_p, r_g
+    in [0, 1) (steps, graphs, particles)."""
+    g = rng(seed)
+    two_pi = 2.0 * np.pi
+    pos = g.uniform(0.0, two_pi, size=(graphs, particles, 2 * p))
+    vel = g.uniform(0.0, two_pi, size=(graphs, particles, 2 * p))
+    rp = g.uniform(size=(steps, graphs, particles))
+    rg = g.uniform(size=(steps, graphs, particles))
+    return pos, vel, rp, rg
