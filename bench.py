@@ -53,6 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the complex64 32q sweep and the QAOA sections")
+    ap.add_argument("--pso-graphs", type=int, default=64, help="graphs of the particle-swarm section (0 skips it)")
     ap.add_argument("--profile-qaoa", default=None, metavar="N,P,BATCH",
                     help="run one complex64 QAOA energy + gradient evaluation of BATCH parameter sets and exit "
                          "(a small, fixed launch sequence for profilers)")
@@ -392,6 +393,46 @@ def qaoa_section(iqs, torch):
     return out
 
 
+def pso_section(iqs, torch, n_graphs: int):
+    """Section 4's experiment: particle swarms over QAOA parameters (p = 4) on
+    random 3-regular graphs of 18 vertices, one swarm per graph, all graphs'
+    swarms scored together in one complex64 engine call per swarm step;
+    particle counts 4..64 with about 5000 evaluations per graph each.  Reports
+    the mean and standard deviation over graphs of the approximation ratio
+    (best energy so far / exact Max-Cut) at fixed evaluation counts, and the
+    evaluation throughput."""
+    import workloads as W
+    n, p, total = 18, 4, 5000
+    gs = [W.random_3regular_graph(n, 3000 + i) for i in range(n_graphs)]
+    marks = [8, 64, 100, 512, 1000, 2000, 4992]
+    out = {"workload": f"PSO (omega 0.66, phi_p 1.6, phi_g 0.62) over QAOA p={p} on {n_graphs} random 3-regular "
+                       f"graphs of {n} vertices, complex64 engine, ~{total} evaluations per graph per particle count",
+           "rows": []}
+    exact = None
+    for R in (4, 8, 16, 32, 64):
+        steps = total // R - 1
+        eng = iqs.QAOA(n, None, "complex64", graphs=gs, per_graph=R)
+        if exact is None:
+            exact = eng.max_cut()
+        pos, vel, rp, rg = W.pso_inputs(n_graphs, R, steps, p, 4000 + R)
+        eng.pso(pos, vel, rp[:1], rg[:1])  # warm-up: captures the engine's graph for this batch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        trace, _, best = eng.pso(pos, vel, rp, rg)
+        dt = time.perf_counter() - t0
+        eng.close()
+        torch.cuda.empty_cache()
+        ratio = trace / exact[:, None]
+        evals = (steps + 1) * R
+        row = {"particles": R, "swarm_steps": steps + 1, "evaluations_per_graph": evals, "seconds": round(dt, 3),
+               "evaluations_per_s": round(n_graphs * evals / dt, 1),
+               "ratio_mean": {str(m): round(float(ratio[:, m - 1].mean()), 4) for m in marks if m <= evals},
+               "ratio_std": {str(m): round(float(ratio[:, m - 1].std()), 4) for m in marks if m <= evals}}
+        out["rows"].append(row)
+    out["exact_maxcut_mean"] = float(exact.mean())
+    return out
+
+
 def ensemble_section(iqs, torch):
     """Noise ensemble: 8 circuits of 16 qubits, depth uniform in [40, 120],
     one-qubit Haar layers + CNOT brick, X/Z noise rotations N(0, 0.02^2) after
@@ -594,6 +635,8 @@ def main(argv=None):
         extra["kq_measure"] = kq_measure_section(iqs, torch, dev)
         extra["qaoa"] = qaoa_section(iqs, torch)
         extra["noise_ensemble"] = ensemble_section(iqs, torch)
+        if args.pso_graphs > 0:
+            extra["pso_qaoa"] = pso_section(iqs, torch, args.pso_graphs)
 
     if rank == 0:
         line = {

@@ -258,6 +258,51 @@ iqs_status iqs_qaoa_get_tma(const iqs_qaoa* q, int* mode, int* available);
  * pass, or after the uncompute when a gradient was computed) to host memory. */
 iqs_status iqs_qaoa_download_state(iqs_qaoa* q, int index, void* host, size_t bytes);
 
+/* Several graphs in one workspace (Section 4: the swarm experiment averages
+ * over many random 3-regular graphs).  ``edges`` holds n_graphs x n_edges
+ * int32 pairs, graph-major; every graph has the same number of edges.  The
+ * workspace holds n_graphs x per_graph states (at most 65535); in
+ * iqs_qaoa_run, parameter set b is scored on graph b / per_graph.
+ * iqs_qaoa_create(n, dtype, B, ...) is the one-graph case. */
+iqs_status iqs_qaoa_create_multi(int n, int dtype, int n_graphs, int per_graph, int n_edges, const int32_t* edges,
+                                 void* stream, iqs_qaoa** out);
+
+/* Shape of a workspace (any pointer may be NULL).  For a one-graph
+ * workspace, per_graph is its batch_max. */
+iqs_status iqs_qaoa_info(const iqs_qaoa* q, int* n, int* dtype, int* n_graphs, int* per_graph, int* n_edges);
+
+/* Section 4: E_exact, the exact Max-Cut value of each graph, as the largest
+ * cut count over all 2^n bipartitions (read from the workspace's cut
+ * tables).  ``out``: host array of n_graphs doubles.  Synchronous. */
+iqs_status iqs_qaoa_max_cut(iqs_qaoa* q, double* out);
+
+/* Section 4, "QAOA with swarm particle optimization": particle swarm
+ * maximisation of L(theta) = <H_MaxCut>, theta = (gamma_1..gamma_p,
+ * beta_1..beta_p), one swarm of per_graph particles per graph of the
+ * workspace, all swarms scored together in one iqs_qaoa_run per step
+ * (energies only).  Each step, for particle k of graph g:
+ *   v <- omega v + phi_p r_p (theta_best_k - theta) + phi_g r_g (theta_best_g - theta),
+ *   theta <- theta + v,
+ * then every new position is scored; a particle's best (and then the swarm's
+ * best) moves only to a strictly larger score, and the swarm's best used by a
+ * step is the one after the previous step.  Reading: the paper's printed
+ * velocity update has theta - theta_best in both attraction terms, which
+ * would repel the particles; the standard swarm update (Kennedy and
+ * Eberhart 1995), which attracts them, is taken.  r_p and r_g are one number
+ * per particle per step, as the paper's equation writes them.
+ *
+ * Host arrays (G = n_graphs, R = per_graph):
+ *   pos0, vel0  [G][R][2p]           initial positions and velocities
+ *   rp, rg      [steps][G][R]        the uniform draws
+ *   trace       [G][(steps+1) R]     best score so far after each evaluation
+ *                                    (step-major, particles in order)
+ *   best_pos    [G][2p], best_val [G]
+ * All random numbers are inputs.  Scores are the engine's energies (complex64
+ * or complex128, as created). */
+iqs_status iqs_qaoa_pso(iqs_qaoa* q, int p, int steps, const double* pos0, const double* vel0, const double* rp,
+                        const double* rg, double omega, double phi_p, double phi_g, double* trace, double* best_pos,
+                        double* best_val);
+
 /* ------------------------------------------------------------ pool of noisy trajectories */
 
 /* Section 2 "Pool of multiple states" and the pool-of-states appendix: a pool

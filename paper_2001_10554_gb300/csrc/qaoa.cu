@@ -115,6 +115,16 @@ __global__ void k_cut_table(uint8_t* cut, uint64_t N, EdgesU8 E) {
     cut[i] = (uint8_t)cut_count((X)i, E);
 }
 
+// Largest cut count of each graph (grid (blocks, n_graphs)); out[g] must be 0 on entry.
+__global__ void k_cut_max(const uint8_t* __restrict__ cut, uint64_t N, unsigned* __restrict__ out) {
+  const uint8_t* c = cut + (uint64_t)blockIdx.y * N;
+  unsigned m = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned)c[i]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, m);
+}
+
 // Mixer pass: RX on the qubits [s, s+m) of every tile (or its inverse, with the
 // gradient term, on two vectors when ADJ).  The tile is staged in shared
 // memory; the gate bits are processed in rounds of up to kRegBits bits, each
@@ -294,11 +304,12 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restr
                                                          double* __restrict__ partials, int part_stride, unsigned* flag,
                                                          const uint8_t* __restrict__ cut,
                                                          const typename TR::PH* __restrict__ tables, int tsize,
-                                                         double* __restrict__ partials_g) {
+                                                         double* __restrict__ partials_g, int per_graph) {
   using W = typename TR::W;
   using PHT = typename TR::PH;
   __shared__ PHT st[PH ? kEdgeChunk + 1 : 1];
   if (PH) {
+    cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
     for (int i = threadIdx.x; i < tsize; i += blockDim.x) {
       const PHT tt = tables[(uint64_t)blockIdx.y * tsize + i];
       st[i] = PH == 2 ? TR::conj(tt) : tt;
@@ -441,7 +452,8 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
                                                         double* __restrict__ partials, int part_stride, unsigned* flag,
                                                         const uint8_t* __restrict__ cut,
                                                         const typename TR::PH* __restrict__ tables, int tsize,
-                                                        double* __restrict__ partials_g, unsigned* err) {
+                                                        double* __restrict__ partials_g, unsigned* err, int per_graph) {
+  if (PH) cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
   using TT = TmaTraits<TR>;
   using V = typename TR::V;
   using W = typename TR::W;
@@ -585,11 +597,13 @@ template <class TR, bool ADJ>
 __global__ void __launch_bounds__(kThreads) k_phase(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam,
                                                     uint64_t N, const uint8_t* __restrict__ cut,
                                                     const typename TR::PH* __restrict__ tables, int tsize,
-                                                    double* __restrict__ partials, int part_stride, unsigned* flag) {
+                                                    double* __restrict__ partials, int part_stride, unsigned* flag,
+                                                    int per_graph) {
   using PH = typename TR::PH;
   using W = typename TR::W;
   __shared__ PH st[kEdgeChunk + 1];
   const unsigned b = blockIdx.y;
+  cut += (uint64_t)(b / (unsigned)per_graph) * N;
   for (int i = threadIdx.x; i < tsize; i += blockDim.x) {
     const PH t = tables[(uint64_t)b * tsize + i];
     st[i] = ADJ ? TR::conj(t) : t;
@@ -624,8 +638,9 @@ __global__ void __launch_bounds__(kThreads) k_energy_lambda(const typename TR::V
                                                             typename TR::V* __restrict__ lam, uint64_t N,
                                                             const uint8_t* __restrict__ cut,
                                                             double* __restrict__ partials, int part_stride,
-                                                            unsigned* flag) {
+                                                            unsigned* flag, int per_graph) {
   const unsigned b = blockIdx.y;
+  cut += (uint64_t)(b / (unsigned)per_graph) * N;
   const typename TR::V* P = phi + (uint64_t)b * N;
   typename TR::V* L = lam ? lam + (uint64_t)b * N : nullptr;
   unsigned bad = 0;
@@ -711,6 +726,8 @@ __global__ void k_rescale(V* __restrict__ a, uint64_t N, const double* __restric
 // ================================================================ host engine
 struct iqs_qaoa {
   int n = 0, dtype = IQS_C64, bmax = 0, n_edges = 0;
+  int n_graphs = 1;          // cut tables, one per graph ([n_graphs][N] bytes)
+  int per_graph = 1 << 30;   // state b uses graph b / per_graph
   uint64_t N = 0;
   cudaStream_t stream = nullptr;
   int renorm_every = 0;
@@ -791,6 +808,7 @@ struct PhaseFuse {
   const typename TR::PH* tables = nullptr;
   int tsize = 0;
   double* partials_g = nullptr;
+  int per_graph = 1 << 30;  // state b uses cut table b / per_graph
 };
 
 template <class TR, bool ADJ, int C>
@@ -798,13 +816,15 @@ void launch_fast(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, ty
                  const typename TR::RX* rx, double* partials, int ps, unsigned* flag, const PhaseFuse<TR>& f) {
   if (!ADJ && f.mode == 1)
     k_mixer_fast<TR, ADJ, C, (ADJ ? 0 : 1)><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
-                                                                          f.cut, f.tables, f.tsize, f.partials_g);
+                                                                          f.cut, f.tables, f.tsize, f.partials_g,
+                                                                          f.per_graph);
   else if (ADJ && f.mode == 2)
     k_mixer_fast<TR, ADJ, C, (ADJ ? 2 : 0)><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
-                                                                          f.cut, f.tables, f.tsize, f.partials_g);
+                                                                          f.cut, f.tables, f.tsize, f.partials_g,
+                                                                          f.per_graph);
   else
     k_mixer_fast<TR, ADJ, C, 0><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag, nullptr, nullptr,
-                                                             0, nullptr);
+                                                             0, nullptr, 1);
 }
 
 template <class TR, int C>
@@ -876,7 +896,7 @@ void launch_tma1(dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename T
                  unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta) {
   k_mixer_tma<TR, ADJ, C, PH><<<grid, kThreads, tma_smem<TR>(ADJ), s>>>(
       *ta.phi, ADJ ? *ta.lam : *ta.phi, N, sb, ta.hi_bits, rx, partials, ps, flag, f.cut, f.tables, f.tsize,
-      f.partials_g, ta.err);
+      f.partials_g, ta.err, f.per_graph);
 }
 
 template <class TR, bool ADJ, int C>
@@ -980,7 +1000,8 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
   for (int l = 0; l < p; ++l) {
     const typename TR::PH* tab_l = tab + (uint64_t)l * q->bmax * tsize;
     if (!fuse_in) {
-      k_phase<TR, false><<<g_stream, kThreads, 0, s>>>(phi, nullptr, N, q->cut, tab_l, tsize, nullptr, 0, q->flag);
+      k_phase<TR, false><<<g_stream, kThreads, 0, s>>>(phi, nullptr, N, q->cut, tab_l, tsize, nullptr, 0, q->flag,
+                                                       q->per_graph);
       ++launches;
     }
     for (size_t i = 0; i < q->passes.size(); ++i) {
@@ -991,6 +1012,7 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
       if (i == 0 && fuse_in) {
         f.mode = 1;
         f.cut = q->cut;
+        f.per_graph = q->per_graph;
         f.tables = tab_l;
         f.tsize = tsize;
       }
@@ -1005,7 +1027,8 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
     }
   }
   double* phi_norm = q->norms + 2 * q->bmax;  // |phi|^2 after the forward pass
-  k_energy_lambda<TR><<<g_stream, kThreads, 0, s>>>(phi, grad ? lam : nullptr, N, q->cut, q->partials, ps, q->flag);
+  k_energy_lambda<TR><<<g_stream, kThreads, 0, s>>>(phi, grad ? lam : nullptr, N, q->cut, q->partials, ps, q->flag,
+                                                    q->per_graph);
   k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->results, out_stride, 0);
   k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + PB, PB, ps, 1.0, phi_norm, 1, 0);
   launches += 3;
@@ -1030,6 +1053,7 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
         if (i + 1 == q->passes.size() && fuse_out) {
           f.mode = 2;
           f.cut = q->cut;
+          f.per_graph = q->per_graph;
           f.tables = tab_l;
           f.tsize = tsize;
           f.partials_g = partials_g;
@@ -1052,7 +1076,8 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
         k_finalize_batch<<<B, kThreads, 0, s>>>(partials_g, (int)last_gx, ps, 2.0, q->results, out_stride, 1 + l);
         ++launches;
       } else {
-        k_phase<TR, true><<<g_stream, kThreads, 0, s>>>(phi, lam, N, q->cut, tab_l, tsize, q->partials, ps, q->flag);
+        k_phase<TR, true><<<g_stream, kThreads, 0, s>>>(phi, lam, N, q->cut, tab_l, tsize, q->partials, ps, q->flag,
+                                                        q->per_graph);
         k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 2.0, q->results, out_stride, 1 + l);
         launches += 2;
       }
@@ -1233,18 +1258,26 @@ extern "C" {
 
 iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const int32_t* edges, void* stream,
                            iqs_qaoa** out) {
+  return iqs_qaoa_create_multi(n, dtype, 1, batch_max, n_edges, edges, stream, out);
+}
+
+iqs_status iqs_qaoa_create_multi(int n, int dtype, int n_graphs, int per_graph, int n_edges, const int32_t* edges,
+                                 void* stream, iqs_qaoa** out) {
   using namespace iqs;
   if (out == nullptr) return report(IQS_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 2 || n > IQS_MAX_QUBITS) return report(IQS_EINVAL, "number of qubits %d outside [2, %d]", n, IQS_MAX_QUBITS);
   if (dtype != IQS_C64 && dtype != IQS_C128) return report(IQS_EINVAL, "dtype must be IQS_C64 or IQS_C128");
-  if (batch_max < 1 || batch_max > 65535) return report(IQS_EINVAL, "batch_max %d outside [1, 65535]", batch_max);
+  if (n_graphs < 1 || per_graph < 1 || (int64_t)n_graphs * per_graph > 65535)
+    return report(IQS_EINVAL, "n_graphs %d x per_graph %d outside [1, 65535]", n_graphs, per_graph);
+  const int batch_max = n_graphs * per_graph;
   if (n_edges < 1 || n_edges > kEdgeChunk || edges == nullptr)
     return report(IQS_EINVAL, "n_edges %d outside [1, %d] or edges NULL", n_edges, kEdgeChunk);
-  for (int e = 0; e < n_edges; ++e) {
+  for (int e = 0; e < n_graphs * n_edges; ++e) {
     const int u = edges[2 * e], v = edges[2 * e + 1];
     if (u < 0 || u >= n || v < 0 || v >= n || u == v)
-      return report(IQS_EINVAL, "edge %d = (%d, %d) invalid for %d qubits", e, u, v, n);
+      return report(IQS_EINVAL, "edge %d of graph %d = (%d, %d) invalid for %d qubits", e % n_edges, e / n_edges, u,
+                    v, n);
   }
   if (fault_now(1)) return report(IQS_ENOMEM, "injected allocation failure");
   iqs_qaoa* q = new (std::nothrow) iqs_qaoa();
@@ -1253,6 +1286,8 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
   q->dtype = dtype;
   q->bmax = batch_max;
   q->n_edges = n_edges;
+  q->n_graphs = n_graphs;
+  q->per_graph = n_graphs == 1 ? (1 << 30) : per_graph;
   q->N = 1ull << n;
   q->stream = (cudaStream_t)stream;
   if (q->stream == nullptr) {  // graphs cannot be captured on the legacy stream: use a blocking stream of our own
@@ -1271,7 +1306,7 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
   const int ps = part_stride_for(q);
   bool ok = cudaMalloc(&q->phi, amp * q->N * batch_max) == cudaSuccess &&
             cudaMalloc(&q->lam, amp * q->N * batch_max) == cudaSuccess &&
-            cudaMalloc(&q->cut, q->N) == cudaSuccess && cudaMalloc(&q->rx, q->rx_bytes) == cudaSuccess &&
+            cudaMalloc(&q->cut, q->N * (size_t)n_graphs) == cudaSuccess && cudaMalloc(&q->rx, q->rx_bytes) == cudaSuccess &&
             cudaMalloc(&q->tables, q->table_bytes) == cudaSuccess &&
             cudaMalloc(&q->partials, sizeof(double) * (size_t)ps * batch_max) == cudaSuccess &&
             cudaMalloc(&q->results, sizeof(double) * (size_t)batch_max * (1 + 2 * kMaxP)) == cudaSuccess &&
@@ -1285,18 +1320,23 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
     free_qaoa(q);
     return report(IQS_ENOMEM, "cannot allocate the QAOA workspace (%d states of %d qubits)", batch_max, n);
   }
-  EdgesU8 E;
-  E.m = n_edges;
-  for (int e = 0; e < n_edges; ++e) {
-    E.u[e] = (uint8_t)edges[2 * e];
-    E.v[e] = (uint8_t)edges[2 * e + 1];
+  cudaError_t e = cudaSuccess;
+  for (int gi = 0; gi < n_graphs && e == cudaSuccess; ++gi) {
+    EdgesU8 E;
+    E.m = n_edges;
+    const int32_t* eg = edges + (size_t)2 * n_edges * gi;
+    for (int k = 0; k < n_edges; ++k) {
+      E.u[k] = (uint8_t)eg[2 * k];
+      E.v[k] = (uint8_t)eg[2 * k + 1];
+    }
+    uint8_t* cg = q->cut + q->N * (size_t)gi;
+    if (n <= 32)
+      k_cut_table<uint32_t><<<grid_for(q->N, 1, 16), kThreads, 0, q->stream>>>(cg, q->N, E);
+    else
+      k_cut_table<uint64_t><<<grid_for(q->N, 1, 16), kThreads, 0, q->stream>>>(cg, q->N, E);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) note_launches(1);
   }
-  if (n <= 32)
-    k_cut_table<uint32_t><<<grid_for(q->N, 1, 16), kThreads, 0, q->stream>>>(q->cut, q->N, E);
-  else
-    k_cut_table<uint64_t><<<grid_for(q->N, 1, 16), kThreads, 0, q->stream>>>(q->cut, q->N, E);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) note_launches(1);
   if (e == cudaSuccess) e = cudaMemsetAsync(q->flag, 0, sizeof(unsigned), q->stream);
   if (e == cudaSuccess) e = dtype == IQS_C128 ? set_smem_attrs<T128>() : set_smem_attrs<T64>();
   if (e == cudaSuccess) e = dtype == IQS_C128 ? set_tma_attrs<T128>() : set_tma_attrs<T64>();
@@ -1309,6 +1349,40 @@ iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const i
   load_tuning(q);
   replan(q);
   *out = q;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_info(const iqs_qaoa* q, int* n, int* dtype, int* n_graphs, int* per_graph, int* n_edges) {
+  if (q == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (n) *n = q->n;
+  if (dtype) *dtype = q->dtype;
+  if (n_graphs) *n_graphs = q->n_graphs;
+  if (per_graph) *per_graph = q->n_graphs == 1 ? q->bmax : q->per_graph;
+  if (n_edges) *n_edges = q->n_edges;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_max_cut(iqs_qaoa* q, double* out) {
+  using namespace iqs;
+  if (q == nullptr || out == nullptr) return report(IQS_EINVAL, "handle or out is NULL");
+  unsigned* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof(unsigned) * q->n_graphs, q->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return report(IQS_ENOMEM, "cannot allocate %d words", q->n_graphs);
+  }
+  std::vector<unsigned> h(q->n_graphs);
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned) * q->n_graphs, q->stream);
+  if (e == cudaSuccess) {
+    const dim3 grid((unsigned)std::min<uint64_t>(std::max<uint64_t>(1, q->N / (kThreads * 8)), 2 * kSMs), q->n_graphs);
+    k_cut_max<<<grid, kThreads, 0, q->stream>>>(q->cut, q->N, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) note_launches(1);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned) * q->n_graphs, cudaMemcpyDeviceToHost, q->stream);
+  cudaFreeAsync(d, q->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+  if (e != cudaSuccess) return report(IQS_ECUDA, "max cut: %s", cudaGetErrorString(e));
+  for (int g = 0; g < q->n_graphs; ++g) out[g] = (double)h[g];
   return IQS_OK;
 }
 

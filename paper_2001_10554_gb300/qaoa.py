@@ -31,15 +31,57 @@ class QAOA:
     """
 
     def __init__(self, n: int, edges, dtype="complex64", batch_max: int = 1, stream=None,
-                 renorm_every: int = 0, use_graphs: bool = True):
-        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
-        self.n, self.n_edges, self.batch_max = int(n), e.shape[0], int(batch_max)
+                 renorm_every: int = 0, use_graphs: bool = True, *, graphs=None, per_graph: int = 0):
+        """One graph (``edges``), or with ``graphs`` (a list of edge lists of
+        equal length) one workspace of len(graphs) x ``per_graph`` states in
+        which parameter set b is scored on graph b // per_graph."""
+        self.n = int(n)
         self.dtype_code = _dtype_code(dtype)
         h = C.c_void_p()
-        call("iqs_qaoa_create", self.n, self.dtype_code, self.batch_max, self.n_edges,
-             e.ctypes.data_as(C.POINTER(C.c_int32)), _stream_handle(stream), C.byref(h))
+        if graphs is None:
+            e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+            self.n_edges, self.batch_max, self.n_graphs = e.shape[0], int(batch_max), 1
+            call("iqs_qaoa_create", self.n, self.dtype_code, self.batch_max, self.n_edges,
+                 e.ctypes.data_as(C.POINTER(C.c_int32)), _stream_handle(stream), C.byref(h))
+        else:
+            es = [np.asarray(g, dtype=np.int32).reshape(-1, 2) for g in graphs]
+            if len({x.shape[0] for x in es}) != 1:
+                raise ValueError("every graph needs the same number of edges")
+            e = np.ascontiguousarray(np.concatenate(es))
+            self.n_graphs, self.n_edges = len(es), es[0].shape[0]
+            self.batch_max = self.n_graphs * int(per_graph)
+            call("iqs_qaoa_create_multi", self.n, self.dtype_code, self.n_graphs, int(per_graph), self.n_edges,
+                 e.ctypes.data_as(C.POINTER(C.c_int32)), _stream_handle(stream), C.byref(h))
+        self.per_graph = self.batch_max if graphs is None else int(per_graph)
         self._h = h
         self.set_options(renorm_every, use_graphs)
+
+    def max_cut(self) -> np.ndarray:
+        """Exact Max-Cut value of each graph (largest cut count over all bipartitions)."""
+        out = np.empty(self.n_graphs)
+        call("iqs_qaoa_max_cut", self._h, _ptr(out))
+        return out
+
+    def pso(self, pos0, vel0, rp, rg, omega=0.66, phi_p=1.6, phi_g=0.62):
+        """Particle swarm over (gamma_1..p, beta_1..p), one swarm of per_graph
+        particles per graph.  pos0, vel0: (G, R, 2p); rp, rg: (steps, G, R).
+        Returns (trace (G, (steps+1) R) of best-so-far scores, best_pos (G, 2p),
+        best_val (G,))."""
+        x = np.ascontiguousarray(np.asarray(pos0, dtype=np.float64))
+        v = np.ascontiguousarray(np.asarray(vel0, dtype=np.float64))
+        a = np.ascontiguousarray(np.asarray(rp, dtype=np.float64))
+        b = np.ascontiguousarray(np.asarray(rg, dtype=np.float64))
+        G, R, D = x.shape
+        if (G, R) != (self.n_graphs, self.per_graph) or v.shape != x.shape or D % 2:
+            raise ValueError("positions must be (n_graphs, per_graph, 2p)")
+        steps = a.shape[0]
+        if a.shape != (steps, G, R) or b.shape != a.shape:
+            raise ValueError("rp and rg must be (steps, n_graphs, per_graph)")
+        trace = np.empty((G, (steps + 1) * R))
+        best_pos, best_val = np.empty((G, D)), np.empty(G)
+        call("iqs_qaoa_pso", self._h, D // 2, steps, _ptr(x), _ptr(v), _ptr(a), _ptr(b), C.c_double(omega),
+             C.c_double(phi_p), C.c_double(phi_g), _ptr(trace), _ptr(best_pos), _ptr(best_val))
+        return trace, best_pos, best_val
 
     def set_options(self, renorm_every: int = 0, use_graphs: bool = True) -> None:
         call("iqs_qaoa_set_options", self._h, int(renorm_every), int(bool(use_graphs)))

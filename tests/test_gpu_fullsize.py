@@ -274,3 +274,23 @@ def test_noise_ensemble_full_size_sampled(gpu_lib):
         np.testing.assert_allclose(mean, probs.mean(axis=0), rtol=0, atol=1e-13)
         pool.close()
     torch.cuda.empty_cache()
+
+
+def test_swarm_full_size_sampled(gpu_lib):
+    """The benchmark's swarm configuration (18 qubits, p = 4, 64 graphs, 16
+    particles per graph, complex64 engine), a few steps: E_exact of sampled
+    graphs against the oracle's brute force, and each sampled graph's best
+    value against the oracle energy at the returned best position (2e-6)."""
+    n, p, G, R, steps = 18, 4, 64, 16, 3
+    gs = [W.random_3regular_graph(n, 3000 + i) for i in range(G)]
+    pos, vel, rp, rg = W.pso_inputs(G, R, steps, p, 4016)
+    eng = gpu_lib.QAOA(n, None, "complex64", graphs=gs, per_graph=R)
+    ex = eng.max_cut()
+    trace, best_pos, best_val = eng.pso(pos, vel, rp, rg)
+    eng.close()
+    assert np.all(np.diff(trace, axis=1) >= 0) and np.all(trace <= ex[:, None] + 1e-6)
+    for g in (0, 37, 63):
+        assert ex[g] == oq.maxcut_brute_force(n, gs[g])
+        e = oq.qaoa_energy(n, gs[g], best_pos[g, :p], best_pos[g, p:])
+        assert abs(e - best_val[g]) <= 2e-6
+    torch.cuda.empty_cache()
