@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the complex64 32q sweep and the QAOA sections")
     ap.add_argument("--pso-graphs", type=int, default=64, help="graphs of the particle-swarm section (0 skips it)")
+    ap.add_argument("--profile-ops", type=int, default=0, metavar="N",
+                    help="one small invocation of apply_kq, marginal and sample on N-qubit states (for ncu)")
     ap.add_argument("--profile-qaoa", default=None, metavar="N,P,BATCH",
                     help="run one complex64 QAOA energy + gradient evaluation of BATCH parameter sets and exit "
                          "(a small, fixed launch sequence for profilers)")
@@ -489,6 +491,28 @@ def ensemble_section(iqs, torch):
 
 
 # ---------------------------------------------------------------- GPU arm
+def profile_ops(n: int) -> int:
+    """Single invocations for a profiler: on an n-qubit complex64 and complex128
+    Gaussian state, apply_kq with k = 2..5 (complex64) or 2..4 (complex128) on
+    the lowest and the highest k qubits, one 10-qubit marginal and one
+    2^16-shot sampling call, each once."""
+    import paper_2001_10554_gb300 as iqs
+    import workloads as W
+    g = W.rng(5)
+    for dtype, ks in (("complex64", (2, 3, 4, 5)), ("complex128", (2, 3, 4))):
+        reg = iqs.Register(n, dtype)
+        reg.init_uniform()
+        for k in ks:
+            U = np.linalg.qr(g.normal(size=(1 << k, 1 << k)) + 1j * g.normal(size=(1 << k, 1 << k)))[0]
+            reg.apply_kq(list(range(k)), U)
+            reg.apply_kq(list(range(n - k, n)), U)
+        m = reg.marginal([0, 3, 7, 9, 12, 15, 20, n - 3, n - 2, n - 1])
+        s = reg.sample(g.uniform(size=1 << 16))
+        reg.close()
+        print(json.dumps({"dtype": dtype, "n": n, "marginal_sum": float(m.sum()), "sample_max": int(s.max())}))
+    return 0
+
+
 def profile_qaoa(spec: str) -> int:
     import paper_2001_10554_gb300 as iqs
     import workloads as W
@@ -508,6 +532,8 @@ def main(argv=None):
         return reference_arm(args)
     if args.profile_qaoa:
         return profile_qaoa(args.profile_qaoa)
+    if args.profile_ops:
+        return profile_ops(args.profile_ops)
 
     import torch
     import torch.distributed as dist

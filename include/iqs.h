@@ -177,8 +177,9 @@ iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out);
  * sum_{j <= i} |alpha_j|^2 exceeds u times the total weight (a zero-weight
  * index is never returned: where rounding leaves u * total at or above the
  * last cumulative value, the last index of nonzero weight).  Cumulative
- * weights are FP64; their rounding order (runs of 256 amplitudes, chunks of
- * 256 runs) differs from a sequential sum only by rounding.  IQS_EINVAL for a
+ * weights: FP64 between chunks of 65536 amplitudes, double-float (about
+ * 2^-44 of a chunk's weight) inside a chunk; the rounding order differs
+ * from a sequential sum only by rounding.  IQS_EINVAL for a
  * u outside [0, 1), NULL arrays, or a state of zero weight.  Temporary
  * device memory: N / 256 + 2 N / 65536 doubles plus 16 bytes per shot. */
 iqs_status iqs_sample(iqs_reg* reg, uint64_t shots, const double* uniforms, uint64_t* out);

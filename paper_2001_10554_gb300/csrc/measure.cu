@@ -16,16 +16,17 @@
 // order, so the result is deterministic.
 //
 // Sampling.  Three levels: elements in runs of E = 2^min(n, 8), runs grouped
-// into chunks of up to 256.  One pass stores every run's weight (df accumulated,
-// then FP64) and every chunk's weight; one block forms the chunk prefix P with
-// a chained scan (each thread scans a segment sequentially and the segment
+// into chunks of up to 256.  One pass stores every run's weight (double-float)
+// and every chunk's weight (FP64); one block forms the chunk prefix P with a
+// chained scan (each thread scans a segment sequentially and the segment
 // offsets are chained, so P never decreases and stays equal across chunks of
-// zero weight); each shot then binary-searches P and walks the chunk's runs
-// and the run's elements sequentially in FP64.  At every level the choice is
-// the first entry whose running value fl(base + running sum) exceeds the
-// target, else the last entry of nonzero weight (rounding can leave the target
-// above the level's last running value); either way an index of zero weight is
-// never returned.
+// zero weight); each shot then binary-searches P in FP64 and walks the chunk's
+// runs and the run's elements sequentially in double-float (FP32 pipe), against
+// its target taken relative to the level's base (about 2^-44 of the chunk's
+// weight).  At every level the choice is the first entry of nonzero weight
+// whose running sum exceeds the target, else the last entry of nonzero weight
+// (rounding can leave the target above the level's last running value); a
+// zero-weight entry leaves the running sum unchanged and is never chosen.
 #include <algorithm>
 #include <cstring>
 
@@ -58,29 +59,51 @@ __device__ __forceinline__ void abs2(double2 a, float& p, float& e, unsigned& ba
 
 // Grid (gx, 2^ky); partials[(y * gx + bx) * (2^kl * 2^KR) + pl * 2^KR + rb].
 template <class V, int KR>
-__global__ void __launch_bounds__(kThreads) k_marginal(const V* __restrict__ a, uint64_t n_groups, MargPlan P,
-                                                       double* __restrict__ partials, unsigned* flag) {
+__global__ void __launch_bounds__(kThreads, 2) k_marginal(const V* __restrict__ a, uint64_t n_groups, MargPlan P,
+                                                          double* __restrict__ partials, unsigned* flag) {
   constexpr int R = 1 << KR;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t yoff = 0;
-  for (int j = 0; j < P.ky; ++j) yoff |= (uint64_t)((blockIdx.y >> j) & 1u) << P.ypos[j];
-  uint64_t roff[R];
-#pragma unroll
-  for (int m = 0; m < R; ++m) {
+  __shared__ uint64_t roff[R];  // register bin m -> index offset (with this slice's bits)
+  if (threadIdx.x < R) {
     uint64_t o = 0;
-#pragma unroll
-    for (int j = 0; j < KR; ++j) o |= (uint64_t)((m >> j) & 1) << P.rpos[j];
-    roff[m] = o | yoff;
+    for (int j = 0; j < P.ky; ++j) o |= (uint64_t)((blockIdx.y >> j) & 1u) << P.ypos[j];
+    for (int j = 0; j < KR; ++j) o |= (uint64_t)((threadIdx.x >> j) & 1u) << P.rpos[j];
+    roff[threadIdx.x] = o;
   }
+  __syncthreads();
   dfx::Acc acc[R];
   unsigned bad = 0;
-  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_groups; g += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t base = g;
-    for (int j = 0; j < P.kz; ++j) base = insert_zero(base, P.zpos[j]);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  // two groups per iteration: 2^(KR+1) independent loads in flight per thread
+  for (; g + stride < n_groups; g += 2 * stride) {
+    uint64_t b0 = g, b1 = g + stride;
+    for (int j = 0; j < P.kz; ++j) {
+      b0 = insert_zero(b0, P.zpos[j]);
+      b1 = insert_zero(b1, P.zpos[j]);
+    }
+    V x0[R], x1[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      x0[m] = a[b0 + roff[m]];
+      x1[m] = a[b1 + roff[m]];
+    }
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       float p, e;
-      abs2(a[base + roff[m]], p, e, bad);
+      abs2(x0[m], p, e, bad);
+      acc[m].add(p, e);
+      abs2(x1[m], p, e, bad);
+      acc[m].add(p, e);
+    }
+  }
+  if (g < n_groups) {
+    uint64_t b0 = g;
+    for (int j = 0; j < P.kz; ++j) b0 = insert_zero(b0, P.zpos[j]);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      float p, e;
+      abs2(a[b0 + roff[m]], p, e, bad);
       acc[m].add(p, e);
     }
   }
@@ -170,11 +193,11 @@ struct SampleGeo {
   uint64_t n_chunks;
 };
 
-// One block per chunk: run weights (df per lane, FP64 per run) and the chunk
-// weight (FP64, runs in order).
+// One block per chunk: run weights (double-float, kept as (h, l) float
+// pairs for the walks) and the chunk weight (FP64, runs in order).
 template <class V>
 __global__ void __launch_bounds__(kThreads) k_sample_runs(const V* __restrict__ a, SampleGeo G,
-                                                          double* __restrict__ run_w, double* __restrict__ chunk_w,
+                                                          float2* __restrict__ run_w, double* __restrict__ chunk_w,
                                                           unsigned* flag) {
   __shared__ double sw[256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -206,9 +229,8 @@ __global__ void __launch_bounds__(kThreads) k_sample_runs(const V* __restrict__ 
         }
       }
       if (lane == 0) {
-        const double w = acc.value();
-        run_w[run] = w;
-        sw[s] = w;
+        run_w[run] = make_float2(acc.h, acc.l);
+        sw[s] = acc.value();
       }
     }
     __syncthreads();
@@ -222,13 +244,15 @@ __global__ void __launch_bounds__(kThreads) k_sample_runs(const V* __restrict__ 
   if (bad) atomicOr(flag, 1u);
 }
 
-// One block of 1024 threads: prefix[b] = weight of chunks before b, chained
-// (see the file comment); prefix[n_chunks] = total.
-__global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__ chunk_w, uint64_t n_chunks,
+// One block: prefix[b] = weight of chunks before b, chained (see the file
+// comment); prefix[n_chunks] = total.  ``active`` threads (about the square
+// root of n_chunks, so the sequential segment sums and the sequential chain of
+// segment offsets are both short) each own one segment.
+__global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__ chunk_w, uint64_t n_chunks, int active,
                                                       double* __restrict__ prefix) {
   __shared__ double seg[1025];
-  const uint64_t per = (n_chunks + blockDim.x - 1) / blockDim.x;
-  const uint64_t lo = threadIdx.x * per;
+  const uint64_t per = (n_chunks + active - 1) / active;
+  const uint64_t lo = threadIdx.x < (unsigned)active ? threadIdx.x * per : n_chunks;
   const uint64_t hi = min(lo + per, n_chunks);
   double r = 0.0;
   for (uint64_t b = lo; b < hi; ++b) r += chunk_w[b];
@@ -236,16 +260,16 @@ __global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__
   __syncthreads();
   if (threadIdx.x == 0) {
     double o = 0.0;
-    seg[0] = 0.0;
-    for (unsigned t = 0; t < blockDim.x; ++t) {
+    for (int t = 0; t < active; ++t) {
       const double w = seg[t + 1];
       seg[t] = o;
       o = o + w;
     }
-    seg[blockDim.x] = o;
+    seg[active] = o;
     prefix[n_chunks] = o;
   }
   __syncthreads();
+  if (threadIdx.x >= (unsigned)active) return;
   const double base = seg[threadIdx.x];
   r = 0.0;
   for (uint64_t b = lo; b < hi; ++b) {
@@ -254,16 +278,18 @@ __global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__
   }
 }
 
-__device__ __forceinline__ double weight(float2 v) {
-  const double re = (double)v.x, im = (double)v.y;
-  return fma(re, re, im * im);
-}
-__device__ __forceinline__ double weight(double2 v) { return fma(v.x, v.x, v.y * v.y); }
 
-// One thread per shot.  out[s] = sampled index, or ~0 when the state has zero weight.
+
+// (r - target) > 0 for a double-float running sum r and target (th, tl).
+__device__ __forceinline__ bool above(const dfx::Acc& r, float th, float tl) { return (r.h - th) + (r.l - tl) > 0.f; }
+
+// One thread per shot.  out[s] = sampled index, or ~0 when the state has zero
+// weight.  Below the chunk level the walks run in double-float on the FP32
+// pipe, against a target taken relative to the level's base: an entry of
+// zero weight leaves the running sum unchanged and is never picked.
 template <class V>
 __global__ void __launch_bounds__(kThreads) k_sample_draw(const V* __restrict__ a, SampleGeo G,
-                                                          const double* __restrict__ run_w,
+                                                          const float2* __restrict__ run_w,
                                                           const double* __restrict__ prefix,
                                                           const double* __restrict__ u, uint64_t shots,
                                                           unsigned long long* __restrict__ out) {
@@ -287,25 +313,33 @@ __global__ void __launch_bounds__(kThreads) k_sample_draw(const V* __restrict__ 
     b = G.n_chunks - 1;
     while (b > 0 && !(prefix[b + 1] > prefix[b])) --b;
   }
-  // run within the chunk: first run whose running value exceeds t, else the
-  // last run of nonzero weight; ``start`` is the running value before it
+  // run within the chunk: the first run of nonzero weight whose running sum
+  // exceeds the target, else the last run of nonzero weight.  Weights are
+  // read 8 at a time so their loads overlap; the walk itself is sequential.
   const int runs = 1 << G.c;
-  const double base = prefix[b];
-  const double* rw = run_w + b * (uint64_t)runs;
+  const float2* rw = run_w + b * (uint64_t)runs;
+  double tau = t - prefix[b];
+  float th = (float)tau, tl = (float)(tau - (double)th);
+  dfx::Acc r, pick_start, nz_start;
   int pick = -1, last_nz = 0;
-  double r = 0.0, pick_start = base, nz_start = base;
-  for (int j = 0; j < runs; ++j) {
-    const double w = rw[j];
-    const double start = base + r;
-    r += w;
-    if (w > 0.0) {
-      last_nz = j;
-      nz_start = start;
-    }
-    if (t < base + r) {
-      pick = j;
-      pick_start = start;
-      break;
+  for (int j0 = 0; j0 < runs && pick < 0; j0 += 8) {
+    float2 w8[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) w8[q] = j0 + q < runs ? rw[j0 + q] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (pick < 0 && j0 + q < runs) {
+        const dfx::Acc start = r;
+        r.add(w8[q].x, w8[q].y);
+        if (w8[q].x != 0.f || w8[q].y != 0.f) {
+          last_nz = j0 + q;
+          nz_start = start;
+          if (above(r, th, tl)) {
+            pick = j0 + q;
+            pick_start = start;
+          }
+        }
+      }
     }
   }
   if (pick < 0) {
@@ -313,18 +347,31 @@ __global__ void __launch_bounds__(kThreads) k_sample_draw(const V* __restrict__ 
     pick_start = nz_start;
   }
   // element within the run, the same rule
+  tau -= (double)pick_start.h + (double)pick_start.l;
+  th = (float)tau;
+  tl = (float)(tau - (double)th);
   const int E = 1 << G.e;
   const uint64_t run = b * (uint64_t)runs + pick;
   const V* p = a + run * (uint64_t)E;
   int el = -1, el_nz = 0;
-  r = 0.0;
-  for (int j = 0; j < E; ++j) {
-    const double w = weight(p[j]);
-    r += w;
-    if (w > 0.0) el_nz = j;
-    if (t < pick_start + r) {
-      el = j;
-      break;
+  unsigned unused = 0;
+  dfx::Acc r2;
+  for (int j0 = 0; j0 < E && el < 0; j0 += 8) {
+    V x8[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (j0 + q < E) x8[q] = p[j0 + q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (el < 0 && j0 + q < E) {
+        float pp, ee;
+        abs2(x8[q], pp, ee, unused);
+        r2.add(pp, ee);
+        if (pp != 0.f || ee != 0.f) {
+          el_nz = j0 + q;
+          if (above(r2, th, tl)) el = j0 + q;
+        }
+      }
     }
   }
   if (el < 0) el = el_nz;
@@ -336,6 +383,30 @@ __global__ void __launch_bounds__(kThreads) k_sample_draw(const V* __restrict__ 
 int max_marginal_qubits() { return kMaxMarginal; }
 
 namespace {
+
+template <class V, int KR>
+int occupancy_of() {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_marginal<V, KR>, kThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 2;
+    }
+    per_sm = std::max(per_sm, 1);
+  }
+  return per_sm;
+}
+
+int marginal_blocks_per_sm(int dtype, int kr) {
+  const bool c64 = dtype == IQS_C64;
+  switch (kr) {
+    case 0: return c64 ? occupancy_of<float2, 0>() : occupancy_of<double2, 0>();
+    case 1: return c64 ? occupancy_of<float2, 1>() : occupancy_of<double2, 1>();
+    case 2: return c64 ? occupancy_of<float2, 2>() : occupancy_of<double2, 2>();
+    case 3: return c64 ? occupancy_of<float2, 3>() : occupancy_of<double2, 3>();
+    default: return c64 ? occupancy_of<float2, 4>() : occupancy_of<double2, 4>();
+  }
+}
 
 struct MarginalLaunch {
   MargPlan P;
@@ -377,9 +448,10 @@ MarginalLaunch plan_marginal(const iqs_reg* r, int k, const int* qubits) {
   }
   M.kl = P.kl;
   M.kr = L.kr;
+  // one resident wave: blocks per SM (from the occupancy of this variant) x SMs, over the slices
   const uint64_t n_groups = num_amps(r) >> (L.kr + P.ky);
   const uint64_t gx = (n_groups + kThreads - 1) / kThreads;
-  const uint64_t cap = std::max<uint64_t>(1, (uint64_t)(4 * kSMs) >> P.ky);
+  const uint64_t cap = std::max<uint64_t>(1, (uint64_t)(marginal_blocks_per_sm(r->dtype, L.kr) * kSMs) >> P.ky);
   L.gx = std::min(gx, cap);
   M.gx = (int)L.gx;
   return L;
@@ -443,8 +515,8 @@ size_t sample_scratch_bytes(int n) {
 cudaError_t launch_sample(iqs_reg* r, uint64_t shots, const double* u_dev, unsigned long long* out_dev,
                           double* scratch) {
   const SampleGeo G = sample_geo(r->n);
-  double* run_w = scratch;
-  double* chunk_w = run_w + G.n_runs;
+  float2* run_w = reinterpret_cast<float2*>(scratch);  // n_runs (h, l) pairs: 8 bytes each
+  double* chunk_w = scratch + G.n_runs;
   double* prefix = chunk_w + G.n_chunks;
   const unsigned gblocks = (unsigned)std::min<uint64_t>(G.n_chunks, 16ull * kSMs);
   const unsigned dblocks = (unsigned)((shots + kThreads - 1) / kThreads);
@@ -454,7 +526,10 @@ cudaError_t launch_sample(iqs_reg* r, uint64_t shots, const double* u_dev, unsig
     k_sample_runs<double2><<<gblocks, kThreads, 0, r->stream>>>((const double2*)r->data, G, run_w, chunk_w, r->flag);
   cudaError_t e = launched(1);
   if (e != cudaSuccess) return e;
-  k_sample_scan<<<1, 1024, 0, r->stream>>>(chunk_w, G.n_chunks, prefix);
+  int lg = 0;
+  while ((1ull << lg) < G.n_chunks) ++lg;
+  const int active = std::min(1024, 1 << ((lg + 1) / 2));
+  k_sample_scan<<<1, 1024, 0, r->stream>>>(chunk_w, G.n_chunks, active, prefix);
   if ((e = launched(1)) != cudaSuccess) return e;
   if (shots == 0) return cudaSuccess;
   if (r->dtype == IQS_C64)
