@@ -209,22 +209,57 @@ __global__ void __launch_bounds__(kThreads) k_kgate_c64_tiled(float2* __restrict
   for (int h = 0; h < D; ++h)
     if (threadIdx.x == 0) hoff[h] = P.hoff[h];
   const uint32_t tmask = (1u << P.t) - 1u;
-  for (uint64_t tau = blockIdx.x; tau < n_tiles; tau += gridDim.x) {
+  constexpr int LPT = S / 2 / kThreads;  // 16-byte loads per thread per tile
+  auto tile_base = [&](uint64_t tau) {
     uint64_t gbase = tau << P.t;
 #pragma unroll
     for (int j = 0; j < K; ++j)
       if (j < P.kh) gbase = insert_zero(gbase, P.hpos[j]);
+    return gbase;
+  };
+  // Software pipeline through registers: the next tile's loads are issued
+  // before this tile's compute and store phases, so HBM latency overlaps them.
+  // (k = 5 keeps its registers for the 32-amplitude groups and loads each
+  // tile just before it is used.)
+  constexpr bool kPipe = K <= 4;
+  float4 pre[LPT];
+  __syncthreads();  // hoff is visible
+  if (kPipe && blockIdx.x < n_tiles) {
+    const uint64_t gbase = tile_base(blockIdx.x);
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const uint32_t e = 2 * (threadIdx.x + k * kThreads);
+      pre[k] = *reinterpret_cast<const float4*>(a + (gbase | (e & tmask) | hoff[e >> P.t]));
+    }
+  }
+  for (uint64_t tau = blockIdx.x; tau < n_tiles; tau += gridDim.x) {
+    const uint64_t gbase = tile_base(tau);
+    if constexpr (!kPipe) {
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const uint32_t e = 2 * (threadIdx.x + k * kThreads);
+        pre[k] = *reinterpret_cast<const float4*>(a + (gbase | (e & tmask) | hoff[e >> P.t]));
+      }
+    }
     __syncthreads();  // the previous tile's stores have read the buffer
-#pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < S / 2; i += kThreads) {
-      const uint32_t e = 2 * i;
-      const uint64_t gi = gbase | (e & tmask) | hoff[e >> P.t];
-      float4 v = *reinterpret_cast<const float4*>(a + gi);
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const uint32_t e = 2 * (threadIdx.x + k * kThreads);
       const uint32_t sw = tile_swz<K>(e, P);
+      float4 v = pre[k];
       if (sw & 1u) v = make_float4(v.z, v.w, v.x, v.y);
       *reinterpret_cast<float4*>(tile + ((e ^ sw) & ~1u)) = v;
     }
     __syncthreads();
+    const uint64_t nxt = tau + gridDim.x;
+    if (kPipe && nxt < n_tiles) {
+      const uint64_t nbase = tile_base(nxt);
+#pragma unroll
+      for (int k = 0; k < LPT; ++k) {
+        const uint32_t e = 2 * (threadIdx.x + k * kThreads);
+        pre[k] = *reinterpret_cast<const float4*>(a + (nbase | (e & tmask) | hoff[e >> P.t]));
+      }
+    }
 #pragma unroll 1
     for (int j = 0; j < GPT; ++j) {
       uint32_t gb = threadIdx.x + j * kThreads;
@@ -247,14 +282,13 @@ __global__ void __launch_bounds__(kThreads) k_kgate_c64_tiled(float2* __restrict
       }
     }
     __syncthreads();
-#pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < S / 2; i += kThreads) {
-      const uint32_t e = 2 * i;
-      const uint64_t gi = gbase | (e & tmask) | hoff[e >> P.t];
+#pragma unroll
+    for (int k = 0; k < LPT; ++k) {
+      const uint32_t e = 2 * (threadIdx.x + k * kThreads);
       const uint32_t sw = tile_swz<K>(e, P);
       float4 v = *reinterpret_cast<const float4*>(tile + ((e ^ sw) & ~1u));
       if (sw & 1u) v = make_float4(v.z, v.w, v.x, v.y);
-      *reinterpret_cast<float4*>(a + gi) = v;
+      *reinterpret_cast<float4*>(a + (gbase | (e & tmask) | hoff[e >> P.t])) = v;
     }
   }
 }
