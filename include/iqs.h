@@ -326,6 +326,17 @@ iqs_status iqs_pool_destroy(iqs_pool* p);
  * brick circuit on n qubits: sum over layers of n + 2 x (CNOTs in the layer). */
 int iqs_pool_noise_count(int n, int depth);
 
+/* Execution engine of iqs_pool_run_brick: 0 (default) picks the
+ * cluster-resident engine when a state fits, 1 forces the tiled passes
+ * (two passes over every state per layer through HBM), 2 forces the
+ * cluster-resident engine: each trajectory lives in the distributed shared
+ * memory of a thread-block cluster (up to 8 CTAs of 128 KB) for the whole
+ * circuit, and its state is written to HBM once at the end.  It takes
+ * complex64 states of 8..17 qubits and complex128 of 8..16; mode 2 on a
+ * state that does not fit is IQS_EINVAL.  Mode 0 uses it for complex64 only.  Results agree within the
+ * rounding of the dtype (the gates are grouped differently). */
+iqs_status iqs_pool_set_engine(iqs_pool* p, int engine);
+
 /* Run ``batch`` trajectories from |0...0>.  ``unitaries``: host doubles
  * [depth][n][8] (each U row-major as (re, im) pairs).  ``angles``: host
  * doubles [batch][iqs_pool_noise_count(n, depth)][2] = (tx, tz) in the order

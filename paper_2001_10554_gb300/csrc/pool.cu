@@ -32,6 +32,12 @@
 #include "pool_common.cuh"
 
 namespace iqs {
+
+// pool_cluster.cu
+bool pool_cluster_eligible(int n, int dtype);
+cudaError_t launch_pool_cluster(const void* allm, int n, int dtype, int phases, int depth, int batch, void* psi,
+                                double* probs, cudaStream_t s);
+
 namespace {
 
 using qops::S2;
@@ -42,8 +48,10 @@ using namespace iqs::pool;
 // qubits [q_lo, q_hi) (all inside the gate bits), then the CNOTs whose
 // controls are the local bits in ``cmask``.
 template <class TR>
-__global__ void __launch_bounds__(kThreads) k_pool_pass(typename TR::V* __restrict__ psi, uint64_t N, Geo g, int q_lo,
-                                                        int q_hi, unsigned cmask, Circuit circ, int layer,
+__global__ void __launch_bounds__(kThreads, TR::kMinBlocks) k_pool_pass(typename TR::V* __restrict__ psi, uint64_t N, Geo g, int q_lo,
+                                                        int q_hi, unsigned cmask,
+                                                        const typename TR::Mat* __restrict__ allm, int phases, int nq,
+                                                        int layer,
                                                         unsigned* flag) {
   using W = typename TR::W;
   using Mat = typename TR::Mat;
@@ -56,7 +64,8 @@ __global__ void __launch_bounds__(kThreads) k_pool_pass(typename TR::V* __restri
   const unsigned T = 1u << K;
   const unsigned b = blockIdx.y;
   const int ng = q_hi - q_lo;
-  if ((int)threadIdx.x < ng) mats[threadIdx.x] = TR::make(compose(circ, b, layer, q_lo + threadIdx.x));
+  // fused matrices composed once per run by k_pool_compose: [b][phase][qubit]
+  if ((int)threadIdx.x < ng) mats[threadIdx.x] = allm[((uint64_t)b * phases + layer) * nq + q_lo + threadIdx.x];
   __syncthreads();
   // local bit of qubit q: q - s + c for a high pass, q for the low pass
   const int lb0 = (g.c == 0 && g.s == 0) ? q_lo : (q_lo - g.s + g.c);
@@ -65,6 +74,20 @@ __global__ void __launch_bounds__(kThreads) k_pool_pass(typename TR::V* __restri
   unsigned bad = 0;
   for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) pool_tile<TR>(sp, mats, P, g, t, lb0, ng, cmask, bad);
   if (bad) atomicOr(flag, 1u);
+}
+
+// Fused one-qubit matrix of every (trajectory, phase, qubit), composed once
+// in FP64 (sincos of the noise angles) instead of once per tile.
+template <class TR>
+__global__ void k_pool_compose(Circuit C, int batch, int phases, typename TR::Mat* __restrict__ out) {
+  const uint64_t total = (uint64_t)batch * phases * C.n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i % C.n);
+    const uint64_t bl = i / C.n;
+    const int l = (int)(bl % phases);
+    const int b = (int)(bl / phases);
+    out[i] = TR::make(compose(C, b, l, q));
+  }
 }
 
 template <class V>
@@ -145,12 +168,14 @@ struct iqs_pool {
   double* U = nullptr;
   double* angles = nullptr;
   int* layer_base = nullptr;
+  void* mats = nullptr;  // [batch_max][depth_max + 1][n] fused matrices in the kernel's format
   double* partials = nullptr;
   double* probs = nullptr;
   double* mean = nullptr;
   unsigned* flag = nullptr;
   size_t angle_cap = 0;  // doubles
   int part_stride = 0, nblk = 0;
+  int engine = 0;  // 0 auto (cluster-resident when the state fits), 1 tiled passes, 2 cluster-resident
 };
 
 namespace iqs {
@@ -203,11 +228,26 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
   cudaStream_t s = P->stream;
   V* psi = (V*)P->psi;
   int launches = 0;
-  k_basis0_batch<V><<<grid_for(N * batch, 1, 16), kThreads, 0, s>>>(psi, N, batch);
-  ++launches;
   Circuit C{P->n, depth, P->U, noisy ? P->angles : nullptr, P->layer_base, n_noise_ops(P->n, depth)};
   const std::vector<Pass> passes = plan_pool(P->n, TR::kTileBits, TR::kRowBits);
   const int phases = noisy ? depth + 1 : depth;
+  using Mat = typename TR::Mat;
+  Mat* allm = (Mat*)P->mats;
+  k_pool_compose<TR><<<grid_for((uint64_t)batch * phases * P->n, 1, 8), kThreads, 0, s>>>(C, batch, phases, allm);
+  ++launches;
+  // auto: the cluster-resident engine for complex64; complex128 runs faster in the tiled passes
+  const bool cluster = P->engine == 2 || (P->engine == 0 && P->dtype == IQS_C64 && pool_cluster_eligible(P->n, P->dtype));
+  if (cluster) {
+    // the whole circuit of every trajectory in one launch, states resident in cluster shared memory
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) note_launches(launches);
+    if (e == cudaSuccess) e = launch_pool_cluster(allm, P->n, P->dtype, phases, depth, batch, P->psi, P->probs, s);
+    if (e != cudaSuccess) return e;
+    k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
+    return launched(1);
+  }
+  k_basis0_batch<V><<<grid_for(N * batch, 1, 16), kThreads, 0, s>>>(psi, N, batch);
+  ++launches;
   for (int l = 0; l < phases; ++l) {
     for (const Pass& p : passes) {
       const unsigned K = p.g.c + p.g.m;
@@ -215,8 +255,8 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
       const unsigned gx = (unsigned)std::min<uint64_t>(tiles, (uint64_t)std::max(1, 2432 / batch));
       const unsigned cm = l < depth ? cnot_mask(p, P->n, l) : 0u;
       const size_t smem = ((size_t)1 << K) * sizeof(typename TR::W);
-      k_pool_pass<TR><<<dim3(std::max(1u, gx), batch), kThreads, smem, s>>>(psi, N, p.g, p.q_lo, p.q_hi, cm, C, l,
-                                                                            P->flag);
+      k_pool_pass<TR><<<dim3(std::max(1u, gx), batch), kThreads, smem, s>>>(psi, N, p.g, p.q_lo, p.q_hi, cm, allm,
+                                                                            phases, P->n, l, P->flag);
       ++launches;
     }
   }
@@ -241,6 +281,7 @@ void free_pool(iqs_pool* p) {
   cudaFree(p->U);
   cudaFree(p->angles);
   cudaFree(p->layer_base);
+  cudaFree(p->mats);
   cudaFree(p->partials);
   cudaFree(p->probs);
   cudaFree(p->mean);
@@ -287,6 +328,8 @@ iqs_status iqs_pool_create(int n, int dtype, int batch_max, int depth_max, void*
                   cudaMalloc(&p->U, sizeof(double) * 8 * (size_t)n * depth_max) == cudaSuccess &&
                   cudaMalloc(&p->angles, sizeof(double) * p->angle_cap) == cudaSuccess &&
                   cudaMalloc(&p->layer_base, sizeof(int) * (size_t)depth_max) == cudaSuccess &&
+                  cudaMalloc(&p->mats, (dtype == IQS_C128 ? sizeof(P128::Mat) : sizeof(P64::Mat)) * (size_t)batch_max *
+                                           (size_t)(depth_max + 1) * (size_t)n) == cudaSuccess &&
                   cudaMalloc(&p->partials, sizeof(double) * (size_t)p->part_stride * batch_max) == cudaSuccess &&
                   cudaMalloc(&p->probs, sizeof(double) * (size_t)n * batch_max) == cudaSuccess &&
                   cudaMalloc(&p->mean, sizeof(double) * (size_t)n) == cudaSuccess &&
@@ -314,6 +357,16 @@ iqs_status iqs_pool_destroy(iqs_pool* p) {
 }
 
 int iqs_pool_noise_count(int n, int depth) { return iqs::n_noise_ops(n, depth); }
+
+iqs_status iqs_pool_set_engine(iqs_pool* p, int engine) {
+  using namespace iqs;
+  if (p == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (engine < 0 || engine > 2) return report(IQS_EINVAL, "engine must be 0 (auto), 1 (tiled passes) or 2 (cluster)");
+  if (engine == 2 && !pool_cluster_eligible(p->n, p->dtype))
+    return report(IQS_EINVAL, "a %d-qubit state of this dtype does not fit a cluster's shared memory", p->n);
+  p->engine = engine;
+  return IQS_OK;
+}
 
 iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* unitaries, const double* angles,
                               double* probs, double* mean) {

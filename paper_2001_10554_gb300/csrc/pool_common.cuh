@@ -117,6 +117,7 @@ struct P64 {
     float r[4], i[4];
   };
   static constexpr int kTileBits = 12, kRowBits = 4, kRegBits = 4, kSwzBits = 4;
+  static constexpr int kMinBlocks = 3;  // resident pass blocks per SM the registers are sized for
   static constexpr bool kTmaSwizzle = false;
   __device__ static W load(V v, unsigned&) { return v; }
   __device__ static V store(const W& w) { return w; }
@@ -147,6 +148,7 @@ struct P128 {
     dfx::Coef c[16];  // rows out0.re, out0.im, out1.re, out1.im over (x0.re, x0.im, x1.re, x1.im)
   };
   static constexpr int kTileBits = 11, kRowBits = 3, kRegBits = 3, kSwzBits = 3;
+  static constexpr int kMinBlocks = 2;
   static constexpr bool kTmaSwizzle = false;
   __device__ static W load(V v, unsigned& bad) { return qops::to_split(v, bad); }
   __device__ static V store(const W& w) { return qops::from_split(w); }

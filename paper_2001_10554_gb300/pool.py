@@ -33,6 +33,10 @@ class Pool:
              C.byref(h))
         self._h = h
 
+    def set_engine(self, engine: str = "auto") -> None:
+        """"auto" (cluster-resident when a state fits), "passes" or "cluster"."""
+        call("iqs_pool_set_engine", self._h, {"auto": 0, "passes": 1, "cluster": 2}[engine])
+
     def run_brick(self, unitaries, angles=None):
         U = np.asarray(unitaries, dtype=np.complex128).reshape(-1, self.n, 2, 2)
         depth = U.shape[0]

@@ -157,3 +157,51 @@ def test_persistent_wait_limit_reports_timeout_and_recovers(gpu_lib):
     n, ops, ang = work[1]
     ref = oe.all_probabilities(oe.run_ops(n, ops))
     assert np.max(np.abs(res[1][0][0] - ref)) <= 1e-5
+
+
+# ---------------------------------------------------------------- cluster-resident engine
+@pytest.mark.parametrize("dtype,ns", [("complex64", (8, 12, 14, 15, 16, 17)), ("complex128", (8, 13, 15, 16))])
+def test_cluster_engine_matches_oracle_and_passes(gpu_lib, dtype, ns):
+    """Each trajectory resident in a thread-block cluster (1..8 CTAs): states and
+    probabilities against the oracle trajectory by trajectory, noisy and
+    noiseless, and against the tiled-pass engine on the same inputs."""
+    for n in ns:
+        depth, batch = 5, 3
+        ops = W.random_circuit_layers(n, depth, seed=1200 + n)
+        U = brick_unitaries(ops, n)
+        ang = W.rng(1300 + n).normal(0.0, 0.1, size=(batch, noise_count(n, depth), 2))
+        res = {}
+        for eng in ("passes", "cluster"):
+            pool = gpu_lib.Pool(n, dtype, batch_max=batch, depth_max=depth)
+            pool.set_engine(eng)
+            probs, mean = pool.run_brick(U, ang)
+            states = [pool.state(b).astype(np.complex128) for b in range(batch)]
+            p0, _ = pool.run_brick(U)                      # noiseless
+            s0 = pool.state(0).astype(np.complex128)
+            res[eng] = (probs, mean, states, p0, s0)
+            pool.close()
+        tol = 1e-12 if dtype == "complex128" else c64_tol(depth)
+        probs, mean, states, p0, s0 = res["cluster"]
+        per = []
+        for b in range(batch):
+            ref = oe.run_ops(n, oe.noisy_trajectory_ops(ops, ang[b]))
+            assert np.max(np.abs(states[b] - ref)) <= tol, (n, b)
+            pref = oe.all_probabilities(ref)
+            assert np.max(np.abs(probs[b] - pref)) <= (1e-12 if dtype == "complex128" else 4 * tol)
+            per.append(pref)
+        assert np.max(np.abs(mean - oe.pool_average(per))) <= (1e-12 if dtype == "complex128" else 4 * tol)
+        ref0 = oe.run_ops(n, ops)
+        assert np.max(np.abs(s0 - ref0)) <= tol
+        assert np.max(np.abs(p0[0] - oe.all_probabilities(ref0))) <= (1e-12 if dtype == "complex128" else 4 * tol)
+        # the two engines agree to the dtype's rounding
+        assert np.max(np.abs(res["passes"][0] - probs)) <= (1e-12 if dtype == "complex128" else 4 * tol)
+
+
+def test_cluster_engine_rejects_states_that_do_not_fit(gpu_lib):
+    from paper_2001_10554_gb300 import IQSError
+    for n, dtype in ((5, "complex64"), (18, "complex64"), (17, "complex128")):
+        pool = gpu_lib.Pool(n, dtype, batch_max=1, depth_max=2)
+        with pytest.raises(IQSError):
+            pool.set_engine("cluster")
+        pool.set_engine("auto")
+        pool.close()
