@@ -552,3 +552,49 @@ def test_swarm_converges_on_a_concave_quadratic():
                                          g.uniform(size=(steps, R)), g.uniform(size=(steps, R)), 0.66, 1.6, 0.62)
     assert best_val > -1e-8
     assert np.max(np.abs(best_pos - c)) < 1e-4
+
+
+# ---------------------------------------------------------------- T1/T2 noise gates
+@pytest.mark.parametrize("T1,T2,t", [(30.0, 15.0, 1.0), (500.0, 250.0, 1.0), (10.0, 20.0, 0.5), (5.0, 1.0, 0.3),
+                                     (2.0, 1.5, 0.2)])
+def test_t1t2_noise_gate_averages_to_the_twirled_decay_channel(T1, T2, t):
+    """Averaged over its Gaussian angles (Gauss-Hermite quadrature, exact to
+    rounding), the noise gate is the Pauli channel that keeps the identity,
+    multiplies the transverse Bloch components by exp(-t/T2) and the
+    longitudinal one by exp(-t/T1): the decay laws that T1 and T2 name."""
+    from oracle import noise
+    R = noise.averaged_channel_ptm(T1, T2, t)
+    expect = np.diag([1.0, np.exp(-t / T2), np.exp(-t / T2), np.exp(-t / T1)])
+    np.testing.assert_allclose(R, expect, rtol=0, atol=1e-12)
+
+
+def test_t1t2_sigmas_limits_and_validity():
+    from oracle import noise
+    assert noise.t1t2_sigmas(30.0, 15.0, 0.0) == (0.0, 0.0, 0.0)
+    sx, sy, sz = noise.t1t2_sigmas(10.0, 20.0, 1.0)           # T2 = 2 T1: no pure dephasing
+    assert sz == 0.0 and abs(sx * sx - 0.1) < 1e-15 and sx == sy
+    for bad in ((0.0, 1.0, 1.0), (1.0, 3.0, 1.0), (1.0, 1.0, -1.0)):
+        with pytest.raises(ValueError):
+            noise.t1t2_sigmas(*bad)
+
+
+def test_t1t2_trajectories_converge_to_the_decay_of_coherence():
+    """Monte Carlo: under k noise gates the trajectory average of <X> on |+>
+    approaches exp(-k t / T2) and of <Z> on |0> approaches exp(-k t / T1),
+    within 5 standard errors."""
+    from oracle import noise
+    g = W.rng(601)
+    T1, T2, t, k, traj = 20.0, 12.0, 1.0, 6, 4000
+    s = np.array(noise.t1t2_sigmas(T1, T2, t))
+    xs, zs = [], []
+    for _ in range(traj):
+        plus = np.array([1, 1], dtype=complex) / np.sqrt(2)
+        zero = np.array([1, 0], dtype=complex)
+        for _ in range(k):
+            plus = noise.noise_gate_matrix(s * g.normal(size=3)) @ plus
+            zero = noise.noise_gate_matrix(s * g.normal(size=3)) @ zero
+        xs.append(sv.expectation(plus, "X").real)
+        zs.append(sv.expectation(zero, "Z").real)
+    for vals, target in ((xs, np.exp(-k * t / T2)), (zs, np.exp(-k * t / T1))):
+        m, se = np.mean(vals), np.std(vals) / np.sqrt(traj)
+        assert abs(m - target) < 5 * se
