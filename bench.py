@@ -478,6 +478,22 @@ def ensemble_section(iqs, torch):
         m = np.array([r[1] for r in res])
         out[dtype]["one_launch"] = {"trajectories_per_s": round(circuits * traj / dt, 1), "seconds": round(dt, 3),
                                     "mean_diff_vs_per_circuit_max": float(np.max(np.abs(m - means[dtype])))}
+    # T1/T2 noise gates (T1 = 500 gate times, T2 = T1 / 2, as in the paper's
+    # noisy QAOA ensembles): same circuits, normal triples as the draws
+    for dtype in ("complex64", "complex128"):
+        pool = iqs.Pool(n, dtype, batch_max=traj, depth_max=max(depths))
+        pool.set_noise_t1t2(500.0, 250.0, 1.0)
+        draws = [W.noise_draws(traj, iqs.pool.noise_count(n, c["depth"]), 5000 + i) for i, c in enumerate(ens)]
+        pool.run_brick(Us[0][:2], draws[0][:, :iqs.pool.noise_count(n, 2)])  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(circuits):
+            pool.run_brick(Us[i], draws[i])
+        dt = time.perf_counter() - t0
+        pool.close()
+        torch.cuda.empty_cache()
+        out[dtype]["t1t2"] = {"trajectories_per_s": round(circuits * traj / dt, 1), "seconds": round(dt, 3),
+                              "model": "noise gates of one gate time, T1 = 500, T2 = 250 (RX.RY.RZ, Gaussian angles)"}
     # FP64 oracle on a bounded sample: 2 trajectories of the first circuit
     from oracle import ensemble as oe
     t0 = time.perf_counter()

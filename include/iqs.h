@@ -326,6 +326,20 @@ iqs_status iqs_pool_destroy(iqs_pool* p);
  * brick circuit on n qubits: sum over layers of n + 2 x (CNOTs in the layer). */
 int iqs_pool_noise_count(int n, int depth);
 
+/* Noise gates from relaxation and dephasing times (Section 2 and the pool
+ * appendix: SetNoiseTimescales(T1, T2), ApplyNoiseGate(qubit, duration)).
+ * After this call, every noise rotation of iqs_pool_run_brick is a noise
+ * gate of duration ``gate_time``: RX(s_x z_x), then RY(s_y z_y), then
+ * RZ(s_z z_z), and ``angles`` holds the standard normal draws
+ * [batch][iqs_pool_noise_count(n, depth)][3] = (z_x, z_y, z_z).  The
+ * deviations are s_x^2 = s_y^2 = t / T1 and s_z^2 = 2 t / T2 - t / T1, so the
+ * gate averaged over its draws is the Pauli-twirled relaxation and dephasing
+ * channel: Bloch components transverse to Z decay by exp(-t / T2), the Z
+ * component by exp(-t / T1).  (The paper cites other work for the angle law;
+ * this is the reading.)  Needs 0 < T2 <= 2 T1 and gate_time >= 0; T1 <= 0
+ * returns to the (tx, tz) angle pairs. */
+iqs_status iqs_pool_set_noise_t1t2(iqs_pool* p, double T1, double T2, double gate_time);
+
 /* Execution engine of iqs_pool_run_brick: 0 (default) picks the
  * cluster-resident engine when a state fits, 1 forces the tiled passes
  * (two passes over every state per layer through HBM), 2 forces the

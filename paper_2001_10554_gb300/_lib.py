@@ -84,6 +84,7 @@ SIGNATURES = {
     "iqs_pool_noise_count": ([C.c_int, C.c_int], C.c_int),
     "iqs_pool_run_brick": ([C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp], C.c_int),
     "iqs_pool_set_engine": ([C.c_void_p, C.c_int], C.c_int),
+    "iqs_pool_set_noise_t1t2": ([C.c_void_p, C.c_double, C.c_double, C.c_double], C.c_int),
     "iqs_pool_download_state": ([C.c_void_p, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
     "iqs_pool_many_create": ([C.c_int, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "iqs_pool_many_destroy": ([C.c_void_p], C.c_int),

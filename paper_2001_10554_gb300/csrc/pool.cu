@@ -176,6 +176,8 @@ struct iqs_pool {
   size_t angle_cap = 0;  // doubles
   int part_stride = 0, nblk = 0;
   int engine = 0;  // 0 auto (cluster-resident when the state fits), 1 tiled passes, 2 cluster-resident
+  int noise_model = 0;       // 0 angle pairs (tx, tz); 1 T1/T2 gates from normal triples
+  double sig[3] = {0, 0, 0};  // T1/T2 gate angle standard deviations (x, y, z)
 };
 
 namespace iqs {
@@ -229,6 +231,8 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
   V* psi = (V*)P->psi;
   int launches = 0;
   Circuit C{P->n, depth, P->U, noisy ? P->angles : nullptr, P->layer_base, n_noise_ops(P->n, depth)};
+  C.model = P->noise_model;
+  for (int k = 0; k < 3; ++k) C.sig[k] = P->sig[k];
   const std::vector<Pass> passes = plan_pool(P->n, TR::kTileBits, TR::kRowBits);
   const int phases = noisy ? depth + 1 : depth;
   using Mat = typename TR::Mat;
@@ -323,7 +327,7 @@ iqs_status iqs_pool_create(int n, int dtype, int batch_max, int depth_max, void*
   const size_t amp = dtype == IQS_C128 ? 16 : 8;
   p->nblk = (int)std::max<uint64_t>(1, std::min<uint64_t>(p->N / 4096, 64));
   p->part_stride = p->nblk * (kPoolMaxQubits + 1);
-  p->angle_cap = (size_t)batch_max * n_noise_ops(n, depth_max) * 2;
+  p->angle_cap = (size_t)batch_max * n_noise_ops(n, depth_max) * 3;  // pairs or triples
   const bool ok = cudaMalloc(&p->psi, amp * p->N * batch_max) == cudaSuccess &&
                   cudaMalloc(&p->U, sizeof(double) * 8 * (size_t)n * depth_max) == cudaSuccess &&
                   cudaMalloc(&p->angles, sizeof(double) * p->angle_cap) == cudaSuccess &&
@@ -358,6 +362,25 @@ iqs_status iqs_pool_destroy(iqs_pool* p) {
 
 int iqs_pool_noise_count(int n, int depth) { return iqs::n_noise_ops(n, depth); }
 
+iqs_status iqs_pool_set_noise_t1t2(iqs_pool* p, double T1, double T2, double gate_time) {
+  using namespace iqs;
+  if (p == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (T1 <= 0.0) {  // back to explicit angle pairs
+    p->noise_model = 0;
+    return IQS_OK;
+  }
+  if (!(T2 > 0.0) || T2 > 2.0 * T1 || !(gate_time >= 0.0) || !std::isfinite(T1) || !std::isfinite(gate_time))
+    return report(IQS_EINVAL, "need T1 > 0, 0 < T2 <= 2 T1 and a finite gate time >= 0");
+  // Bloch factors of the averaged gate: transverse exp(-t/T2), longitudinal
+  // exp(-t/T1); the rotation variances that give them (see the header)
+  const double vx = gate_time / T1, vz = 2.0 * gate_time / T2 - gate_time / T1;
+  p->sig[0] = std::sqrt(vx);
+  p->sig[1] = std::sqrt(vx);
+  p->sig[2] = std::sqrt(vz > 0.0 ? vz : 0.0);
+  p->noise_model = 1;
+  return IQS_OK;
+}
+
 iqs_status iqs_pool_set_engine(iqs_pool* p, int engine) {
   using namespace iqs;
   if (p == nullptr) return report(IQS_EINVAL, "handle is NULL");
@@ -387,7 +410,8 @@ iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* u
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->layer_base, base.data(), sizeof(int) * depth, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && angles)
-    e = cudaMemcpyAsync(p->angles, angles, sizeof(double) * 2 * (size_t)nn * batch, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(p->angles, angles, sizeof(double) * (p->noise_model == 1 ? 3 : 2) * (size_t)nn * batch,
+                        cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return report(IQS_ECUDA, "pool upload: %s", cudaGetErrorString(e));
   e = p->dtype == IQS_C128 ? run_pool<P128>(p, batch, depth, angles != nullptr)
                            : run_pool<P64>(p, batch, depth, angles != nullptr);

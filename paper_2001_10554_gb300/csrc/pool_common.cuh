@@ -63,16 +63,42 @@ __device__ __forceinline__ M2 noise_rot(double tx, double tz) {
   return m;
 }
 
+// RZ(tz) . RY(ty) . RX(tx): the T1/T2 noise gate (RX acts first).
+__device__ __forceinline__ M2 noise_rot3(double tx, double ty, double tz) {
+  double sy, cy;
+  sincos(0.5 * ty, &sy, &cy);
+  M2 ry;  // [[cy, -sy], [sy, cy]]
+  ry.r[0] = cy;  ry.i[0] = 0.0; ry.r[1] = -sy; ry.i[1] = 0.0;
+  ry.r[2] = sy;  ry.i[2] = 0.0; ry.r[3] = cy;  ry.i[3] = 0.0;
+  const M2 x = noise_rot(tx, 0.0);  // RX
+  const M2 z = noise_rot(0.0, tz);  // RZ
+  return mmul(z, mmul(ry, x));
+}
+
 struct Circuit {
   int n, depth;
   const double* U;          // [depth][n][8]
-  const double* angles;     // [batch][n_noise][2] or nullptr
+  const double* angles;     // [batch][n_noise][width] or nullptr
   const int* layer_base;    // [depth]: index of the first noise op of layer l
   int n_noise;
+  // noise model: 0 = angle pairs (tx, tz) as given (RX then RZ); 1 = T1/T2
+  // gates: standard normal triples scaled by sig (RX, RY, RZ)
+  int model = 0;
+  double sig[3] = {0.0, 0.0, 0.0};
+  __host__ __device__ int width() const { return model == 1 ? 3 : 2; }
 };
 
+// Noise rotation k of one trajectory whose draws start at ``ang``.
+__device__ __forceinline__ M2 noise_op(const Circuit& C, const double* ang, int k) {
+  if (C.model == 1) {
+    const double* z = ang + 3 * k;
+    return noise_rot3(C.sig[0] * z[0], C.sig[1] * z[1], C.sig[2] * z[2]);
+  }
+  return noise_rot(ang[2 * k], ang[2 * k + 1]);
+}
+
 // Fused one-qubit matrix of phase l (0..depth) for qubit q of one trajectory
-// whose angle pairs start at ``ang`` (nullptr: noiseless).
+// whose noise draws start at ``ang`` (nullptr: noiseless).
 __device__ __forceinline__ M2 compose_traj(const Circuit& C, const double* ang, int l, int q) {
   M2 G = identity2();
   if (ang && l > 0) {
@@ -83,7 +109,7 @@ __device__ __forceinline__ M2 compose_traj(const Circuit& C, const double* ang, 
       const int ctrl = o + 2 * j;
       if (ctrl + 1 < C.n) {
         const int k = C.layer_base[l - 1] + C.n + 2 * j + (q == ctrl ? 0 : 1);
-        G = noise_rot(ang[2 * k], ang[2 * k + 1]);
+        G = noise_op(C, ang, k);
       }
     }
   }
@@ -96,17 +122,14 @@ __device__ __forceinline__ M2 compose_traj(const Circuit& C, const double* ang, 
       U.i[e] = u[2 * e + 1];
     }
     G = mmul(U, G);
-    if (ang) {
-      const int k = C.layer_base[l] + q;
-      G = mmul(noise_rot(ang[2 * k], ang[2 * k + 1]), G);
-    }
+    if (ang) G = mmul(noise_op(C, ang, C.layer_base[l] + q), G);
   }
   return G;
 }
 
-// The same for trajectory b of a circuit whose angles are stored [b][n_noise][2].
+// The same for trajectory b of a circuit whose draws are stored [b][n_noise][width].
 __device__ __forceinline__ M2 compose(const Circuit& C, int b, int l, int q) {
-  return compose_traj(C, C.angles ? C.angles + (uint64_t)b * C.n_noise * 2 : nullptr, l, q);
+  return compose_traj(C, C.angles ? C.angles + (uint64_t)b * C.n_noise * C.width() : nullptr, l, q);
 }
 
 // ---------------------------------------------------------------- storage traits

@@ -37,6 +37,13 @@ class Pool:
         """"auto" (cluster-resident when a state fits), "passes" or "cluster"."""
         call("iqs_pool_set_engine", self._h, {"auto": 0, "passes": 1, "cluster": 2}[engine])
 
+    def set_noise_t1t2(self, T1: float, T2: float, gate_time: float) -> None:
+        """Noise gates of duration gate_time from T1/T2: ``angles`` of run_brick
+        become standard normal triples (batch, noise_count, 3).  T1 <= 0 restores
+        the (tx, tz) angle pairs."""
+        call("iqs_pool_set_noise_t1t2", self._h, C.c_double(T1), C.c_double(T2), C.c_double(gate_time))
+        self._width = 3 if T1 > 0 else 2
+
     def run_brick(self, unitaries, angles=None):
         U = np.asarray(unitaries, dtype=np.complex128).reshape(-1, self.n, 2, 2)
         depth = U.shape[0]
@@ -46,8 +53,9 @@ class Pool:
         else:
             a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64))
             batch = a.shape[0]
-            if a.shape[1:] != (noise_count(self.n, depth), 2):
-                raise ValueError(f"angles must have shape (batch, {noise_count(self.n, depth)}, 2)")
+            w = getattr(self, "_width", 2)
+            if a.shape[1:] != (noise_count(self.n, depth), w):
+                raise ValueError(f"angles must have shape (batch, {noise_count(self.n, depth)}, {w})")
             ap = a.ctypes.data_as(_dp)
         probs = np.empty((batch, self.n))
         mean = np.empty(self.n)

@@ -205,3 +205,46 @@ def test_cluster_engine_rejects_states_that_do_not_fit(gpu_lib):
             pool.set_engine("cluster")
         pool.set_engine("auto")
         pool.close()
+
+
+# ---------------------------------------------------------------- T1/T2 noise gates
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+@pytest.mark.parametrize("engine", ["passes", "cluster"])
+def test_t1t2_noise_gates_match_oracle(gpu_lib, dtype, engine):
+    """Noise gates of duration t from (T1, T2): the same standard normal draws
+    on both sides, trajectory by trajectory, and the pool mean."""
+    from oracle import noise as on
+    n, depth, batch = 10, 4, 3
+    T1, T2, tg = 30.0, 15.0, 1.0
+    ops = W.random_circuit_layers(n, depth, seed=1400)
+    U = brick_unitaries(ops, n)
+    z = W.rng(1401).normal(size=(batch, noise_count(n, depth), 3))
+    pool = gpu_lib.Pool(n, dtype, batch_max=batch, depth_max=depth)
+    pool.set_engine(engine)
+    pool.set_noise_t1t2(T1, T2, tg)
+    probs, mean = pool.run_brick(U, z)
+    tol = 1e-12 if dtype == "complex128" else c64_tol(depth)
+    per = []
+    for b in range(batch):
+        ref = oe.run_ops(n, on.t1t2_trajectory_ops(ops, z[b], T1, T2, tg))
+        assert np.max(np.abs(pool.state(b).astype(np.complex128) - ref)) <= tol
+        pref = oe.all_probabilities(ref)
+        assert np.max(np.abs(probs[b] - pref)) <= (1e-12 if dtype == "complex128" else 4 * tol)
+        per.append(pref)
+    assert np.max(np.abs(mean - oe.pool_average(per))) <= (1e-12 if dtype == "complex128" else 4 * tol)
+    # back to angle pairs on the same pool
+    pool.set_noise_t1t2(0.0, 0.0, 0.0)
+    ang = W.rng(1402).normal(0.0, 0.1, size=(batch, noise_count(n, depth), 2))
+    probs2, _ = pool.run_brick(U, ang)
+    ref = oe.run_ops(n, oe.noisy_trajectory_ops(ops, ang[1]))
+    assert np.max(np.abs(probs2[1] - oe.all_probabilities(ref))) <= (1e-12 if dtype == "complex128" else 4 * tol)
+    pool.close()
+
+
+def test_t1t2_rejects_unphysical_times(gpu_lib):
+    from paper_2001_10554_gb300 import IQSError
+    pool = gpu_lib.Pool(8, "complex64", batch_max=1, depth_max=2)
+    for T1, T2, tg in ((10.0, 25.0, 1.0), (10.0, 0.0, 1.0), (10.0, 5.0, -1.0)):
+        with pytest.raises(IQSError):
+            pool.set_noise_t1t2(T1, T2, tg)
+    pool.close()

@@ -211,3 +211,8 @@ def pso_inputs(graphs: int, particles: int, steps: int, p: int, seed: int):
     rp = g.uniform(size=(steps, graphs, particles))
     rg = g.uniform(size=(steps, graphs, particles))
     return pos, vel, rp, rg
+
+
+def noise_draws(trajectories: int, n_noise: int, seed: int) -> np.ndarray:
+    """Standard normal triples (trajectories, n_noise, 3) for T1/T2 noise gates."""
+    return rng(seed).normal(size=(trajectories, n_noise, 3))
