@@ -388,6 +388,15 @@ iqs_status iqs_pool_many_destroy(iqs_pool_many* w);
  * the first job's first wait can never be satisfied, so the timeout path runs. */
 iqs_status iqs_pool_many_set_wait_limit(iqs_pool_many* w, double seconds, int debug_never);
 
+/* Engine of iqs_pool_many_run: 0 (default) runs every trajectory of every
+ * circuit in one launch of the cluster-resident engine (see
+ * iqs_pool_set_engine) when the dtype is complex64 and every state fits one
+ * cluster size (qubit counts from 2 logc + 1 to the largest), else the
+ * persistent tiled kernel; 1 forces the persistent kernel (the only one with
+ * bounded waits and IQS_ETIMEOUT); 2 forces the cluster-resident engine
+ * (IQS_EINVAL at run time when a state does not fit). */
+iqs_status iqs_pool_many_set_engine(iqs_pool_many* w, int engine);
+
 /* Run all circuits (at most 8 distinct qubit counts per call) from |0...0>.
  * Outputs (host): probs = per-trajectory P(q = 1) (divided by the state's FP64
  * squared norm), concatenated circuit by circuit as [trajectories][n], or NULL;

@@ -88,6 +88,7 @@ SIGNATURES = {
     "iqs_pool_download_state": ([C.c_void_p, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
     "iqs_pool_many_create": ([C.c_int, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "iqs_pool_many_destroy": ([C.c_void_p], C.c_int),
+    "iqs_pool_many_set_engine": ([C.c_void_p, C.c_int], C.c_int),
     "iqs_pool_many_set_wait_limit": ([C.c_void_p, C.c_double, C.c_int], C.c_int),
     "iqs_pool_many_run": ([C.c_void_p, C.c_int, C.c_void_p, _dp, _dp], C.c_int),
     "iqs_probabilities_noalloc": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, _dp], C.c_int),

@@ -35,8 +35,7 @@ namespace iqs {
 
 // pool_cluster.cu
 bool pool_cluster_eligible(int n, int dtype);
-cudaError_t launch_pool_cluster(const void* allm, int n, int dtype, int phases, int depth, int batch, void* psi,
-                                double* probs, cudaStream_t s);
+cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s);
 
 namespace {
 
@@ -169,6 +168,7 @@ struct iqs_pool {
   double* angles = nullptr;
   int* layer_base = nullptr;
   void* mats = nullptr;  // [batch_max][depth_max + 1][n] fused matrices in the kernel's format
+  iqs::pool::ClusterJob* cjobs = nullptr;  // [batch_max] job table of the cluster-resident engine
   double* partials = nullptr;
   double* probs = nullptr;
   double* mean = nullptr;
@@ -245,7 +245,13 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
     // the whole circuit of every trajectory in one launch, states resident in cluster shared memory
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) note_launches(launches);
-    if (e == cudaSuccess) e = launch_pool_cluster(allm, P->n, P->dtype, phases, depth, batch, P->psi, P->probs, s);
+    std::vector<ClusterJob> jobs(batch);
+    for (int b = 0; b < batch; ++b)
+      jobs[b] = ClusterJob{allm + (uint64_t)b * phases * P->n, psi + (uint64_t)b * N, P->probs + (uint64_t)b * P->n,
+                           P->n, phases, depth};
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P->cjobs, jobs.data(), sizeof(ClusterJob) * batch, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_pool_cluster(P->cjobs, batch, P->n, P->dtype, s);
     if (e != cudaSuccess) return e;
     k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
     return launched(1);
@@ -286,6 +292,7 @@ void free_pool(iqs_pool* p) {
   cudaFree(p->angles);
   cudaFree(p->layer_base);
   cudaFree(p->mats);
+  cudaFree(p->cjobs);
   cudaFree(p->partials);
   cudaFree(p->probs);
   cudaFree(p->mean);
@@ -334,6 +341,7 @@ iqs_status iqs_pool_create(int n, int dtype, int batch_max, int depth_max, void*
                   cudaMalloc(&p->layer_base, sizeof(int) * (size_t)depth_max) == cudaSuccess &&
                   cudaMalloc(&p->mats, (dtype == IQS_C128 ? sizeof(P128::Mat) : sizeof(P64::Mat)) * (size_t)batch_max *
                                            (size_t)(depth_max + 1) * (size_t)n) == cudaSuccess &&
+                  cudaMalloc(&p->cjobs, sizeof(iqs::pool::ClusterJob) * (size_t)batch_max) == cudaSuccess &&
                   cudaMalloc(&p->partials, sizeof(double) * (size_t)p->part_stride * batch_max) == cudaSuccess &&
                   cudaMalloc(&p->probs, sizeof(double) * (size_t)n * batch_max) == cudaSuccess &&
                   cudaMalloc(&p->mean, sizeof(double) * (size_t)n) == cudaSuccess &&

@@ -21,7 +21,10 @@
 //      the phase.
 // After the last phase the state is written to HBM once (for inspection) and
 // P(q = 1) / norm of every qubit is reduced across the cluster, in a fixed
-// order.  HBM traffic per trajectory is that one write instead of two passes
+// order.  Work comes as a table of jobs (one per trajectory: its matrices,
+// qubit count, phases, and where its state and probabilities go), so one
+// launch covers trajectories of different circuits, depths and qubit counts
+// (all with the same cluster size).  HBM traffic per trajectory is that one write instead of two passes
 // over the state per layer.
 #include <algorithm>
 #include <cooperative_groups.h>
@@ -115,8 +118,7 @@ __device__ __forceinline__ void local_round_any(typename TR::W* st, const typena
 
 template <class TR, int LOGC>
 __global__ void __launch_bounds__(CT<TR>::kThreads, CT<TR>::kMinBlocks)
-    k_pool_cluster(const typename TR::Mat* __restrict__ allm, int n, int phases, int depth, int batch,
-                   typename TR::V* __restrict__ psi_out, double* __restrict__ probs) {
+    k_pool_cluster(const ClusterJob* __restrict__ jobs, int n_jobs) {
   constexpr int kCT = CT<TR>::kThreads;
   using W = typename TR::W;
   using Mat = typename TR::Mat;
@@ -124,21 +126,23 @@ __global__ void __launch_bounds__(CT<TR>::kThreads, CT<TR>::kMinBlocks)
   constexpr int RB = TR::kRegBits;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
-  const int L = n - LOGC;
-  const unsigned NL = 1u << L;
-  const uint64_t N = 1ull << n;
   extern __shared__ __align__(16) unsigned char raw[];
   W* st = reinterpret_cast<W*>(raw);
   __shared__ Mat mats[kPoolMaxQubits];
   __shared__ double part[C][kPoolMaxQubits + 1];  // read on rank 0: every rank's slice sums
   __shared__ double red[kCT / 32][kPoolMaxQubits + 1];
   const unsigned cid = blockIdx.x / C, ncl = gridDim.x / C;
-  for (unsigned b = cid; b < (unsigned)batch; b += ncl) {
+  for (unsigned jb = cid; jb < (unsigned)n_jobs; jb += ncl) {
+    const ClusterJob J = jobs[jb];
+    const int n = J.n, phases = J.phases, depth = J.depth;
+    const Mat* allm = static_cast<const Mat*>(J.mats);
+    const int L = n - LOGC;
+    const unsigned NL = 1u << L;
     for (unsigned i = threadIdx.x; i < NL; i += kCT) st[i] = zero_w<TR>();
     __syncthreads();
     if (rank == 0 && threadIdx.x == 0) st[0] = one_w<TR>();
     for (int l = 0; l < phases; ++l) {
-      if ((int)threadIdx.x < n) mats[threadIdx.x] = allm[((uint64_t)b * phases + l) * n + threadIdx.x];
+      if ((int)threadIdx.x < n) mats[threadIdx.x] = allm[(uint64_t)l * n + threadIdx.x];
       __syncthreads();
       for (int b0 = 0; b0 < L; b0 += RB) {
         local_round_any<TR, kCT>(st, mats, b0, min(RB, L - b0), NL);
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(CT<TR>::kThreads, CT<TR>::kMinBlocks)
       }
     }
     // the final state, once, to HBM (logical order)
-    typename TR::V* out = psi_out + (uint64_t)b * N + (uint64_t)rank * NL;
+    typename TR::V* out = static_cast<typename TR::V*>(J.psi) + (uint64_t)rank * NL;
     for (unsigned i = threadIdx.x; i < NL; i += kCT) out[i] = TR::store(st[phys(i)]);
     // P(q = 1) and the norm of this slice: double-float per thread, FP64
     // across; in groups of 8 sums (slot 24 is the norm) to bound registers
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(CT<TR>::kThreads, CT<TR>::kMinBlocks)
         if (q < L) pq += part[r][q];
         else if ((r >> (q - L)) & 1) pq += part[r][kPoolMaxQubits];
       }
-      probs[(uint64_t)b * n + q] = pq / norm;
+      J.probs[q] = pq / norm;
     }
     cl.sync();  // rank 0 has read part[] before any rank writes the next trajectory's sums
   }
@@ -252,10 +256,9 @@ int cluster_logc(int n, int dtype) {
 }
 
 template <class TR, int LOGC>
-cudaError_t launch_cluster_t(const void* allm, int n, int phases, int depth, int batch, void* psi, double* probs,
-                             cudaStream_t s) {
+cudaError_t launch_cluster_t(const ClusterJob* jobs, int n_jobs, int max_n, cudaStream_t s) {
   auto kern = k_pool_cluster<TR, LOGC>;
-  const size_t smem = ((size_t)1 << (n - LOGC)) * sizeof(typename TR::W);
+  const size_t smem = ((size_t)1 << (max_n - LOGC)) * sizeof(typename TR::W);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -273,37 +276,37 @@ cudaError_t launch_cluster_t(const void* allm, int n, int phases, int depth, int
   int clusters = 0;
   e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
   if (e != cudaSuccess) return e;
-  clusters = std::max(1, std::min(clusters, batch));
+  clusters = std::max(1, std::min(clusters, n_jobs));
   cfg.gridDim = dim3((unsigned)clusters << LOGC, 1, 1);
-  e = cudaLaunchKernelEx(&cfg, kern, (const typename TR::Mat*)allm, n, phases, depth, batch, (typename TR::V*)psi,
-                         probs);
-  return e;
+  return cudaLaunchKernelEx(&cfg, kern, jobs, n_jobs);
 }
 
 }  // namespace
 
 bool pool_cluster_eligible(int n, int dtype) { return cluster_logc(n, dtype) >= 0; }
 
-// One launch for all ``batch`` trajectories; allm holds the composed matrices
-// [batch][phases][n] in the dtype's kernel format.
-cudaError_t launch_pool_cluster(const void* allm, int n, int dtype, int phases, int depth, int batch, void* psi,
-                                double* probs, cudaStream_t s) {
-  const int lc = cluster_logc(n, dtype);
+int pool_cluster_logc(int n, int dtype) { return cluster_logc(n, dtype); }
+
+// Jobs of qubit counts in [2 logc + 1, max_n] on clusters of 2^logc CTAs
+// (logc = pool_cluster_logc(max_n, dtype)); ``jobs`` is a device array.
+cudaError_t launch_pool_cluster(const ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s) {
+  const int lc = cluster_logc(max_n, dtype);
   cudaError_t e = cudaErrorInvalidValue;
+  if (n_jobs < 1) return cudaSuccess;
   if (dtype == IQS_C128) {
     switch (lc) {
-      case 0: e = launch_cluster_t<P128, 0>(allm, n, phases, depth, batch, psi, probs, s); break;
-      case 1: e = launch_cluster_t<P128, 1>(allm, n, phases, depth, batch, psi, probs, s); break;
-      case 2: e = launch_cluster_t<P128, 2>(allm, n, phases, depth, batch, psi, probs, s); break;
-      case 3: e = launch_cluster_t<P128, 3>(allm, n, phases, depth, batch, psi, probs, s); break;
+      case 0: e = launch_cluster_t<P128, 0>(jobs, n_jobs, max_n, s); break;
+      case 1: e = launch_cluster_t<P128, 1>(jobs, n_jobs, max_n, s); break;
+      case 2: e = launch_cluster_t<P128, 2>(jobs, n_jobs, max_n, s); break;
+      case 3: e = launch_cluster_t<P128, 3>(jobs, n_jobs, max_n, s); break;
       default: break;
     }
   } else {
     switch (lc) {
-      case 0: e = launch_cluster_t<P64, 0>(allm, n, phases, depth, batch, psi, probs, s); break;
-      case 1: e = launch_cluster_t<P64, 1>(allm, n, phases, depth, batch, psi, probs, s); break;
-      case 2: e = launch_cluster_t<P64, 2>(allm, n, phases, depth, batch, psi, probs, s); break;
-      case 3: e = launch_cluster_t<P64, 3>(allm, n, phases, depth, batch, psi, probs, s); break;
+      case 0: e = launch_cluster_t<P64, 0>(jobs, n_jobs, max_n, s); break;
+      case 1: e = launch_cluster_t<P64, 1>(jobs, n_jobs, max_n, s); break;
+      case 2: e = launch_cluster_t<P64, 2>(jobs, n_jobs, max_n, s); break;
+      case 3: e = launch_cluster_t<P64, 3>(jobs, n_jobs, max_n, s); break;
       default: break;
     }
   }

@@ -132,6 +132,14 @@ __device__ __forceinline__ M2 compose(const Circuit& C, int b, int l, int q) {
   return compose_traj(C, C.angles ? C.angles + (uint64_t)b * C.n_noise * C.width() : nullptr, l, q);
 }
 
+// One trajectory for the cluster-resident engine.
+struct ClusterJob {
+  const void* mats;  // [phases][n] fused matrices in the dtype's Mat format
+  void* psi;         // the final state, 2^n amplitudes
+  double* probs;     // P(q = 1) / norm, n values
+  int n, phases, depth;
+};
+
 // ---------------------------------------------------------------- storage traits
 struct P64 {
   using V = float2;

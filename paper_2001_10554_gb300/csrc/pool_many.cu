@@ -17,6 +17,11 @@
 // Jobs are grouped by qubit count (one tile geometry per group) and, inside a
 // group, sorted by decreasing depth, so the jobs still alive at a step form a
 // prefix of the group and the ticket -> item decode is arithmetic.
+//
+// When every state fits a thread-block cluster (pool_cluster.cu), the same
+// job list instead runs on the cluster-resident engine: one compose launch
+// builds all fused matrices and one cluster launch runs every trajectory of
+// every circuit to its end, each state resident on chip.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,6 +34,11 @@
 #include "pool_common.cuh"
 
 namespace iqs {
+
+// pool_cluster.cu
+int pool_cluster_logc(int n, int dtype);
+cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s);
+
 namespace {
 
 using namespace iqs::pool;
@@ -203,6 +213,20 @@ __global__ void __launch_bounds__(kThreads) k_pool_persistent(typename TR::V* __
   if (bad) atomicOr(flag, 1u);
 }
 
+// Fused matrices of every job for the cluster-resident path: job j's
+// [phases][n] matrices start at mat_off[j]; blockIdx.y strides over jobs.
+template <class TR>
+__global__ void k_many_compose(const Job* __restrict__ jobs, int njobs, const uint64_t* __restrict__ mat_off,
+                               typename TR::Mat* __restrict__ mats) {
+  for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
+    const Job job = jobs[j];
+    const Circuit C{job.n, job.depth, job.U, job.ang, job.layer_base, job.n_noise};
+    const int total = job.phases * job.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+      mats[mat_off[j] + i] = TR::make(compose_traj(C, job.ang, i / job.n, i % job.n));
+  }
+}
+
 // |0...0> for every job (the arena is zeroed first).
 template <class V>
 __global__ void k_many_init(V* arena, const Job* __restrict__ jobs, int njobs) {
@@ -257,6 +281,9 @@ struct iqs_pool_many {
   size_t arena_bytes = 0;
   void* blob = nullptr;  // params, tables, jobs, counters, partials, outputs
   size_t blob_bytes = 0;
+  int engine = 0;         // 0 auto (cluster-resident for complex64 when every state fits), 1 persistent, 2 cluster
+  void* mats = nullptr;   // fused matrices of the cluster-resident path
+  size_t mats_bytes = 0;
 };
 
 namespace iqs {
@@ -331,6 +358,7 @@ iqs_status iqs_pool_many_destroy(iqs_pool_many* w) {
   cudaStreamSynchronize(w->stream);
   cudaFree(w->arena);
   cudaFree(w->blob);
+  cudaFree(w->mats);
   if (w->own_stream) cudaStreamDestroy(w->stream);
   delete w;
   return IQS_OK;
@@ -341,6 +369,13 @@ iqs_status iqs_pool_many_set_wait_limit(iqs_pool_many* w, double seconds, int de
   if (!(seconds > 0.0) || seconds > 600.0) return iqs::report(IQS_EINVAL, "wait limit must be in (0, 600] s");
   w->timeout_ns = (uint64_t)(seconds * 1e9);
   w->debug_never = debug_never ? 1 : 0;
+  return IQS_OK;
+}
+
+iqs_status iqs_pool_many_set_engine(iqs_pool_many* w, int engine) {
+  if (w == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (engine < 0 || engine > 2) return iqs::report(IQS_EINVAL, "engine must be 0 (auto), 1 (persistent) or 2 (cluster)");
+  w->engine = engine;
   return IQS_OK;
 }
 
@@ -580,6 +615,74 @@ iqs_status run_many(iqs_pool_many* W, int nc, const iqs_circuit_desc* cd, double
   if (e == cudaSuccess) e = cudaMemsetAsync(B + o_done, 0, njobs * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(B + o_ctrl, 0, 64, st);
   if (e != cudaSuccess) return report(IQS_ECUDA, "pool upload: %s", cudaGetErrorString(e));
+  // ---- cluster-resident path: every trajectory in one cluster launch
+  int max_n = 0, min_n = 1 << 30;
+  for (int c = 0; c < nc; ++c) {
+    max_n = std::max(max_n, cd[c].n);
+    min_n = std::min(min_n, cd[c].n);
+  }
+  const int lc = pool_cluster_logc(max_n, W->dtype);
+  const bool fits = lc >= 0 && min_n >= 2 * lc + 1;
+  if (W->engine == 2 && !fits)
+    return report(IQS_EINVAL, "the cluster engine takes these circuits only if every state fits (%d..%d qubits)",
+                  min_n, max_n);
+  if (W->engine == 2 || (W->engine == 0 && W->dtype == IQS_C64 && fits)) {
+    using Mat = typename TR::Mat;
+    std::vector<uint64_t> mat_off(njobs);
+    uint64_t nmat = 0;
+    for (size_t j = 0; j < njobs; ++j) {
+      mat_off[j] = nmat;
+      nmat += (uint64_t)jobs[j].phases * jobs[j].n;
+    }
+    if (W->mats_bytes < nmat * sizeof(Mat)) {
+      cudaFree(W->mats);
+      W->mats = nullptr;
+      W->mats_bytes = 0;
+      if (cudaMalloc(&W->mats, nmat * sizeof(Mat)) != cudaSuccess) {
+        cudaGetLastError();
+        return report(IQS_ENOMEM, "cannot allocate %zu bytes of fused matrices", (size_t)(nmat * sizeof(Mat)));
+      }
+      W->mats_bytes = nmat * sizeof(Mat);
+    }
+    // the job table and the matrix offsets: scratch from the stream-ordered allocator
+    void* scratch = nullptr;
+    const size_t tb = njobs * (sizeof(ClusterJob) + sizeof(uint64_t));
+    if (cudaMallocAsync(&scratch, tb, st) != cudaSuccess) {
+      cudaGetLastError();
+      return report(IQS_ENOMEM, "cannot allocate the cluster job table");
+    }
+    ClusterJob* dcj = static_cast<ClusterJob*>(scratch);
+    uint64_t* dmo = reinterpret_cast<uint64_t*>(dcj + njobs);
+    Mat* mats = static_cast<Mat*>(W->mats);
+    double* dprobs = reinterpret_cast<double*>(B + o_probs);
+    std::vector<ClusterJob> cj(njobs);
+    for (size_t j = 0; j < njobs; ++j)
+      cj[j] = ClusterJob{mats + mat_off[j], static_cast<V*>(W->arena) + jobs[j].state_off,
+                         dprobs + out_off[jobs[j].out_index], jobs[j].n, jobs[j].phases, jobs[j].depth};
+    e = cudaMemcpyAsync(dcj, cj.data(), njobs * sizeof(ClusterJob), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmo, mat_off.data(), njobs * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
+    const Job* djobs = reinterpret_cast<const Job*>(B + o_jobs);
+    if (e == cudaSuccess) {
+      const dim3 cg(8, (unsigned)std::min<size_t>(njobs, 65535));
+      k_many_compose<TR><<<cg, kThreads, 0, st>>>(djobs, (int)njobs, dmo, mats);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_pool_cluster(dcj, (int)njobs, max_n, W->dtype, st);
+    if (e == cudaSuccess) {
+      k_many_means<<<nc, 32, 0, st>>>(dprobs, reinterpret_cast<const uint64_t*>(B + o_cf),
+                                      reinterpret_cast<const int*>(B + o_ct), reinterpret_cast<const int*>(B + o_cn),
+                                      reinterpret_cast<const uint64_t*>(B + o_mo), reinterpret_cast<double*>(B + o_means));
+      e = cudaGetLastError();
+    }
+    cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return report(IQS_ECUDA, "cluster pool launch: %s", cudaGetErrorString(e));
+    note_launches(2);  // compose and means (the cluster launch counts itself)
+    if (probs_out) e = cudaMemcpyAsync(probs_out, dprobs, nprob * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(means_out, B + o_means, nmean * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return report(IQS_ECUDA, "pool results: %s", cudaGetErrorString(e));
+    return IQS_OK;
+  }
   unsigned long long* ticket = reinterpret_cast<unsigned long long*>(B + o_ctrl);
   unsigned* status = reinterpret_cast<unsigned*>(B + o_ctrl + 8);
   unsigned* abort_flag = reinterpret_cast<unsigned*>(B + o_ctrl + 12);

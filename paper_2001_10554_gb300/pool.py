@@ -99,6 +99,10 @@ class PoolMany:
         call("iqs_pool_many_create", self.dtype_code, _stream_handle(stream), C.byref(h))
         self._h = h
 
+    def set_engine(self, engine: str = "auto") -> None:
+        """"auto", "persistent" (tiled, bounded waits) or "cluster" (states resident on chip)."""
+        call("iqs_pool_many_set_engine", self._h, {"auto": 0, "persistent": 1, "cluster": 2}[engine])
+
     def set_wait_limit(self, seconds: float, debug_never: bool = False) -> None:
         call("iqs_pool_many_set_wait_limit", self._h, C.c_double(seconds), int(bool(debug_never)))
 
