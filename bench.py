@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the complex64 32q sweep and the QAOA sections")
     ap.add_argument("--pso-graphs", type=int, default=64, help="graphs of the particle-swarm section (0 skips it)")
+    ap.add_argument("--profile-pool", default=None, metavar="N,TRAJ,DEPTH",
+                    help="one noisy brick circuit of TRAJ complex64 trajectories on the cluster-resident engine (for ncu)")
     ap.add_argument("--profile-ops", type=int, default=0, metavar="N",
                     help="one small invocation of apply_kq, marginal and sample on N-qubit states (for ncu)")
     ap.add_argument("--profile-qaoa", default=None, metavar="N,P,BATCH",
@@ -507,6 +509,25 @@ def ensemble_section(iqs, torch):
 
 
 # ---------------------------------------------------------------- GPU arm
+def profile_pool(spec: str) -> int:
+    """One run of a noisy brick circuit (X/Z angles N(0, 0.02^2)) on the
+    cluster-resident pool engine, after one warm-up run."""
+    import paper_2001_10554_gb300 as iqs
+    import workloads as W
+    from paper_2001_10554_gb300.pool import brick_unitaries, noise_count
+    n, traj, depth = (int(v) for v in spec.split(","))
+    ops = W.random_circuit_layers(n, depth, seed=3)
+    U = brick_unitaries(ops, n)
+    ang = W.rng(4).normal(0.0, 0.02, size=(traj, noise_count(n, depth), 2))
+    pool = iqs.Pool(n, "complex64", batch_max=traj, depth_max=depth)
+    pool.set_engine("cluster")
+    for _ in range(2):
+        _, mean = pool.run_brick(U, ang)
+    pool.close()
+    print(json.dumps({"n": n, "trajectories": traj, "depth": depth, "mean_p1_sum": float(mean.sum())}))
+    return 0
+
+
 def profile_ops(n: int) -> int:
     """Single invocations for a profiler: on an n-qubit complex64 and complex128
     Gaussian state, apply_kq with k = 2..5 (complex64) or 2..4 (complex128) on
@@ -550,6 +571,8 @@ def main(argv=None):
         return profile_qaoa(args.profile_qaoa)
     if args.profile_ops:
         return profile_ops(args.profile_ops)
+    if args.profile_pool:
+        return profile_pool(args.profile_pool)
 
     import torch
     import torch.distributed as dist
