@@ -672,6 +672,10 @@ def main(argv=None):
             host_out = torch.empty(N, dtype=torch.complex128, pin_memory=True)
             host_in.copy_(state)
             nbytes = N * 16
+            # one untimed pass maps the freshly pinned pages of both host buffers
+            reg.upload_ptr(host_in.data_ptr(), nbytes)
+            step(False)
+            reg.download_ptr(host_out.data_ptr(), nbytes)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
