@@ -221,6 +221,16 @@ iqs_status iqs_qaoa_destroy(iqs_qaoa* q);
  * (batch, p, gradient) shape from a captured CUDA graph. */
 iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs);
 
+/* Engine of energy-only runs (iqs_qaoa_run without gradient outputs): 0
+ * (default) and 1 use the tiled passes; 2 keeps every complex64 state of
+ * 8..18 qubits resident in the shared memory of a thread-block cluster for
+ * all p layers (up to 16 CTAs of 128 KB; the state is written once, for
+ * iqs_qaoa_download_state).  Mode 2 is IQS_EINVAL where it is unavailable.
+ * Gradient runs and complex128 always use the tiled passes.  Energies agree
+ * within complex64 rounding.  (Measured, the cluster engine ties the tiled
+ * passes up to 14 qubits and is slower at 16 and 18, hence the default.) */
+iqs_status iqs_qaoa_set_engine(iqs_qaoa* q, int engine);
+
 /* Evaluate ``batch`` parameter sets of depth p (1..64).  Host arrays,
  * row-major [batch][p]: gammas, betas.  Outputs (host): energies[batch] and,
  * when both are non-NULL, grad_gammas[batch][p] and grad_betas[batch][p].

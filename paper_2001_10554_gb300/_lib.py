@@ -67,6 +67,7 @@ SIGNATURES = {
     "iqs_qaoa_create": ([C.c_int, C.c_int, C.c_int, C.c_int, _i32p, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "iqs_qaoa_create_multi": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _i32p, C.c_void_p, C.POINTER(C.c_void_p)],
                               C.c_int),
+    "iqs_qaoa_set_engine": ([C.c_void_p, C.c_int], C.c_int),
     "iqs_qaoa_info": ([C.c_void_p] + [C.POINTER(C.c_int)] * 5, C.c_int),
     "iqs_qaoa_max_cut": ([C.c_void_p, _dp], C.c_int),
     "iqs_qaoa_pso": ([C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp,

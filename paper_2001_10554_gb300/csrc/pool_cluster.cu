@@ -49,7 +49,7 @@ struct CT {
   static constexpr int kThreads = 512;
   static constexpr int kMinBlocks = 1;
 };
-constexpr int kMaxLogC = 3;       // portable clusters (8 CTAs)
+constexpr int kMaxLogC = 4;       // 16-CTA clusters need the non-portable size opt-in
 // shared-memory slice per CTA
 constexpr size_t kSliceBytes64 = 128 << 10, kSliceBytes128 = 128 << 10;
 
@@ -116,6 +116,43 @@ __device__ __forceinline__ void local_round_any(typename TR::W* st, const typena
   }
 }
 
+// Exchange round: groups of 2C amplitudes whose element c has bit 0 = qubit
+// L-1 (local) and bits 1.. = the CTA rank (the top qubits).  Rank r handles
+// a 1/C share of the 2^(L-1) groups: it gathers each group through
+// distributed shared memory, applies the gates of the top qubits (mats[L..]),
+// and stores it back through the involution c -> c ^ ((c & cmg) << 1) (the
+// CNOT pairs that touch the top qubits; cmg = 0 for none).  Callers bracket it
+// with cluster barriers.
+template <class TR, int LOGC, int kCT>
+__device__ __forceinline__ void exchange_round(cg::cluster_group& cl, typename TR::W* st,
+                                               const typename TR::Mat* mats, int L, unsigned rank, unsigned cmg) {
+  using W = typename TR::W;
+  constexpr int C = 1 << LOGC;
+  const unsigned NL = 1u << L;
+  const unsigned G = NL >> 1, per = G / C;
+  const unsigned hib = 1u << (L - 1);
+  for (unsigned g = rank * per + threadIdx.x; g < (rank + 1) * per; g += kCT) {
+    W x[2 * C];
+#pragma unroll
+    for (int c = 0; c < 2 * C; ++c) {
+      const W* rs = cl.map_shared_rank(st, (unsigned)(c >> 1));
+      x[c] = rs[phys(g | ((c & 1) ? hib : 0u))];
+    }
+#pragma unroll
+    for (int j = 0; j < LOGC; ++j) {
+#pragma unroll
+      for (int c = 0; c < 2 * C; ++c)
+        if (!((c >> (j + 1)) & 1)) TR::apply(mats[L + j], x[c], x[c | (2 << j)]);
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * C; ++c) {
+      const unsigned d = (unsigned)c ^ (((unsigned)c & cmg) << 1);
+      W* rs = cl.map_shared_rank(st, d >> 1);
+      rs[phys(g | ((d & 1) ? hib : 0u))] = x[c];
+    }
+  }
+}
+
 template <class TR, int LOGC>
 __global__ void __launch_bounds__(CT<TR>::kThreads, CT<TR>::kMinBlocks)
     k_pool_cluster(const ClusterJob* __restrict__ jobs, int n_jobs) {
@@ -165,34 +202,11 @@ __global__ void __launch_bounds__(CT<TR>::kThreads, CT<TR>::kMinBlocks)
       }
       if constexpr (LOGC > 0) {
         cl.sync();
-        // exchange: element c of a group has bit 0 = qubit L-1 and bits 1.. = the rank
         unsigned cmg = 0;
         if (l < depth)
           for (int i = o; i + 1 < n; i += 2)
             if (i >= L - 1) cmg |= 1u << (i - (L - 1));
-        const unsigned G = NL >> 1, per = G / C;
-        const unsigned hib = 1u << (L - 1);
-        for (unsigned g = rank * per + threadIdx.x; g < (rank + 1) * per; g += kCT) {
-          W x[2 * C];
-#pragma unroll
-          for (int c = 0; c < 2 * C; ++c) {
-            const W* rs = cl.map_shared_rank(st, (unsigned)(c >> 1));
-            x[c] = rs[phys(g | ((c & 1) ? hib : 0u))];
-          }
-#pragma unroll
-          for (int j = 0; j < LOGC; ++j) {
-#pragma unroll
-            for (int c = 0; c < 2 * C; ++c)
-              if (!((c >> (j + 1)) & 1)) TR::apply(mats[L + j], x[c], x[c | (2 << j)]);
-          }
-          // new[perm(c)] = old[c] for the involution perm(c) = c ^ ((c & cmg) << 1)
-#pragma unroll
-          for (int c = 0; c < 2 * C; ++c) {
-            const unsigned d = (unsigned)c ^ (((unsigned)c & cmg) << 1);
-            W* rs = cl.map_shared_rank(st, d >> 1);
-            rs[phys(g | ((d & 1) ? hib : 0u))] = x[c];
-          }
-        }
+        exchange_round<TR, LOGC, kCT>(cl, st, mats, L, rank, cmg);
         cl.sync();
       } else {
         __syncthreads();
@@ -246,6 +260,147 @@ __global__ void __launch_bounds__(CT<TR>::kThreads, CT<TR>::kMinBlocks)
   }
 }
 
+// ---------------------------------------------------------------- QAOA forward on clusters
+// Section 4's objective, energies only: state b (graph b / per_graph) starts
+// in |+>^n (every amplitude 2^(-n/2)); each layer multiplies amplitude x by the
+// phase table entry T_b[C(x)] (C read from the graph's one-byte cut table),
+// then applies RX(2 beta) to every qubit through the local rounds and one
+// exchange round; at the end E_b = sum C(x) |psi_x|^2 / sum |psi_x|^2
+// (double-float per thread, FP64 across the cluster in a fixed order) goes to
+// results[b * rstride] and the final state to phi[b] (complex64).
+template <int LOGC>
+__global__ void __launch_bounds__(CT<P64>::kThreads, 1)
+    k_qaoa_cluster(const uint8_t* __restrict__ cut, uint64_t N, int per_graph, const float2* __restrict__ rx,
+                   const float2* __restrict__ tables, int tsize, int bmax, int n, int p, int batch,
+                   float2* __restrict__ phi, double* __restrict__ results, int rstride) {
+  using TR = P64;
+  using W = float2;
+  using Mat = P64::Mat;
+  constexpr int kCT = CT<P64>::kThreads;
+  constexpr int C = 1 << LOGC;
+  constexpr int RB = TR::kRegBits;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank();
+  const int L = n - LOGC;
+  const unsigned NL = 1u << L;
+  extern __shared__ __align__(16) unsigned char raw[];
+  W* st = reinterpret_cast<W*>(raw);
+  __shared__ Mat mats[kPoolMaxQubits];
+  __shared__ float2 ph[256];
+  __shared__ double part[C][2];
+  __shared__ double red[kCT / 32][2];
+  const float amp0 = (float)exp2(-0.5 * n);
+  const unsigned cid = blockIdx.x / C, ncl = gridDim.x / C;
+  for (unsigned b = cid; b < (unsigned)batch; b += ncl) {
+    const uint8_t* cb = cut + (uint64_t)(b / (unsigned)per_graph) * N + (uint64_t)rank * NL;
+    for (unsigned i = threadIdx.x; i < NL; i += kCT) st[i] = make_float2(amp0, 0.f);
+    for (int l = 0; l < p; ++l) {
+      const uint64_t lb = (uint64_t)l * bmax + b;
+      for (int k = threadIdx.x; k < tsize; k += kCT) ph[k] = tables[lb * tsize + k];
+      if ((int)threadIdx.x < n) {
+        const float2 k = rx[lb];  // (cos beta, sin beta): RX(2 beta) = [[c, -i s], [-i s, c]]
+        Mat m;
+        m.r[0] = k.x; m.i[0] = 0.f; m.r[1] = 0.f;  m.i[1] = -k.y;
+        m.r[2] = 0.f; m.i[2] = -k.y; m.r[3] = k.x; m.i[3] = 0.f;
+        mats[threadIdx.x] = m;
+      }
+      __syncthreads();
+      for (unsigned i = threadIdx.x; i < NL; i += kCT) {  // cost phase
+        const float2 t = ph[cb[i]];
+        const float2 x = st[phys(i)];
+        st[phys(i)] = make_float2(t.x * x.x - t.y * x.y, t.x * x.y + t.y * x.x);
+      }
+      __syncthreads();
+      for (int b0 = 0; b0 < L; b0 += RB) {
+        local_round_any<TR, kCT>(st, mats, b0, min(RB, L - b0), NL);
+        __syncthreads();
+      }
+      if constexpr (LOGC > 0) {
+        cl.sync();
+        exchange_round<TR, LOGC, kCT>(cl, st, mats, L, rank, 0u);
+        cl.sync();
+      }
+    }
+    float2* out = phi + (uint64_t)b * N + (uint64_t)rank * NL;
+    dfx::Acc ae, an;
+    for (unsigned i = threadIdx.x; i < NL; i += kCT) {
+      const float2 x = st[phys(i)];
+      out[i] = x;
+      float pp, ee;
+      dfx::abs2_c64(x.x, x.y, pp, ee);
+      an.add(pp, ee);
+      const float cf = (float)cb[i];
+      const float q = cf * pp;
+      ae.add(q, fmaf(cf, pp, -q) + cf * ee);
+    }
+    double v[2] = {ae.value(), an.value()};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+      if (lane == 0) red[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double sum = 0.0;
+      for (int w = 0; w < kCT / 32; ++w) sum += red[w][threadIdx.x];
+      double* p0 = cl.map_shared_rank(&part[0][0], 0u);
+      p0[rank * 2 + threadIdx.x] = sum;
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+      double e = 0.0, nn = 0.0;
+      for (int r = 0; r < C; ++r) {
+        e += part[r][0];
+        nn += part[r][1];
+      }
+      results[(uint64_t)b * rstride] = e / nn;
+    }
+    cl.sync();
+  }
+}
+
+// Launch configuration; with ``clusters`` it also sets the kernel's
+// attributes and queries the co-resident cluster count (done once, outside
+// any stream capture).
+template <int LOGC>
+cudaError_t qaoa_cluster_config(int n, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int* clusters) {
+  auto kern = k_qaoa_cluster<LOGC>;
+  const size_t smem = ((size_t)1 << (n - LOGC)) * sizeof(float2);
+  cudaError_t e = cudaSuccess;
+  if (clusters) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && LOGC > 3) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cfg = {};
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1u << LOGC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(CT<P64>::kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(1u << LOGC, 1, 1);
+  return clusters ? cudaOccupancyMaxActiveClusters(clusters, kern, &cfg) : cudaSuccess;
+}
+
+template <int LOGC>
+cudaError_t launch_qaoa_t(int clusters, const uint8_t* cut, uint64_t N, int per_graph, const float2* rx,
+                          const float2* tables, int tsize, int bmax, int n, int p, int batch, float2* phi,
+                          double* results, int rstride, cudaStream_t s) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e = qaoa_cluster_config<LOGC>(n, cfg, attr, nullptr);
+  if (e != cudaSuccess) return e;
+  cfg.stream = s;
+  cfg.gridDim = dim3((unsigned)std::max(1, std::min(clusters, batch)) << LOGC, 1, 1);
+  return cudaLaunchKernelEx(&cfg, k_qaoa_cluster<LOGC>, cut, N, per_graph, rx, tables, tsize, bmax, n, p, batch, phi,
+                            results, rstride);
+}
+
 int cluster_logc(int n, int dtype) {
   const size_t w = dtype == IQS_C128 ? sizeof(qops::S2) : sizeof(float2);
   const size_t slice = dtype == IQS_C128 ? kSliceBytes128 : kSliceBytes64;
@@ -260,6 +415,7 @@ cudaError_t launch_cluster_t(const ClusterJob* jobs, int n_jobs, int max_n, cuda
   auto kern = k_pool_cluster<TR, LOGC>;
   const size_t smem = ((size_t)1 << (max_n - LOGC)) * sizeof(typename TR::W);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && LOGC > 3) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -276,7 +432,8 @@ cudaError_t launch_cluster_t(const ClusterJob* jobs, int n_jobs, int max_n, cuda
   int clusters = 0;
   e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
   if (e != cudaSuccess) return e;
-  clusters = std::max(1, std::min(clusters, n_jobs));
+  if (clusters < 1) return cudaErrorInvalidConfiguration;  // this cluster size cannot be scheduled
+  clusters = std::min(clusters, n_jobs);
   cfg.gridDim = dim3((unsigned)clusters << LOGC, 1, 1);
   return cudaLaunchKernelEx(&cfg, kern, jobs, n_jobs);
 }
@@ -299,6 +456,7 @@ cudaError_t launch_pool_cluster(const ClusterJob* jobs, int n_jobs, int max_n, i
       case 1: e = launch_cluster_t<P128, 1>(jobs, n_jobs, max_n, s); break;
       case 2: e = launch_cluster_t<P128, 2>(jobs, n_jobs, max_n, s); break;
       case 3: e = launch_cluster_t<P128, 3>(jobs, n_jobs, max_n, s); break;
+      case 4: e = launch_cluster_t<P128, 4>(jobs, n_jobs, max_n, s); break;
       default: break;
     }
   } else {
@@ -307,10 +465,49 @@ cudaError_t launch_pool_cluster(const ClusterJob* jobs, int n_jobs, int max_n, i
       case 1: e = launch_cluster_t<P64, 1>(jobs, n_jobs, max_n, s); break;
       case 2: e = launch_cluster_t<P64, 2>(jobs, n_jobs, max_n, s); break;
       case 3: e = launch_cluster_t<P64, 3>(jobs, n_jobs, max_n, s); break;
+      case 4: e = launch_cluster_t<P64, 4>(jobs, n_jobs, max_n, s); break;
       default: break;
     }
   }
   return e == cudaSuccess ? launched(1) : e;
+}
+
+// QAOA forward on clusters (complex64): the cluster size for n qubits and the
+// number of co-resident clusters (0 when the kernel cannot run), queried once.
+int qaoa_cluster_setup(int n, int* logc) {
+  const int lc = cluster_logc(n, IQS_C64);
+  *logc = lc;
+  if (lc < 0) return 0;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  int clusters = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (lc) {
+    case 0: e = qaoa_cluster_config<0>(n, cfg, attr, &clusters); break;
+    case 1: e = qaoa_cluster_config<1>(n, cfg, attr, &clusters); break;
+    case 2: e = qaoa_cluster_config<2>(n, cfg, attr, &clusters); break;
+    case 3: e = qaoa_cluster_config<3>(n, cfg, attr, &clusters); break;
+    case 4: e = qaoa_cluster_config<4>(n, cfg, attr, &clusters); break;
+    default: break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return clusters;
+}
+
+cudaError_t launch_qaoa_cluster(int logc, int clusters, const uint8_t* cut, uint64_t N, int per_graph,
+                                const float2* rx, const float2* tables, int tsize, int bmax, int n, int p, int batch,
+                                float2* phi, double* results, int rstride, cudaStream_t s) {
+  switch (logc) {
+    case 0: return launch_qaoa_t<0>(clusters, cut, N, per_graph, rx, tables, tsize, bmax, n, p, batch, phi, results, rstride, s);
+    case 1: return launch_qaoa_t<1>(clusters, cut, N, per_graph, rx, tables, tsize, bmax, n, p, batch, phi, results, rstride, s);
+    case 2: return launch_qaoa_t<2>(clusters, cut, N, per_graph, rx, tables, tsize, bmax, n, p, batch, phi, results, rstride, s);
+    case 3: return launch_qaoa_t<3>(clusters, cut, N, per_graph, rx, tables, tsize, bmax, n, p, batch, phi, results, rstride, s);
+    case 4: return launch_qaoa_t<4>(clusters, cut, N, per_graph, rx, tables, tsize, bmax, n, p, batch, phi, results, rstride, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace iqs

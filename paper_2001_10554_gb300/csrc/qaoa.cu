@@ -726,6 +726,9 @@ __global__ void k_rescale(V* __restrict__ a, uint64_t N, const double* __restric
 // ================================================================ host engine
 struct iqs_qaoa {
   int n = 0, dtype = IQS_C64, bmax = 0, n_edges = 0;
+  int engine = 0;     // 0 auto (= tiled), 1 tiled passes, 2 cluster-resident (energies only, complex64)
+  int clogc = -1;     // cluster size 2^clogc of the cluster-resident forward (-1: not available)
+  int cclusters = 0;  // co-resident clusters of that kernel
   int n_graphs = 1;          // cut tables, one per graph ([n_graphs][N] bytes)
   int per_graph = 1 << 30;   // state b uses graph b / per_graph
   uint64_t N = 0;
@@ -758,7 +761,19 @@ struct iqs_qaoa {
 };
 
 namespace iqs {
+
+// pool_cluster.cu: the cluster-resident forward pass (energies only, complex64)
+int qaoa_cluster_setup(int n, int* logc);
+cudaError_t launch_qaoa_cluster(int logc, int clusters, const uint8_t* cut, uint64_t N, int per_graph,
+                                const float2* rx, const float2* tables, int tsize, int bmax, int n, int p, int batch,
+                                float2* phi, double* results, int rstride, cudaStream_t s);
+
 namespace {
+
+// The cluster-resident forward only on request: measured against the tiled
+// passes it ties up to 14 qubits and loses at 16 and 18 (issue-bound at 16
+// warps per SM, while the batched tiled passes mostly hit L2).
+bool use_cluster(const iqs_qaoa* q) { return q->engine == 2 && q->clogc >= 0 && q->cclusters > 0; }
 
 // Partial slots per state: mixer passes x blocks (<= 4 x 2432), then the fused
 // phase-gradient partials at kGammaCol.
@@ -988,6 +1003,14 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
   const int PB = blocks_per_state(q, B);
   const int ps = part_stride_for(q);
   int launches = 0;
+  if constexpr (std::is_same<TR, T64>::value) {
+    if (!grad && use_cluster(q)) {  // every state resident in a thread-block cluster for all p layers
+      *n_launches = 1;
+      return launch_qaoa_cluster(q->clogc, q->cclusters, q->cut, N, q->per_graph, (const float2*)q->rx,
+                                 (const float2*)q->tables, tsize, q->bmax, q->n, p, B, (float2*)q->phi, q->results,
+                                 out_stride, s);
+    }
+  }
   const double amp = std::pow(2.0, -q->n / 2.0);
   V v0;
   v0.x = (decltype(v0.x))amp;
@@ -1348,6 +1371,7 @@ iqs_status iqs_qaoa_create_multi(int n, int dtype, int n_graphs, int per_graph, 
   }
   load_tuning(q);
   replan(q);
+  if (dtype == IQS_C64) q->cclusters = qaoa_cluster_setup(n, &q->clogc);
   *out = q;
   return IQS_OK;
 }
@@ -1398,6 +1422,21 @@ iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs) {
   if (renorm_every < 0) return iqs::report(IQS_EINVAL, "renorm_every must be >= 0");
   q->renorm_every = renorm_every;
   q->use_graphs = use_graphs != 0;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_set_engine(iqs_qaoa* q, int engine) {
+  using namespace iqs;
+  if (q == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (engine < 0 || engine > 2) return report(IQS_EINVAL, "engine must be 0 (auto), 1 (tiled) or 2 (cluster)");
+  if (engine == 2 && !(q->clogc >= 0 && q->cclusters > 0))
+    return report(IQS_EINVAL, "the cluster-resident forward takes complex64 states of 8..18 qubits on this device");
+  if (engine != q->engine) {  // captured graphs embed the engine's kernels
+    cudaStreamSynchronize(q->stream);
+    for (auto& kv : q->graphs) cudaGraphExecDestroy(kv.second.first);
+    q->graphs.clear();
+  }
+  q->engine = engine;
   return IQS_OK;
 }
 

@@ -56,6 +56,10 @@ class QAOA:
         self._h = h
         self.set_options(renorm_every, use_graphs)
 
+    def set_engine(self, engine: str = "auto") -> None:
+        """Energy-only runs: "auto", "tiled" or "cluster" (complex64 states resident on chip)."""
+        call("iqs_qaoa_set_engine", self._h, {"auto": 0, "tiled": 1, "cluster": 2}[engine])
+
     def max_cut(self) -> np.ndarray:
         """Exact Max-Cut value of each graph (largest cut count over all bipartitions)."""
         out = np.empty(self.n_graphs)

@@ -209,7 +209,7 @@ def test_cluster_engine_matches_oracle_and_passes(gpu_lib, dtype, ns):
 
 def test_cluster_engine_rejects_states_that_do_not_fit(gpu_lib):
     from paper_2001_10554_gb300 import IQSError
-    for n, dtype in ((5, "complex64"), (18, "complex64"), (17, "complex128")):
+    for n, dtype in ((5, "complex64"), (19, "complex64"), (18, "complex128")):
         pool = gpu_lib.Pool(n, dtype, batch_max=1, depth_max=2)
         with pytest.raises(IQSError):
             pool.set_engine("cluster")

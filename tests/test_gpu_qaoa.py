@@ -226,3 +226,31 @@ def test_qaoa_tma_staged_passes_match(gpu_lib, dtype, n):
         assert np.max(np.abs(E - Eo)) <= tol_e
         assert np.max(np.abs(dg - dgo)) <= tol_g and np.max(np.abs(db - dbo)) <= tol_g
     eng.close()
+
+
+# ---------------------------------------------------------------- cluster-resident forward (energies only)
+@pytest.mark.parametrize("n", [8, 12, 14, 16, 18])
+def test_cluster_forward_matches_oracle_and_tiled(gpu_lib, n):
+    """complex64 states resident in a thread-block cluster for all layers:
+    energies against the oracle (2e-6, the complex64 bound of this file) and
+    the tiled engine, and the final state against the oracle's state."""
+    from paper_2001_10554_gb300 import IQSError
+    p, B = 3, 5
+    edges = W.random_3regular_graph(n, 1500 + n)
+    gm, bt = W.qaoa_parameter_sets(p, B, 1600 + n)
+    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=B)
+    try:
+        eng.set_engine("cluster")
+    except IQSError:
+        eng.close()
+        pytest.skip("the cluster-resident forward is not available for this size on this device")
+    E = eng.run(gm, bt, grad=False)
+    state = eng.state(1).astype(np.complex128)
+    eng.set_engine("tiled")
+    Et = eng.run(gm, bt, grad=False)
+    eng.close()
+    assert np.max(np.abs(E - Et)) <= 2e-6
+    for b in ((0, 1, 4) if n <= 16 else (1,)):
+        assert abs(E[b] - oq.qaoa_energy(n, edges, gm[b], bt[b])) <= 2e-6
+    ref = oq.qaoa_state(n, edges, gm[1], bt[1])
+    assert np.max(np.abs(state - ref)) <= (n + 1) * p * 8 * 2.0 ** -24 * np.max(np.abs(ref)) * 4
