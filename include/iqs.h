@@ -354,10 +354,12 @@ iqs_status iqs_pool_set_noise_t1t2(iqs_pool* p, double T1, double T2, double gat
  * cluster-resident engine when a state fits, 1 forces the tiled passes
  * (two passes over every state per layer through HBM), 2 forces the
  * cluster-resident engine: each trajectory lives in the distributed shared
- * memory of a thread-block cluster (up to 8 CTAs of 128 KB) for the whole
+ * memory of a thread-block cluster (up to 16 CTAs of 128 KB) for the whole
  * circuit, and its state is written to HBM once at the end.  It takes
- * complex64 states of 8..17 qubits and complex128 of 8..16; mode 2 on a
- * state that does not fit is IQS_EINVAL.  Mode 0 uses it for complex64 only.  Results agree within the
+ * complex64 states of 8..18 qubits and complex128 of 8..17 (clusters of up
+ * to 16 CTAs); mode 2 on a state that does not fit is IQS_EINVAL.  Mode 0
+ * uses it for complex64 states that fit clusters of up to 4 CTAs (16
+ * qubits).  Results agree within the
  * rounding of the dtype (the gates are grouped differently). */
 iqs_status iqs_pool_set_engine(iqs_pool* p, int engine);
 
@@ -401,7 +403,8 @@ iqs_status iqs_pool_many_set_wait_limit(iqs_pool_many* w, double seconds, int de
 /* Engine of iqs_pool_many_run: 0 (default) runs every trajectory of every
  * circuit in one launch of the cluster-resident engine (see
  * iqs_pool_set_engine) when the dtype is complex64 and every state fits one
- * cluster size (qubit counts from 2 logc + 1 to the largest), else the
+ * cluster size of up to 4 CTAs (qubit counts from 2 logc + 1 to the
+ * largest), else the
  * persistent tiled kernel; 1 forces the persistent kernel (the only one with
  * bounded waits and IQS_ETIMEOUT); 2 forces the cluster-resident engine
  * (IQS_EINVAL at run time when a state does not fit). */

@@ -35,6 +35,7 @@ namespace iqs {
 
 // pool_cluster.cu
 bool pool_cluster_eligible(int n, int dtype);
+int pool_cluster_logc(int n, int dtype);
 cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s);
 
 namespace {
@@ -240,7 +241,9 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
   k_pool_compose<TR><<<grid_for((uint64_t)batch * phases * P->n, 1, 8), kThreads, 0, s>>>(C, batch, phases, allm);
   ++launches;
   // auto: the cluster-resident engine for complex64; complex128 runs faster in the tiled passes
-  const bool cluster = P->engine == 2 || (P->engine == 0 && P->dtype == IQS_C64 && pool_cluster_eligible(P->n, P->dtype));
+  // (up to 4-CTA clusters: larger clusters keep fewer states on chip at once)
+  const bool cluster = P->engine == 2 || (P->engine == 0 && P->dtype == IQS_C64 && pool_cluster_eligible(P->n, P->dtype) &&
+                                          pool_cluster_logc(P->n, P->dtype) <= 2);
   if (cluster) {
     // the whole circuit of every trajectory in one launch, states resident in cluster shared memory
     cudaError_t e = cudaGetLastError();

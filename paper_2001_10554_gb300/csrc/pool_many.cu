@@ -626,7 +626,7 @@ iqs_status run_many(iqs_pool_many* W, int nc, const iqs_circuit_desc* cd, double
   if (W->engine == 2 && !fits)
     return report(IQS_EINVAL, "the cluster engine takes these circuits only if every state fits (%d..%d qubits)",
                   min_n, max_n);
-  if (W->engine == 2 || (W->engine == 0 && W->dtype == IQS_C64 && fits)) {
+  if (W->engine == 2 || (W->engine == 0 && W->dtype == IQS_C64 && fits && lc <= 2)) {
     using Mat = typename TR::Mat;
     std::vector<uint64_t> mat_off(njobs);
     uint64_t nmat = 0;
