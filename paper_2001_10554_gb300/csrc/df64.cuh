@@ -114,14 +114,20 @@ __device__ __forceinline__ void sqr(float x, float& p, float& e) {
   e = fmaf(x, x, -p);
 }
 
-// A double-float accumulator (h + l); add() takes an unevaluated pair.
+// A double-float accumulator (h + l); add() takes an unevaluated pair.  After
+// the error-free TwoSum of the leading parts the pair is renormalised
+// (Fast2Sum: |l| stays below half an ulp of h), so each add loses at most
+// about 2^-48 of the running sum however many terms one thread accumulates;
+// without it the low word grows with the term count and its own rounding
+// then drops the small residuals.
 struct Acc {
   float h = 0.f, l = 0.f;
   __device__ __forceinline__ void add(float p, float e) {
     float s, t;
     two_sum(h, p, s, t);
-    h = s;
-    l += t + e;
+    const float lo = l + (t + e);
+    h = s + lo;
+    l = lo - (h - s);
   }
   // Final value; uses two FP32->FP64 conversions and one FP64 add (once per thread).
   __device__ __forceinline__ double value() const { return (double)h + (double)l; }

@@ -294,3 +294,56 @@ def test_swarm_full_size_sampled(gpu_lib):
         e = oq.qaoa_energy(n, gs[g], best_pos[g, :p], best_pos[g, p:])
         assert abs(e - best_val[g]) <= 2e-6
     torch.cuda.empty_cache()
+
+
+def test_33q_c64_beyond_32bit_indices(gpu_lib, dev):
+    """A 33-qubit complex64 state (64 GiB) has amplitude indices past 2^32, so
+    the 64-bit index paths run: sampled one-qubit and CNOT pairs against the
+    oracle's pair update, qubit 32's probability against a marginal, and the
+    Max-Cut energy of |+>^33 (every edge cut with probability 1/2, unchanged by
+    the cost phase, which only multiplies amplitudes by phases) = |E|/2 per
+    unit norm."""
+    n, N = 33, 1 << 33
+    g = W.rng(5301)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        st = torch.empty(N, dtype=torch.complex64, device=dev)
+    stream.synchronize()
+    reg = gpu_lib.Register.wrap(st, stream=stream)
+    reg.init_uniform()
+    edges = np.array([(0, 32), (31, 32), (5, 17), (2, 30), (16, 32)] +
+                     [(k, k + 1) for k in range(6, 12)], dtype=np.int32)
+    reg.apply_zz_phase(edges, 0.73)
+    nn = reg.norm2()
+    # complex64 phase factors have |t|^2 = 1 +- 2^-23 (cos and sin rounded to
+    # FP32), so each weight |psi_x|^2 moves by that relative amount: the
+    # Rayleigh quotient stays within |E| * 2 * 2^-23 of |E|/2
+    assert abs(reg.energy_maxcut(edges) / nn - len(edges) / 2) <= len(edges) * 2 * 2.0 ** -23
+    for q in (32, 0):
+        U = W.haar_u2(g)
+        k = g.integers(0, N // 2, size=4096)
+        i0 = insert_zero(k, q)
+        i1 = i0 | (1 << q)
+        a0, a1 = gather(st, i0), gather(st, i1)
+        reg.apply_1q(q, U)
+        reg.synchronize()
+        e0, e1 = sv.pair_update(a0, a1, U.astype(np.complex64).astype(np.complex128))
+        scale = np.maximum(np.abs(a0), np.abs(a1))
+        assert np.all(np.abs(gather(st, i0) - e0) <= C64_GATE * 2 * scale + 1e-30), q
+        assert np.all(np.abs(gather(st, i1) - e1) <= C64_GATE * 2 * scale + 1e-30), q
+    idx = g.integers(0, N, size=4096)
+    src = np.where((idx >> 32) & 1, idx ^ 1, idx)
+    before = gather(st, src)
+    reg.apply_c1q(32, 0, np.array([[0, 1], [1, 0]]))
+    reg.synchronize()
+    np.testing.assert_array_equal(gather(st, idx), before)
+    # Two reductions of 2^33 weights in different orders: each thread adds up
+    # to ~2^17 terms into a double-float accumulator (about 2^-48 relative per
+    # add), so their difference stays far below 1e-10; a plain FP64 running
+    # sum of the same data would drift by about sqrt(2^33) * 2^-53 ~ 1e-11.
+    P = reg.probabilities()
+    assert abs(reg.marginal([32])[1] - P[32]) <= 1e-10
+    assert abs(reg.marginal([32, 0, 16]).sum() - reg.norm2()) <= 1e-10
+    reg.close()
+    del st
+    torch.cuda.empty_cache()
