@@ -281,6 +281,62 @@ def sweep_c64(iqs, torch, dev, n: int, steps: int, warmup: int):
             "error_bound": "FP32 gate arithmetic: <= 8 * 2^-24 per gate on unit-norm states (tests/test_gpu_parity.py)"}
 
 
+def random_circuit_section(iqs, torch):
+    """Config 1: the 12-qubit complex128 random circuit (20 layers of Haar
+    one-qubit gates on every qubit plus the CNOT brick, 350 gates) from
+    |0...0> to its 4096 amplitudes and 12 P(1) values: latency per circuit
+    (a) gate by gate through iqs_apply_1q / iqs_apply_c1q, (b) through the
+    pool engine's tiled passes (fused layers), (b') as one cluster-resident
+    launch, and (c) through the FP64 CPU oracle.  Launch- and latency-bound, not a roofline test."""
+    import workloads as W
+    from oracle import ensemble as oe
+    from paper_2001_10554_gb300.pool import brick_unitaries
+    n, depth = 12, 20
+    ops = W.random_circuit_layers(n, depth, seed=12)
+    X = np.array([[0, 1], [1, 0]])
+    reg = iqs.Register(n, "complex128")
+
+    def gates():
+        reg.init_basis(0)
+        for op in ops:
+            if op[0] == "1q":
+                reg.apply_1q(op[1], op[2])
+            else:
+                reg.apply_c1q(op[1], op[2], X)
+        return reg.probabilities()
+
+    gates()
+    t0 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        p_gates = gates()
+    dt_gates = (time.perf_counter() - t0) / reps
+    reg.close()
+    U = brick_unitaries(ops, n)
+    pool = iqs.Pool(n, "complex128", batch_max=1, depth_max=depth)
+    pool.run_brick(U)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        p_pool, _ = pool.run_brick(U)
+    dt_pool = (time.perf_counter() - t0) / reps
+    pool.set_engine("cluster")  # the whole circuit in one launch, the state resident on chip
+    pool.run_brick(U)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        p_cl, _ = pool.run_brick(U)
+    dt_cl = (time.perf_counter() - t0) / reps
+    pool.close()
+    t0 = time.perf_counter()
+    ref = oe.all_probabilities(oe.run_ops(n, ops))
+    dt_cpu = time.perf_counter() - t0
+    return {"workload": f"{n}-qubit complex128 random circuit, {depth} layers, {len(ops)} gates, |0> to P(1) of every qubit",
+            "gate_by_gate_us": round(dt_gates * 1e6, 1), "pool_tiled_passes_us": round(dt_pool * 1e6, 1),
+            "pool_cluster_one_launch_us": round(dt_cl * 1e6, 1),
+            "cpu_oracle_us": round(dt_cpu * 1e6, 1),
+            "max_p1_err_vs_oracle": float(max(np.max(np.abs(p_gates - ref)), np.max(np.abs(p_pool[0] - ref)),
+                                              np.max(np.abs(p_cl[0] - ref))))}
+
+
 def kq_measure_section(iqs, torch, dev):
     """Dense k-qubit gates, qubit-group marginals and sampling at the sweep's
     state sizes (30-qubit complex128, 32-qubit complex64): average launch time
@@ -702,6 +758,7 @@ def main(argv=None):
     if not args.no_extra:
         extra["c64_32q"] = sweep_c64(iqs, torch, dev, 32, steps=3, warmup=2)
         extra["kq_measure"] = kq_measure_section(iqs, torch, dev)
+        extra["random_circuit_12q"] = random_circuit_section(iqs, torch)
         extra["qaoa"] = qaoa_section(iqs, torch)
         extra["noise_ensemble"] = ensemble_section(iqs, torch)
         if args.pso_graphs > 0:
