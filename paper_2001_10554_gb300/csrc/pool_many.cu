@@ -48,6 +48,7 @@ constexpr int kMaxPasses = 4;
 
 struct Job {
   uint64_t state_off;      // first amplitude in the arena
+  void* mats;              // [phases][n] fused matrices (the dtype's Mat format), built by k_many_compose
   const double* U;         // [depth][n][8] on the device
   const double* ang;       // this trajectory's [n_noise][2] or nullptr
   const int* layer_base;   // [depth]
@@ -179,10 +180,8 @@ __global__ void __launch_bounds__(kThreads) k_pool_persistent(typename TR::V* __
     if (!prob) {
       const PassInfo& pi = gr.pass[p];
       const int ng = pi.q_hi - pi.q_lo;
-      if ((int)threadIdx.x < ng) {
-        Circuit C{job.n, job.depth, job.U, job.ang, job.layer_base, job.n_noise};
-        mats[threadIdx.x] = TR::make(compose_traj(C, job.ang, layer, pi.q_lo + threadIdx.x));
-      }
+      if ((int)threadIdx.x < ng)
+        mats[threadIdx.x] = static_cast<const Mat*>(job.mats)[(uint64_t)layer * job.n + pi.q_lo + threadIdx.x];
       __syncthreads();
       const unsigned cm = layer < job.depth ? pi.cmask[layer & 1] : 0u;
       pool_tile<TR>(sp, mats, P, pi.g, t, pi.lb0, ng, cm, bad);
@@ -213,17 +212,17 @@ __global__ void __launch_bounds__(kThreads) k_pool_persistent(typename TR::V* __
   if (bad) atomicOr(flag, 1u);
 }
 
-// Fused matrices of every job for the cluster-resident path: job j's
-// [phases][n] matrices start at mat_off[j]; blockIdx.y strides over jobs.
+// Fused matrices of every job, composed once in FP64 before the simulation
+// launch (job j's [phases][n] matrices at job.mats); blockIdx.y strides over jobs.
 template <class TR>
-__global__ void k_many_compose(const Job* __restrict__ jobs, int njobs, const uint64_t* __restrict__ mat_off,
-                               typename TR::Mat* __restrict__ mats) {
+__global__ void k_many_compose(const Job* __restrict__ jobs, int njobs) {
   for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
     const Job job = jobs[j];
     const Circuit C{job.n, job.depth, job.U, job.ang, job.layer_base, job.n_noise};
+    typename TR::Mat* m = static_cast<typename TR::Mat*>(job.mats);
     const int total = job.phases * job.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
-      mats[mat_off[j] + i] = TR::make(compose_traj(C, job.ang, i / job.n, i % job.n));
+      m[i] = TR::make(compose_traj(C, job.ang, i / job.n, i % job.n));
   }
 }
 
@@ -581,6 +580,27 @@ iqs_status run_many(iqs_pool_many* W, int nc, const iqs_circuit_desc* cd, double
     W->blob_bytes = off;
   }
   char* B = static_cast<char*>(W->blob);
+  // fused matrices of every job: [phases][n] each
+  using Mat = typename TR::Mat;
+  uint64_t nmat = 0;
+  for (const Job& j : jobs) nmat += (uint64_t)j.phases * j.n;
+  if (W->mats_bytes < nmat * sizeof(Mat)) {
+    cudaFree(W->mats);
+    W->mats = nullptr;
+    W->mats_bytes = 0;
+    if (cudaMalloc(&W->mats, nmat * sizeof(Mat)) != cudaSuccess) {
+      cudaGetLastError();
+      return report(IQS_ENOMEM, "cannot allocate %zu bytes of fused matrices", (size_t)(nmat * sizeof(Mat)));
+    }
+    W->mats_bytes = nmat * sizeof(Mat);
+  }
+  {
+    uint64_t mo = 0;
+    for (Job& j : jobs) {
+      j.mats = static_cast<Mat*>(W->mats) + mo;
+      mo += (uint64_t)j.phases * j.n;
+    }
+  }
   for (size_t i = 0; i < jobs.size(); ++i) {
     jobs[i].U = reinterpret_cast<const double*>(B + o_u) + job_u[i];
     jobs[i].ang = job_a[i] >= 0 ? reinterpret_cast<const double*>(B + o_a) + job_a[i] : nullptr;
@@ -615,6 +635,13 @@ iqs_status run_many(iqs_pool_many* W, int nc, const iqs_circuit_desc* cd, double
   if (e == cudaSuccess) e = cudaMemsetAsync(B + o_done, 0, njobs * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(B + o_ctrl, 0, 64, st);
   if (e != cudaSuccess) return report(IQS_ECUDA, "pool upload: %s", cudaGetErrorString(e));
+  {
+    const dim3 cg(8, (unsigned)std::min<size_t>(njobs, 65535));
+    k_many_compose<TR><<<cg, kThreads, 0, st>>>(reinterpret_cast<const Job*>(B + o_jobs), (int)njobs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return report(IQS_ECUDA, "compose launch: %s", cudaGetErrorString(e));
+    note_launches(1);
+  }
   // ---- cluster-resident path: every trajectory in one cluster launch
   int max_n = 0, min_n = 1 << 30;
   for (int c = 0; c < nc; ++c) {
@@ -627,46 +654,20 @@ iqs_status run_many(iqs_pool_many* W, int nc, const iqs_circuit_desc* cd, double
     return report(IQS_EINVAL, "the cluster engine takes these circuits only if every state fits (%d..%d qubits)",
                   min_n, max_n);
   if (W->engine == 2 || (W->engine == 0 && W->dtype == IQS_C64 && fits && lc <= 2)) {
-    using Mat = typename TR::Mat;
-    std::vector<uint64_t> mat_off(njobs);
-    uint64_t nmat = 0;
-    for (size_t j = 0; j < njobs; ++j) {
-      mat_off[j] = nmat;
-      nmat += (uint64_t)jobs[j].phases * jobs[j].n;
-    }
-    if (W->mats_bytes < nmat * sizeof(Mat)) {
-      cudaFree(W->mats);
-      W->mats = nullptr;
-      W->mats_bytes = 0;
-      if (cudaMalloc(&W->mats, nmat * sizeof(Mat)) != cudaSuccess) {
-        cudaGetLastError();
-        return report(IQS_ENOMEM, "cannot allocate %zu bytes of fused matrices", (size_t)(nmat * sizeof(Mat)));
-      }
-      W->mats_bytes = nmat * sizeof(Mat);
-    }
-    // the job table and the matrix offsets: scratch from the stream-ordered allocator
+    // the job table: scratch from the stream-ordered allocator
     void* scratch = nullptr;
-    const size_t tb = njobs * (sizeof(ClusterJob) + sizeof(uint64_t));
+    const size_t tb = njobs * sizeof(ClusterJob);
     if (cudaMallocAsync(&scratch, tb, st) != cudaSuccess) {
       cudaGetLastError();
       return report(IQS_ENOMEM, "cannot allocate the cluster job table");
     }
     ClusterJob* dcj = static_cast<ClusterJob*>(scratch);
-    uint64_t* dmo = reinterpret_cast<uint64_t*>(dcj + njobs);
-    Mat* mats = static_cast<Mat*>(W->mats);
     double* dprobs = reinterpret_cast<double*>(B + o_probs);
     std::vector<ClusterJob> cj(njobs);
     for (size_t j = 0; j < njobs; ++j)
-      cj[j] = ClusterJob{mats + mat_off[j], static_cast<V*>(W->arena) + jobs[j].state_off,
+      cj[j] = ClusterJob{jobs[j].mats, static_cast<V*>(W->arena) + jobs[j].state_off,
                          dprobs + out_off[jobs[j].out_index], jobs[j].n, jobs[j].phases, jobs[j].depth};
     e = cudaMemcpyAsync(dcj, cj.data(), njobs * sizeof(ClusterJob), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dmo, mat_off.data(), njobs * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
-    const Job* djobs = reinterpret_cast<const Job*>(B + o_jobs);
-    if (e == cudaSuccess) {
-      const dim3 cg(8, (unsigned)std::min<size_t>(njobs, 65535));
-      k_many_compose<TR><<<cg, kThreads, 0, st>>>(djobs, (int)njobs, dmo, mats);
-      e = cudaGetLastError();
-    }
     if (e == cudaSuccess) e = launch_pool_cluster(dcj, (int)njobs, max_n, W->dtype, st);
     if (e == cudaSuccess) {
       k_many_means<<<nc, 32, 0, st>>>(dprobs, reinterpret_cast<const uint64_t*>(B + o_cf),
@@ -676,7 +677,7 @@ iqs_status run_many(iqs_pool_many* W, int nc, const iqs_circuit_desc* cd, double
     }
     cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return report(IQS_ECUDA, "cluster pool launch: %s", cudaGetErrorString(e));
-    note_launches(2);  // compose and means (the cluster launch counts itself)
+    note_launches(1);  // means (compose and the cluster launch are counted where they launch)
     if (probs_out) e = cudaMemcpyAsync(probs_out, dprobs, nprob * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(means_out, B + o_means, nmean * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
