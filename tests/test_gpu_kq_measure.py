@@ -291,3 +291,56 @@ def test_sample_frequencies_follow_marginal(gpu_lib):
     p = r.marginal(qs)
     assert np.all(np.abs(freq - p) <= 5 * np.sqrt(p * (1 - p) / len(s)))
     r.close()
+
+
+# ---------------------------------------------------------------- degenerate shapes
+@pytest.mark.parametrize("dtype,math,n", [("complex64", None, 3), ("complex64", None, 5), ("complex128", "native", 3),
+                                          ("complex128", "emulated", 4)])
+def test_apply_kq_on_every_qubit_is_the_full_matrix(gpu_lib, dtype, math, n):
+    """k = n: one group, the gate is the whole unitary acting on the state."""
+    g = W.rng(4300 + n)
+    psi = state(n, 4301, dtype)
+    r = make_reg(gpu_lib, n, dtype, math, psi)
+    qs = list(g.permutation(n))
+    U = haar(n, g)
+    r.apply_kq(qs, U)
+    Ur = U.astype(np.complex64).astype(np.complex128) if dtype == "complex64" else U
+    ref = sv.apply_kq(psi.astype(np.complex128), qs, Ur)
+    tol = 1e-12 if dtype == "complex128" else gamma(2 << n) * np.sqrt(2) * np.max(np.abs(ref)) * np.sqrt(1 << n) * 2
+    assert np.max(np.abs(r.download().astype(np.complex128) - ref)) <= tol
+    r.close()
+
+
+@pytest.mark.parametrize("dtype,math", MODES)
+def test_apply_kq_single_qubit_agrees_with_apply_1q(gpu_lib, dtype, math):
+    n = 11
+    g = W.rng(4401)
+    psi = state(n, 4402, dtype)
+    a = make_reg(gpu_lib, n, dtype, math, psi)
+    b = make_reg(gpu_lib, n, dtype, math, psi)
+    for q in (0, 4, 10):
+        U = W.haar_u2(g)
+        a.apply_kq([q], U)
+        b.apply_1q(q, U)
+    tol = 1e-12 if dtype == "complex128" else 3 * 8 * 2.0 ** -24
+    assert np.max(np.abs(a.download().astype(np.complex128) - b.download().astype(np.complex128))) <= tol
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+@pytest.mark.parametrize("n", [4, 7, 10])
+def test_marginal_over_all_qubits_is_the_distribution(gpu_lib, dtype, n):
+    """A marginal over every qubit (in a permuted order) is |psi_i|^2 with the
+    index bits reordered."""
+    g = W.rng(4500 + n)
+    psi = state(n, 4501 + n, dtype)
+    r = make_reg(gpu_lib, n, dtype, None, psi)
+    qs = [int(q) for q in g.permutation(n)]
+    m = r.marginal(qs)
+    w = np.abs(psi.astype(np.complex128)) ** 2
+    ref = np.zeros(1 << n)
+    for i in range(1 << n):
+        ref[sum(((i >> q) & 1) << j for j, q in enumerate(qs))] = w[i]
+    assert np.max(np.abs(m - ref)) <= 1e-12
+    r.close()

@@ -103,3 +103,24 @@ def test_multi_graph_rejects_bad_arguments(gpu_lib):
     with pytest.raises(ValueError):
         eng.pso(pos[:1], vel[:1], rp[:, :1], rg[:, :1])
     eng.close()
+
+
+def test_cluster_forward_on_a_multi_graph_workspace(gpu_lib):
+    """The opt-in cluster-resident forward reads each state's own graph."""
+    from paper_2001_10554_gb300 import IQSError
+    n, p, G, R = 12, 3, 3, 4
+    gs = graphs(n, G, 1700)
+    gm, bt = W.qaoa_parameter_sets(p, G * R, 1701)
+    eng = gpu_lib.QAOA(n, None, "complex64", graphs=gs, per_graph=R)
+    try:
+        eng.set_engine("cluster")
+    except IQSError:
+        eng.close()
+        pytest.skip("cluster-resident forward unavailable")
+    E = eng.run(gm, bt, grad=False)
+    eng.set_engine("tiled")
+    Et = eng.run(gm, bt, grad=False)
+    eng.close()
+    assert np.max(np.abs(E - Et)) <= 2e-6
+    for b in (0, 5, 11):
+        assert abs(E[b] - oq.qaoa_energy(n, gs[b // R], gm[b], bt[b])) <= 2e-6
