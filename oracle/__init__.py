@@ -16,18 +16,24 @@ building blocks.  Readings of points the paper leaves open are stated at the
 function that takes them.
 
 Modules:
-  statevector  state initialisation, one-qubit and controlled one-qubit gates,
-               the Max-Cut cost diagonal and its phase, probability, Pauli
-               expectation, norm, energy.
+  statevector  state initialisation, one-qubit, controlled one-qubit and
+               dense k-qubit gates, the Max-Cut cost diagonal and its phase,
+               probability, qubit-group marginals, inverse-transform
+               sampling, Pauli expectation, norm, energy.
   qaoa         QAOA Max-Cut state and energy, stored-state adjoint gradient,
-               central finite differences.
+               central finite differences, brute-force Max-Cut.
   ensemble     gate lists run on one state, noise-rotation trajectories and
                pool (ensemble) averages.
+  noise        T1/T2 noise gates (the angle law is a reading: the paper cites
+               it from other work) and their averaged channel.
+  pso          the particle swarm over QAOA parameters (Section 4).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-to closed forms, brute-force Kronecker matrices, invariants, or the paper's
-own worked listing, except ``ensemble.noisy_trajectory_ops`` whose noise model
-(X then Z rotation with Gaussian angles) is not the paper's T1/T2 model; its
-statistical pin is against a density-matrix channel written in the test.
+to closed forms, brute-force matrices and sums, invariants, special cases
+worked by hand, or the paper's own worked listing.  Two noise models are
+pinned statistically and by quadrature: ``ensemble.noisy_trajectory_ops``
+(X then Z rotations with Gaussian angles, against a density-matrix channel
+written in the test) and ``noise.t1t2_trajectory_ops`` (against the decay
+laws exp(-t/T1), exp(-t/T2) that T1 and T2 name).
 """
-from . import statevector, qaoa, ensemble  # noqa: F401
+from . import statevector, qaoa, ensemble, noise, pso  # noqa: F401
