@@ -84,11 +84,7 @@ __device__ __forceinline__ void local_round(typename TR::W* st, const typename T
   }
   const unsigned ngr = NL >> RBT;
   const unsigned lowm = (1u << b0) - 1u;
-  for (unsigned g = threadIdx.x; g < ngr; g += kCT) {
-    const unsigned base = ((g >> b0) << (b0 + RBT)) | (g & lowm);
-    W x[1 << RBT];
-#pragma unroll
-    for (int c = 0; c < (1 << RBT); ++c) x[c] = st[phys(base | ((unsigned)c << b0))];
+  auto apply_group = [&](W (&x)[1 << RBT]) {
 #pragma unroll
     for (int j = 0; j < RBT; ++j) {
 #pragma unroll
@@ -98,6 +94,34 @@ __device__ __forceinline__ void local_round(typename TR::W* st, const typename T
           else TR::apply(mats[b0 + j], x[c], x[c | (1 << j)]);
         }
     }
+  };
+  // complex64: two groups per iteration (their shared-memory loads overlap),
+  // then a tail of one; complex128 groups are too large for two in registers
+  unsigned g = threadIdx.x;
+  for (; sizeof(W) == 8 && g + kCT < ngr; g += 2 * kCT) {
+    const unsigned base0 = ((g >> b0) << (b0 + RBT)) | (g & lowm);
+    const unsigned g1 = g + kCT;
+    const unsigned base1 = ((g1 >> b0) << (b0 + RBT)) | (g1 & lowm);
+    W x0[1 << RBT], x1[1 << RBT];
+#pragma unroll
+    for (int c = 0; c < (1 << RBT); ++c) {
+      x0[c] = st[phys(base0 | ((unsigned)c << b0))];
+      x1[c] = st[phys(base1 | ((unsigned)c << b0))];
+    }
+    apply_group(x0);
+    apply_group(x1);
+#pragma unroll
+    for (int c = 0; c < (1 << RBT); ++c) {
+      st[phys(base0 | ((unsigned)c << b0))] = x0[c];
+      st[phys(base1 | ((unsigned)c << b0))] = x1[c];
+    }
+  }
+  for (; g < ngr; g += kCT) {
+    const unsigned base = ((g >> b0) << (b0 + RBT)) | (g & lowm);
+    W x[1 << RBT];
+#pragma unroll
+    for (int c = 0; c < (1 << RBT); ++c) x[c] = st[phys(base | ((unsigned)c << b0))];
+    apply_group(x);
 #pragma unroll
     for (int c = 0; c < (1 << RBT); ++c) st[phys(base | ((unsigned)c << b0))] = x[c];
   }
