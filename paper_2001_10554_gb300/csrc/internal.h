@@ -1,6 +1,7 @@
 // Internal declarations shared by the C-ABI layer and the kernel files.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -29,6 +30,29 @@ constexpr int kRedBlocks = 1024;        // blocks of every reduction kernel (fix
 constexpr int kRedSlots = 40;           // values reduced at once (n + 1 for all-qubit probabilities)
 constexpr int kMaxEdgesFast = 255;      // unweighted ZZ phase: table-driven fast path bound
 constexpr int kMaxEdges = 4096;
+
+// A positive integer worked out once per device (kernel attributes and
+// occupancy belong to a device).  Threads that race on the first call each
+// compute it and store the same value; devices past kDevices are not cached.
+struct PerDevice {
+  static constexpr int kDevices = 64;
+  std::atomic<int> v[kDevices] = {};
+  // ``compute(&x)`` sets x (> 0) for the current device.
+  template <class F>
+  cudaError_t get(int* out, F&& compute) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool cached = dev >= 0 && dev < kDevices;
+    if (cached && (*out = v[dev].load(std::memory_order_acquire)) > 0) return cudaSuccess;
+    int x = 0;
+    e = compute(&x);
+    if (e != cudaSuccess) return e;
+    *out = x > 0 ? x : 1;
+    if (cached) v[dev].store(*out, std::memory_order_release);
+    return cudaSuccess;
+  }
+};
 
 // Kernel-launch accounting (iqs_kernel_launches).
 void note_launches(int k);

@@ -469,15 +469,15 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
       TilePlan<K> P;
       if (low && make_tile_plan<K>(r->n, qubits, P)) {
         const size_t smem = sizeof(float2) * ((size_t)(1 << tile_bits<K>()) + (size_t)(D * D)) + sizeof(uint64_t) * D;
-        static int per_sm = 0;  // per K instantiation: resident blocks per SM
-        if (per_sm == 0) {
-          cudaError_t e = cudaFuncSetAttribute(k_kgate_c64_tiled<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        static PerDevice resident;  // per K instantiation: resident blocks per SM
+        int per_sm = 0;
+        cudaError_t e = resident.get(&per_sm, [&](int* x) {
+          cudaError_t f = cudaFuncSetAttribute(k_kgate_c64_tiled<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
-          if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kgate_c64_tiled<K>, kThreads, smem);
-          if (e != cudaSuccess) return e;
-          per_sm = std::max(per_sm, 1);
-        }
+          if (f == cudaSuccess) f = cudaOccupancyMaxActiveBlocksPerMultiprocessor(x, k_kgate_c64_tiled<K>, kThreads, smem);
+          return f;
+        });
+        if (e != cudaSuccess) return e;
         const uint64_t n_tiles = num_amps(r) >> tile_bits<K>();
         const unsigned tg = (unsigned)std::min<uint64_t>(n_tiles, (uint64_t)per_sm * kSMs);
         k_kgate_c64_tiled<K><<<tg, kThreads, smem, r->stream>>>((float2*)r->data, n_tiles, P, u);

@@ -386,13 +386,13 @@ namespace {
 
 template <class V, int KR>
 int occupancy_of() {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_marginal<V, KR>, kThreads, 0) != cudaSuccess) {
-      cudaGetLastError();
-      per_sm = 2;
-    }
-    per_sm = std::max(per_sm, 1);
+  static PerDevice resident;
+  int per_sm = 0;
+  if (resident.get(&per_sm, [](int* x) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(x, k_marginal<V, KR>, kThreads, 0);
+      }) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 2;  // the kernel's launch bound
   }
   return per_sm;
 }
