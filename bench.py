@@ -58,9 +58,9 @@ def parse_args(argv=None):
                     help="one noisy brick circuit of TRAJ complex64 trajectories on the cluster-resident engine (for ncu)")
     ap.add_argument("--profile-ops", type=int, default=0, metavar="N",
                     help="one small invocation of apply_kq, marginal and sample on N-qubit states (for ncu)")
-    ap.add_argument("--profile-qaoa", default=None, metavar="N,P,BATCH",
-                    help="run one complex64 QAOA energy + gradient evaluation of BATCH parameter sets and exit "
-                         "(a small, fixed launch sequence for profilers)")
+    ap.add_argument("--profile-qaoa", default=None, metavar="N,P,BATCH[,RENORM]",
+                    help="run one complex64 QAOA energy + gradient evaluation of BATCH parameter sets (renormalised "
+                         "every RENORM layers, default never) and exit (a small, fixed launch sequence for profilers)")
     return ap.parse_args(argv)
 
 
@@ -609,12 +609,14 @@ def profile_ops(n: int) -> int:
 def profile_qaoa(spec: str) -> int:
     import paper_2001_10554_gb300 as iqs
     import workloads as W
-    n, p, batch = (int(v) for v in spec.split(","))
+    vals = [int(v) for v in spec.split(",")]
+    n, p, batch = vals[:3]
+    renorm = vals[3] if len(vals) > 3 else 0
     edges = W.random_3regular_graph(n, 1000 + n)
     gm, bt = W.qaoa_parameter_sets(p, batch, 7)
-    eng = iqs.QAOA(n, edges, "complex64", batch_max=batch)
+    eng = iqs.QAOA(n, edges, "complex64", batch_max=batch, renorm_every=renorm)
     E, _, _ = eng.run(gm, bt)
-    print(json.dumps({"profile_qaoa": [n, p, batch], "energy0": float(E[0])}))
+    print(json.dumps({"profile_qaoa": [n, p, batch, renorm], "energy0": float(E[0])}))
     eng.close()
     return 0
 

@@ -261,7 +261,8 @@ iqs_status iqs_qaoa_tuning(const iqs_qaoa* q, int* row_bits, int* grid_mult);
  * loads and stores, double-buffered): mode 0 off, 1 forward passes, 2 forward
  * and adjoint passes.  It applies to full 2^K-amplitude tiles (n >= 12 for
  * complex64, 11 for complex128); ``available`` reports whether the tensor maps
- * of the current plan could be built.  The autotuner also chooses this mode. */
+ * of the current plan could be built.  The default is 1; the autotuner also
+ * chooses this mode. */
 iqs_status iqs_qaoa_set_tma(iqs_qaoa* q, int mode);
 iqs_status iqs_qaoa_get_tma(const iqs_qaoa* q, int* mode, int* available);
 

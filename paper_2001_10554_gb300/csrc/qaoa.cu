@@ -292,22 +292,55 @@ __device__ __forceinline__ void mixer_rounds(typename TR::W* sp, typename TR::W*
   }
 }
 
+// Renormalisation fused into the adjoint passes (complex64 only).  With
+// ``norms`` set, a pass scales phi and lambda by sqrt(target / norm) as it loads
+// them; ``norms`` holds [4][stride] values: current |phi|^2, lambda target,
+// phi target, current |lambda|^2.  With ``partials`` set, the fused-phase pass
+// (PH = 2) sums |phi|^2 and |lambda|^2 of the values it stores, per block, in
+// FP64-equivalent arithmetic, to partials[b][x] and partials[b][kRnCol + x].
+struct RenormFuse {
+  const double* norms = nullptr;
+  int stride = 0;
+  double* partials = nullptr;
+};
+constexpr int kRnCol = 2432;
+
 // PH = 1 (forward, low pass): the layer's cost phase T_b[C(x)] is applied to
 // each amplitude as the tile is loaded.  PH = 2 (adjoint, last pass): after the
 // mixer uncompute, each amplitude contributes C(x) Im(conj(lambda) phi) to the
 // phase gradient (partials_g) and both vectors are multiplied by
 // conj(T_b[C(x)]) as they are stored.  Either way one full pass per layer is saved.
 template <class TR, bool ADJ, int C, int PH>
-__global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restrict__ phi,
+__device__ __forceinline__ void mixer_fast_body(typename TR::V* __restrict__ phi,
                                                          typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
                                                          const typename TR::RX* __restrict__ rx,
                                                          double* __restrict__ partials, int part_stride, unsigned* flag,
                                                          const uint8_t* __restrict__ cut,
                                                          const typename TR::PH* __restrict__ tables, int tsize,
-                                                         double* __restrict__ partials_g, int per_graph) {
+                                                         double* __restrict__ partials_g, int per_graph,
+                                                         const RenormFuse rn) {
   using W = typename TR::W;
   using PHT = typename TR::PH;
+  constexpr bool kRn = ADJ && TR::kBlockSum;  // fused renormalisation: complex64 adjoint passes
   __shared__ PHT st[PH ? kEdgeChunk + 1 : 1];
+  __shared__ float rn_f[2];
+  bool scale_in = false;
+  float f_phi = 1.f, f_lam = 1.f;
+  if constexpr (kRn) {
+    if (rn.norms) {
+      if (threadIdx.x == 0) {
+        const unsigned b = blockIdx.y;
+        const double np = rn.norms[b], tl = rn.norms[rn.stride + b];
+        const double tp = rn.norms[2 * rn.stride + b], nl = rn.norms[3 * rn.stride + b];
+        rn_f[0] = (float)(np > 0.0 ? sqrt(tp / np) : 1.0);
+        rn_f[1] = (float)(nl > 0.0 ? sqrt(tl / nl) : 1.0);
+      }
+      __syncthreads();
+      scale_in = true;
+      f_phi = rn_f[0];
+      f_lam = rn_f[1];
+    }
+  }
   if (PH) {
     cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
     for (int i = threadIdx.x; i < tsize; i += blockDim.x) {
@@ -338,6 +371,14 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restr
   const int mid = s - C;
   unsigned bad = 0;
   dfx::Acc acc, accg;
+  // fused renormalisation: this thread's running |phi|^2 and |lambda|^2, kept in
+  // shared memory between tiles so that they hold no registers across the rounds
+  __shared__ dfx::Acc rn_acc[kRn && PH == 2 ? 2 * kThreads : 1];
+  const bool norm_out = kRn && PH == 2 && rn.partials != nullptr;
+  if constexpr (kRn && PH == 2) {
+    rn_acc[tid] = dfx::Acc();
+    rn_acc[kThreads + tid] = dfx::Acc();
+  }
   for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
 #pragma unroll
@@ -345,13 +386,33 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restr
       const unsigned l = tid + kThreads * i;
       const uint64_t x = C <= 8 ? tbase + off0 + step * i : tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
       const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
-      if (PH == 1) sp[idx] = TR::mul(st[cut[x]], TR::load(P[x], bad));
-      else sp[idx] = TR::load(P[x], bad);
-      if (ADJ) sl[idx] = TR::load(L[x], bad);
+      if (PH == 1) {
+        sp[idx] = TR::mul(st[cut[x]], TR::load(P[x], bad));
+      } else {
+        W w = TR::load(P[x], bad);
+        if constexpr (kRn) {
+          if (scale_in) w = qops::scale_int(w, f_phi);
+        }
+        sp[idx] = w;
+      }
+      if (ADJ) {
+        W w = TR::load(L[x], bad);
+        if constexpr (kRn) {
+          if (scale_in) w = qops::scale_int(w, f_lam);
+        }
+        sl[idx] = w;
+      }
     }
     __syncthreads();
     mixer_rounds<TR, ADJ, C, C>(sp, sl, k, acc);
     float gsum = 0.f;
+    dfx::Acc acc_np, acc_nl;
+    if constexpr (kRn && PH == 2) {
+      if (norm_out) {
+        acc_np = rn_acc[tid];
+        acc_nl = rn_acc[kThreads + tid];
+      }
+    }
 #pragma unroll
     for (unsigned i = 0; i < PER; ++i) {
       const unsigned l = tid + kThreads * i;
@@ -369,19 +430,70 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast(typename TR::V* __restr
           const float qq = cf * pp;
           accg.add(qq, fmaf(cf, pp, -qq) + cf * ee);
         }
-        P[x] = TR::store(TR::mul(st[c], xv));
-        L[x] = TR::store(TR::mul(st[c], yv));
+        const W xo = TR::mul(st[c], xv), yo = TR::mul(st[c], yv);
+        if constexpr (kRn) {
+          if (norm_out) {
+            float pp, ee;
+            qops::abs2(xo, pp, ee);
+            acc_np.add(pp, ee);
+            qops::abs2(yo, pp, ee);
+            acc_nl.add(pp, ee);
+          }
+        }
+        P[x] = TR::store(xo);
+        L[x] = TR::store(yo);
       } else {
         P[x] = TR::store(sp[idx]);
         if (ADJ) L[x] = TR::store(sl[idx]);
       }
     }
     if (PH == 2 && TR::kBlockSum) accg.add(gsum, 0.f);
+    if constexpr (kRn && PH == 2) {
+      if (norm_out) {
+        rn_acc[tid] = acc_np;
+        rn_acc[kThreads + tid] = acc_nl;
+      }
+    }
     __syncthreads();
   }
   if (bad) atomicOr(flag, 1u);
   if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
   if (PH == 2) block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
+  if constexpr (kRn && PH == 2) {
+    if (norm_out) {
+      block_partial(rn_acc[tid].value(), rn.partials + (uint64_t)b * part_stride + blockIdx.x);
+      block_partial(rn_acc[kThreads + tid].value(), rn.partials + (uint64_t)b * part_stride + kRnCol + blockIdx.x);
+    }
+  }
+}
+
+// The shape-specialised pass kernels.  The adjoint ones are held to 128
+// registers (two 256-thread blocks per SM); the forward ones are left to the
+// compiler's default, which keeps them near 80-100.
+#define IQS_MIXER_FAST_PARAMS                                                                                    \
+  typename TR::V *__restrict__ phi, typename TR::V *__restrict__ lam, uint64_t N, int s_bits,                    \
+      const typename TR::RX *__restrict__ rx, double *__restrict__ partials, int part_stride, unsigned *flag,    \
+      const uint8_t *__restrict__ cut, const typename TR::PH *__restrict__ tables, int tsize,                    \
+      double *__restrict__ partials_g, int per_graph, const RenormFuse rn
+#define IQS_MIXER_FAST_ARGS \
+  phi, lam, N, s_bits, rx, partials, part_stride, flag, cut, tables, tsize, partials_g, per_graph, rn
+template <class TR, int C, int PH>
+__global__ void __launch_bounds__(kThreads) k_mixer_fast_fwd(IQS_MIXER_FAST_PARAMS) {
+  mixer_fast_body<TR, false, C, PH>(IQS_MIXER_FAST_ARGS);
+}
+template <class TR, int C, int PH>
+__global__ void __launch_bounds__(kThreads, 2) k_mixer_fast_adj(IQS_MIXER_FAST_PARAMS) {
+  mixer_fast_body<TR, true, C, PH>(IQS_MIXER_FAST_ARGS);
+}
+#undef IQS_MIXER_FAST_PARAMS
+#undef IQS_MIXER_FAST_ARGS
+
+template <class TR, bool ADJ, int C, int PH>
+constexpr auto k_mixer_fast() {
+  if constexpr (ADJ)
+    return k_mixer_fast_adj<TR, C, PH>;
+  else
+    return k_mixer_fast_fwd<TR, C, PH>;
 }
 
 // ---------------------------------------------------------------- TMA-staged mixer pass
@@ -705,12 +817,21 @@ __global__ void k_finalize_batch(const double* __restrict__ partials, int count,
   }
 }
 
-// a_b <- a_b * sqrt(target_b / norm_b)   (target == nullptr: target 1)
+// a_b <- a_b * sqrt(target_b / norm_b)   (target == nullptr: target 1).  The
+// factor is formed once per block in FP64 and rounded to the storage precision,
+// so complex64 states are scaled on the FP32 pipe (one rounding of the factor,
+// one of the product: the same order as storing an FP64-scaled value).
 template <class V>
 __global__ void k_rescale(V* __restrict__ a, uint64_t N, const double* __restrict__ norm, const double* __restrict__ target) {
+  using S = decltype(V::x);
+  __shared__ S fs;
   const unsigned b = blockIdx.y;
-  const double nb = norm[b];
-  const double f = nb > 0.0 ? sqrt((target ? target[b] : 1.0) / nb) : 1.0;
+  if (threadIdx.x == 0) {
+    const double nb = norm[b];
+    fs = (S)(nb > 0.0 ? sqrt((target ? target[b] : 1.0) / nb) : 1.0);
+  }
+  __syncthreads();
+  const S f = fs;
   V* P = a + (uint64_t)b * N;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
     V v = P[i];
@@ -741,7 +862,8 @@ struct iqs_qaoa {
   void* tables = nullptr;      // [kMaxP][bmax][n_edges + 1] phase factors
   double* partials = nullptr;  // [bmax][part_stride]
   double* results = nullptr;   // [bmax][1 + 2 kMaxP]
-  double* norms = nullptr;     // [3][bmax]: current norm, lambda target, phi norm after the forward pass
+  double* norms = nullptr;     // [4][bmax]: current norm, lambda target, phi norm after the forward pass,
+                               // current lambda norm (fused renormalisation)
   unsigned* flag = nullptr;
   unsigned char* host_params = nullptr;  // pinned staging of rx + tables
   double* host_results = nullptr;        // pinned
@@ -753,8 +875,11 @@ struct iqs_qaoa {
   // tile-shape choice (autotuner): high-pass row bits (-1: default) and grid multiplier
   int row_bits = -1;
   int grid_mult = 1;
-  // TMA-staged mixer passes: 0 off, 1 forward passes, 2 forward and adjoint passes
-  int tma_mode = 0;
+  // TMA-staged mixer passes: 0 off, 1 forward passes, 2 forward and adjoint passes.
+  // Forward staging is the default: it measured 5-6% faster than register-loaded
+  // tiles at 16-28 qubits, while staged adjoint passes (128 KB, one block per SM)
+  // measured slower.  Passes whose tensor maps could not be built load directly.
+  int tma_mode = 1;
   std::vector<CUtensorMap> tm_phi, tm_lam;  // one per mixer pass (valid when tma_ok)
   bool tma_ok = false;
   unsigned* tma_err = nullptr;              // device word: a TMA wait gave up
@@ -776,9 +901,11 @@ namespace {
 bool use_cluster(const iqs_qaoa* q) { return q->engine == 2 && q->clogc >= 0 && q->cclusters > 0; }
 
 // Partial slots per state: mixer passes x blocks (<= 4 x 2432), then the fused
-// phase-gradient partials at kGammaCol.
+// phase-gradient partials at kGammaCol, then the fused renormalisation's norm
+// partials (|phi|^2 at kNormCol, |lambda|^2 at kNormCol + kRnCol).
 constexpr int kGammaCol = 2432 * 4;
-int part_stride_for(const iqs_qaoa* q) { return 2432 * 5; }
+constexpr int kNormCol = 2432 * 5;
+int part_stride_for(const iqs_qaoa* q) { return 2432 * 7; }
 
 int blocks_per_state(const iqs_qaoa* q, int B) {
   const uint64_t by_size = std::max<uint64_t>(1, q->N / 4096);
@@ -824,31 +951,32 @@ struct PhaseFuse {
   int tsize = 0;
   double* partials_g = nullptr;
   int per_graph = 1 << 30;  // state b uses cut table b / per_graph
+  RenormFuse rn;            // fused renormalisation (adjoint, complex64, shape-specialised passes)
 };
 
 template <class TR, bool ADJ, int C>
 void launch_fast(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N, int sb,
                  const typename TR::RX* rx, double* partials, int ps, unsigned* flag, const PhaseFuse<TR>& f) {
   if (!ADJ && f.mode == 1)
-    k_mixer_fast<TR, ADJ, C, (ADJ ? 0 : 1)><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
+    k_mixer_fast<TR, ADJ, C, (ADJ ? 0 : 1)>()<<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
                                                                           f.cut, f.tables, f.tsize, f.partials_g,
-                                                                          f.per_graph);
+                                                                          f.per_graph, RenormFuse());
   else if (ADJ && f.mode == 2)
-    k_mixer_fast<TR, ADJ, C, (ADJ ? 2 : 0)><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
+    k_mixer_fast<TR, ADJ, C, (ADJ ? 2 : 0)>()<<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag,
                                                                           f.cut, f.tables, f.tsize, f.partials_g,
-                                                                          f.per_graph);
+                                                                          f.per_graph, f.rn);
   else
-    k_mixer_fast<TR, ADJ, C, 0><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag, nullptr, nullptr,
-                                                             0, nullptr, 1);
+    k_mixer_fast<TR, ADJ, C, 0>()<<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, partials, ps, flag, nullptr, nullptr,
+                                                             0, nullptr, 1, f.rn);
 }
 
 template <class TR, int C>
 cudaError_t set_attr_c(int bytes) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C, 0>, a, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C, 0>, a, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C, 1>, a, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C, 2>, a, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C, 0>(), a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C, 0>(), a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, false, C, 1>(), a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_fast<TR, true, C, 2>(), a, bytes);
   return e;
 }
 
@@ -1063,8 +1191,15 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
       launches += 2;
     }
     double* partials_g = q->partials + kGammaCol;  // phase-gradient partials of the fused last pass
+    // complex64 on the shape-specialised adjoint passes: the last pass of a layer
+    // sums the norms of what it stores and the next layer's first pass rescales
+    // on load, instead of separate norm and rescale passes over both vectors
+    const bool adj_tma = q->tma_ok && q->tma_mode >= 2;
+    const bool fuse_rn = std::is_same<TR, T64>::value && R > 0 && fuse_out && fuse_in && !adj_tma;
+    bool scale_pending = false;
     for (int l = p - 1; l >= 0; --l) {
       const typename TR::PH* tab_l = tab + (uint64_t)l * q->bmax * tsize;
+      const bool renorm_after = R > 0 && l > 0 && ((p - l) % R) == 0;
       int col = 0;
       unsigned last_gx = 0;
       for (size_t i = 0; i < q->passes.size(); ++i) {
@@ -1080,9 +1215,15 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
           f.tables = tab_l;
           f.tsize = tsize;
           f.partials_g = partials_g;
+          if (fuse_rn && renorm_after) f.rn.partials = q->partials + kNormCol;
+        }
+        if (i == 0 && scale_pending) {
+          f.rn.norms = q->norms;
+          f.rn.stride = q->bmax;
+          scale_pending = false;
         }
         TmaArgs ta;
-        ta.use = q->tma_ok && q->tma_mode >= 2;
+        ta.use = adj_tma;
         ta.phi = &q->tm_phi[i];
         ta.lam = &q->tm_lam[i];
         ta.hi_bits = q->n - g.s - g.m;
@@ -1104,7 +1245,13 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
         k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 2.0, q->results, out_stride, 1 + l);
         launches += 2;
       }
-      if (R > 0 && l > 0 && ((p - l) % R) == 0) {
+      if (renorm_after && fuse_rn) {
+        k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + kNormCol, (int)last_gx, ps, 1.0, q->norms, 1, 0);
+        k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + kNormCol + kRnCol, (int)last_gx, ps, 1.0,
+                                                q->norms + 3 * q->bmax, 1, 0);
+        launches += 2;
+        scale_pending = true;
+      } else if (renorm_after) {
         k_norm_batch<TR><<<g_stream, kThreads, 0, s>>>(phi, N, q->partials, ps, q->flag);
         k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials, PB, ps, 1.0, q->norms, 1, 0);
         k_rescale<V><<<g_stream, kThreads, 0, s>>>(phi, N, q->norms, phi_norm);
@@ -1333,7 +1480,7 @@ iqs_status iqs_qaoa_create_multi(int n, int dtype, int n_graphs, int per_graph, 
             cudaMalloc(&q->tables, q->table_bytes) == cudaSuccess &&
             cudaMalloc(&q->partials, sizeof(double) * (size_t)ps * batch_max) == cudaSuccess &&
             cudaMalloc(&q->results, sizeof(double) * (size_t)batch_max * (1 + 2 * kMaxP)) == cudaSuccess &&
-            cudaMalloc(&q->norms, sizeof(double) * 3 * (size_t)batch_max) == cudaSuccess &&
+            cudaMalloc(&q->norms, sizeof(double) * 4 * (size_t)batch_max) == cudaSuccess &&
             cudaMalloc(&q->flag, sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&q->tma_err, sizeof(unsigned)) == cudaSuccess &&
             cudaMallocHost(&q->host_params, q->rx_bytes + q->table_bytes) == cudaSuccess &&

@@ -117,7 +117,7 @@ class QAOA:
         return {"row_bits": rows.value, "grid_mult": mult.value, "tma_mode": tma.value, "tma_available": bool(avail.value)}
 
     def set_tma(self, mode: int) -> None:
-        """Stage mixer tiles with TMA: 0 off, 1 forward passes, 2 forward and adjoint passes."""
+        """Stage mixer tiles with TMA: 0 off, 1 forward passes (the default), 2 forward and adjoint passes."""
         call("iqs_qaoa_set_tma", self._h, int(mode))
 
     def state(self, index: int = 0) -> np.ndarray:

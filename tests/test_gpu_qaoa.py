@@ -124,6 +124,34 @@ def test_qaoa_renormalisation_keeps_results(gpu_lib):
     assert np.max(np.abs(db1 - dbo)) <= 1e-4
 
 
+@pytest.mark.parametrize("n,R", [(12, 1), (14, 2), (16, 1), (16, 3), (20, 2)])
+def test_qaoa_fused_renormalisation(gpu_lib, n, R):
+    """complex64 renormalisation inside the adjoint passes (norms summed by a
+    layer's last pass, rescaling on the next layer's first load): the same
+    energies and gradients as without renormalisation and as the oracle, and
+    as the separate norm and rescale kernels (TMA adjoint passes) when TMA is
+    available."""
+    p, B = 5, 3
+    edges = W.random_3regular_graph(n, 40 + n)
+    gm, bt = W.qaoa_parameter_sets(p, B, 41 + n)
+    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=B)
+    E0, dg0, db0 = eng.run(gm, bt)
+    eng.set_options(renorm_every=R)
+    E1, dg1, db1 = eng.run(gm, bt)
+    assert np.max(np.abs(E1 - E0)) <= 2e-6
+    assert np.max(np.abs(dg1 - dg0)) <= 1e-4 and np.max(np.abs(db1 - db0)) <= 1e-4
+    if n <= 16:
+        Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+        assert np.max(np.abs(E1 - Eo)) <= 2e-6
+        assert np.max(np.abs(dg1 - dgo)) <= 1e-4 and np.max(np.abs(db1 - dbo)) <= 1e-4
+    if eng.tuning()["tma_available"]:
+        eng.set_tma(2)
+        E2, dg2, db2 = eng.run(gm, bt)
+        assert np.max(np.abs(E2 - E1)) <= 2e-6
+        assert np.max(np.abs(dg2 - dg1)) <= 1e-4 and np.max(np.abs(db2 - db1)) <= 1e-4
+    eng.close()
+
+
 def test_qaoa_batch_items_equal_single_runs(gpu_lib):
     n, p, B = 12, 2, 5
     edges = W.random_3regular_graph(n, 15)
