@@ -371,7 +371,10 @@ iqs_status iqs_pool_set_engine(iqs_pool* p, int engine);
  * each CNOT's control and target), or NULL for the noiseless circuit.
  * Outputs (host): probs[batch][n] = P(q = 1) of each trajectory (divided by
  * the computed state's squared norm, FP64) or NULL; mean[n] = pool average.
- * Synchronous. */
+ * Synchronous.  On the tiled passes the first run of each (batch, depth,
+ * noisy) shape is captured as a CUDA graph and later runs of that shape replay
+ * it (the inputs sit in fixed device buffers); iqs_pool_set_noise_t1t2 drops
+ * the captured graphs.  A pool on the legacy default stream launches directly. */
 iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* unitaries, const double* angles,
                               double* probs, double* mean);
 

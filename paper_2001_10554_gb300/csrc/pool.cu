@@ -21,7 +21,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -179,6 +181,9 @@ struct iqs_pool {
   int engine = 0;  // 0 auto (cluster-resident when the state fits), 1 tiled passes, 2 cluster-resident
   int noise_model = 0;       // 0 angle pairs (tx, tz); 1 T1/T2 gates from normal triples
   double sig[3] = {0, 0, 0};  // T1/T2 gate angle standard deviations (x, y, z)
+  // tiled-pass runs captured as CUDA graphs, per (batch, depth, noisy): the
+  // executable graph and the kernels it launches
+  std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, int>> graphs;
 };
 
 namespace iqs {
@@ -224,30 +229,67 @@ unsigned cnot_mask(const Pass& p, int n, int layer) {
   return mask;
 }
 
+// The circuit description the compose kernel reads (device pointers and the noise law).
+Circuit circuit_of(const iqs_pool* P, int depth, bool noisy) {
+  Circuit C{P->n, depth, P->U, noisy ? P->angles : nullptr, P->layer_base, n_noise_ops(P->n, depth)};
+  C.model = P->noise_model;
+  for (int k = 0; k < 3; ++k) C.sig[k] = P->sig[k];
+  return C;
+}
+
+// The tiled-pass run: fused matrices, |0>, the layer passes, then per-trajectory
+// P(1) and the pool mean.  ``launches`` counts the kernels enqueued.
+template <class TR>
+void enqueue_tiled(iqs_pool* P, int batch, int depth, bool noisy, int* launches) {
+  using V = typename TR::V;
+  using Mat = typename TR::Mat;
+  const uint64_t N = P->N;
+  cudaStream_t s = P->stream;
+  V* psi = (V*)P->psi;
+  Mat* allm = (Mat*)P->mats;
+  const int phases = noisy ? depth + 1 : depth;
+  const std::vector<Pass> passes = plan_pool(P->n, TR::kTileBits, TR::kRowBits);
+  k_pool_compose<TR><<<grid_for((uint64_t)batch * phases * P->n, 1, 8), kThreads, 0, s>>>(circuit_of(P, depth, noisy),
+                                                                                        batch, phases, allm);
+  k_basis0_batch<V><<<grid_for(N * batch, 1, 16), kThreads, 0, s>>>(psi, N, batch);
+  int count = 2;
+  for (int l = 0; l < phases; ++l) {
+    for (const Pass& p : passes) {
+      const unsigned K = p.g.c + p.g.m;
+      const uint64_t tiles = N >> K;
+      const unsigned gx = (unsigned)std::min<uint64_t>(tiles, (uint64_t)std::max(1, 2432 / batch));
+      const unsigned cm = l < depth ? cnot_mask(p, P->n, l) : 0u;
+      const size_t smem = ((size_t)1 << K) * sizeof(typename TR::W);
+      k_pool_pass<TR><<<dim3(std::max(1u, gx), batch), kThreads, smem, s>>>(psi, N, p.g, p.q_lo, p.q_hi, cm, allm,
+                                                                            phases, P->n, l, P->flag);
+      ++count;
+    }
+  }
+  const dim3 gp(P->nblk, batch);
+  k_pool_probs<TR><<<gp, kThreads, 0, s>>>(psi, N, P->n, P->partials, P->part_stride, P->flag);
+  k_pool_finish<<<batch, 32, 0, s>>>(P->partials, P->part_stride, P->nblk, P->n, P->probs);
+  k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
+  *launches = count + 3;
+}
+
 template <class TR>
 cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
   using V = typename TR::V;
   const uint64_t N = P->N;
   cudaStream_t s = P->stream;
   V* psi = (V*)P->psi;
-  int launches = 0;
-  Circuit C{P->n, depth, P->U, noisy ? P->angles : nullptr, P->layer_base, n_noise_ops(P->n, depth)};
-  C.model = P->noise_model;
-  for (int k = 0; k < 3; ++k) C.sig[k] = P->sig[k];
-  const std::vector<Pass> passes = plan_pool(P->n, TR::kTileBits, TR::kRowBits);
   const int phases = noisy ? depth + 1 : depth;
   using Mat = typename TR::Mat;
   Mat* allm = (Mat*)P->mats;
-  k_pool_compose<TR><<<grid_for((uint64_t)batch * phases * P->n, 1, 8), kThreads, 0, s>>>(C, batch, phases, allm);
-  ++launches;
   // auto: the cluster-resident engine for complex64; complex128 runs faster in the tiled passes
   // (up to 4-CTA clusters: larger clusters keep fewer states on chip at once)
   const bool cluster = P->engine == 2 || (P->engine == 0 && P->dtype == IQS_C64 && pool_cluster_eligible(P->n, P->dtype) &&
                                           pool_cluster_logc(P->n, P->dtype) <= 2);
   if (cluster) {
     // the whole circuit of every trajectory in one launch, states resident in cluster shared memory
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) note_launches(launches);
+    k_pool_compose<TR><<<grid_for((uint64_t)batch * phases * P->n, 1, 8), kThreads, 0, s>>>(circuit_of(P, depth, noisy),
+                                                                                          batch, phases, allm);
+    cudaError_t e = launched(1);
     std::vector<ClusterJob> jobs(batch);
     for (int b = 0; b < batch; ++b)
       jobs[b] = ClusterJob{allm + (uint64_t)b * phases * P->n, psi + (uint64_t)b * N, P->probs + (uint64_t)b * P->n,
@@ -259,27 +301,35 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
     k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
     return launched(1);
   }
-  k_basis0_batch<V><<<grid_for(N * batch, 1, 16), kThreads, 0, s>>>(psi, N, batch);
-  ++launches;
-  for (int l = 0; l < phases; ++l) {
-    for (const Pass& p : passes) {
-      const unsigned K = p.g.c + p.g.m;
-      const uint64_t tiles = N >> K;
-      const unsigned gx = (unsigned)std::min<uint64_t>(tiles, (uint64_t)std::max(1, 2432 / batch));
-      const unsigned cm = l < depth ? cnot_mask(p, P->n, l) : 0u;
-      const size_t smem = ((size_t)1 << K) * sizeof(typename TR::W);
-      k_pool_pass<TR><<<dim3(std::max(1u, gx), batch), kThreads, smem, s>>>(psi, N, p.g, p.q_lo, p.q_hi, cm, allm,
-                                                                            phases, P->n, l, P->flag);
-      ++launches;
+  // tiled passes: about two launches per layer, replayed from a CUDA graph
+  // captured on the first run of each (batch, depth, noisy) shape; the inputs
+  // live in fixed device buffers, so a replay reads each call's unitaries and angles
+  const auto key = std::make_tuple(batch, depth, noisy ? 1 : 0);
+  auto it = P->graphs.find(key);
+  if (it == P->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {  // a stream that cannot be captured (the legacy default stream): launch directly
+      cudaGetLastError();
+      int launches = 0;
+      enqueue_tiled<TR>(P, batch, depth, noisy, &launches);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) note_launches(launches);
+      return e;
     }
+    int launches = 0;
+    enqueue_tiled<TR>(P, batch, depth, noisy, &launches);
+    const cudaError_t ee = cudaGetLastError();
+    e = cudaStreamEndCapture(s, &graph);
+    if (ee != cudaSuccess) e = ee;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    it = P->graphs.emplace(key, std::make_pair(exec, launches)).first;
   }
-  const dim3 gp(P->nblk, batch);
-  k_pool_probs<TR><<<gp, kThreads, 0, s>>>(psi, N, P->n, P->partials, P->part_stride, P->flag);
-  k_pool_finish<<<batch, 32, 0, s>>>(P->partials, P->part_stride, P->nblk, P->n, P->probs);
-  k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
-  launches += 3;
-  const cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) note_launches(launches);
+  const cudaError_t e = cudaGraphLaunch(it->second.first, s);
+  if (e == cudaSuccess) note_launches(it->second.second);
   return e;
 }
 
@@ -289,7 +339,13 @@ cudaError_t set_pool_attrs() {
                               (1 << TR::kTileBits) * (int)sizeof(typename TR::W));
 }
 
+void drop_graphs(iqs_pool* p) {
+  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second.first);
+  p->graphs.clear();
+}
+
 void free_pool(iqs_pool* p) {
+  drop_graphs(p);
   cudaFree(p->psi);
   cudaFree(p->U);
   cudaFree(p->angles);
@@ -376,6 +432,7 @@ int iqs_pool_noise_count(int n, int depth) { return iqs::n_noise_ops(n, depth); 
 iqs_status iqs_pool_set_noise_t1t2(iqs_pool* p, double T1, double T2, double gate_time) {
   using namespace iqs;
   if (p == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  drop_graphs(p);  // captured runs embed the noise law
   if (T1 <= 0.0) {  // back to explicit angle pairs
     p->noise_model = 0;
     return IQS_OK;

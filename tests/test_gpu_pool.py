@@ -61,6 +61,30 @@ def test_noisy_trajectories_match_oracle(gpu_lib, dtype, n, depth, batch, sigma)
     pool.close()
 
 
+@pytest.mark.parametrize("dtype", ["complex128", "complex64"])
+def test_replayed_tiled_runs_read_new_inputs(gpu_lib, dtype):
+    """Tiled-pass runs are captured as a CUDA graph per (batch, depth, noisy)
+    shape and replayed: repeated and interleaved shapes with fresh unitaries
+    and angles each match the oracle, and so does a run after the noise law
+    changes (which drops the captured graphs)."""
+    n, sigma = 13, 0.1
+    pool = gpu_lib.Pool(n, dtype, batch_max=3, depth_max=6)
+    pool.set_engine("passes")
+    tol = 1e-12 if dtype == "complex128" else c64_tol(6)
+    for i, (depth, batch) in enumerate([(4, 2), (6, 3), (4, 2), (6, 3), (4, 2)]):
+        g = W.rng(900 + i)
+        ops = W.random_circuit_layers(n, depth, seed=910 + i)
+        angles = g.normal(0.0, sigma, size=(batch, noise_count(n, depth), 2))
+        probs, _ = pool.run_brick(brick_unitaries(ops, n), angles)
+        for b in range(batch):
+            ref = oe.run_ops(n, oe.noisy_trajectory_ops(ops, angles[b]))
+            assert np.max(np.abs(pool.state(b).astype(np.complex128) - ref)) <= tol, (i, b)
+        if i == 2:
+            pool.set_noise_t1t2(500.0, 250.0, 1.0)
+            pool.set_noise_t1t2(0.0, 0.0, 0.0)  # back to angle pairs: the graphs were dropped
+    pool.close()
+
+
 def test_uneven_depth_circuits_share_a_workspace(gpu_lib):
     """Circuits of different depths run one after another in one pool."""
     n = 10
