@@ -11,14 +11,15 @@
 // double-float k >= 3, native k >= 4), the row loop stays rolled and the
 // coefficients are staged once per block in shared memory (all lanes read
 // the same address, so the reads broadcast).  complex64 computes in FP32
-// (k <= 5); complex128 in the double-float emulation (k <= 4) or, for small
-// states or on request, in native FP64.  One read and one write of the state
-// per gate.
+// (k <= 5); complex128 in the double-float emulation (k <= 4; for k >= 2 on
+// paired .f32x2 instructions, two groups per thread) or, for small states or
+// on request, in native FP64.  One read and one write of the state per gate.
 #include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
 #include "df64.cuh"
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace iqs {
@@ -382,58 +383,91 @@ __global__ void __launch_bounds__(kThreads, min_blocks<K + 2>()) k_kgate_c128_df
   if (bad) atomicOr(flag, 1u);
 }
 
-// The double-float dot product of dfx::dot with coefficients packed as
-// (h, l, h52, unused) float4 values in shared memory.
+// The double-float k-qubit gate on paired FP32 instructions.  Each thread owns
+// two amplitude groups (g and g + S, S = the grid's thread count) and runs
+// dfx::dot's operation sequence for both at once, one group per lane of the
+// .f32x2 instructions, in half the FP32 instructions.  The coefficients are
+// staged in shared memory duplicated into both lanes as (h, h), (h52, h52),
+// (l, l).  The error-free transformations need every product rounded on its
+// own before it is added: no rounded product feeds a packed add or subtract
+// directly (the negated product -fl(h x) is formed by flipping sign bits with
+// an integer XOR), so no multiply can be fused into the sums.  The first term
+// runs through the same steps from p = e = 0, which gives it exactly the
+// scalar first-term values (p = fl(h x), e = the product's residual).
+__device__ __forceinline__ f2::P neg_bits(f2::P a) {
+  f2::P d;
+  asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(d) : "l"(a));
+  return d;
+}
+
 template <int M>
-__device__ __forceinline__ void dot_smem(const float4* __restrict__ c, const float* xh, const float* xl, float& p,
-                                         float& e) {
-  float4 k = c[0];
-  p = k.x * xh[0];
-  e = fmaf(k.x, xh[0], -p);
-  e = fmaf(k.z, xl[0], e);
-  e = fmaf(k.y, xh[0], e);
+__device__ __forceinline__ void dot2(const ulonglong2* __restrict__ c, const f2::P* X, const f2::P* XL, f2::P& p,
+                                     f2::P& e) {
+  p = 0ull;
+  e = 0ull;
 #pragma unroll
-  for (int j = 1; j < M; ++j) {
-    k = c[j];
-    const float q = k.x * xh[j];
-    const float eq = fmaf(k.x, xh[j], -q);
-    float s, t;
-    dfx::two_sum(p, q, s, t);
+  for (int j = 0; j < M; ++j) {
+    const ulonglong2 k0 = c[2 * j];  // (h, h), (h52, h52)
+    const f2::P kl = reinterpret_cast<const f2::P*>(c)[4 * j + 2];  // (l, l)
+    const f2::P qn = neg_bits(f2::mul(k0.x, X[j]));  // -fl(h x)
+    const f2::P eq = f2::fma(k0.x, X[j], qn);         // h x - fl(h x), exact
+    // TwoSum(p, q) with q = -qn: s = p + q, t = (p - (s - bb)) + (q - bb)
+    const f2::P s = f2::sub(p, qn);
+    const f2::P bb = f2::sub(s, p);
+    const f2::P t = f2::sub(f2::sub(p, f2::sub(s, bb)), f2::add(qn, bb));
     p = s;
-    e += eq + t;
-    e = fmaf(k.z, xl[j], e);
-    e = fmaf(k.y, xh[j], e);
+    e = f2::add(e, f2::add(eq, t));
+    e = f2::fma(k0.y, XL[j], e);
+    e = f2::fma(kl, X[j], e);
   }
 }
 
 template <int K>
-__global__ void __launch_bounds__(kThreads, 1) k_kgate_c128_df_rows(double2* __restrict__ a, uint64_t n_groups,
-                                                                    Targets<K> T, UDF<K> U, unsigned* flag) {
+__global__ void __launch_bounds__(kThreads, K <= 3 ? 2 : 1) k_kgate_c128_df2(double2* __restrict__ a, uint64_t n_groups,
+                                                                Targets<K> T, UDF<K> U, unsigned* flag) {
   constexpr int D = 1 << K;
   constexpr int M = 2 * D;
-  __shared__ float4 sc[2 * D * M];
+  __shared__ ulonglong2 sc[2 * (2 * D * M)];
   for (int i = threadIdx.x; i < 2 * D * M; i += blockDim.x) {
     const dfx::Coef k = U.c[i];
-    sc[i] = make_float4(k.h, k.l, k.h52, 0.f);
+    sc[2 * i] = make_ulonglong2(f2::pack(k.h, k.h), f2::pack(k.h52, k.h52));
+    sc[2 * i + 1] = make_ulonglong2(f2::pack(k.l, k.l), 0ull);
   }
   __syncthreads();
   unsigned bad = 0;
-  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_groups; g += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t base = group_base<K>(g, T);
-    float xh[M], xl[M];
+  const uint64_t S = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g0 < n_groups; g0 += 2 * S) {
+    const bool two = g0 + S < n_groups;  // the last round may hold one group: lane 1 repeats it, unstored
+    const uint64_t b0 = group_base<K>(g0, T);
+    const uint64_t b1 = two ? group_base<K>(g0 + S, T) : b0;
+    f2::P X[M], XL[M];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      const double2 v = a[base + T.off[c]];
-      dfx::split(v.x, xh[2 * c], xl[2 * c], bad);
-      dfx::split(v.y, xh[2 * c + 1], xl[2 * c + 1], bad);
+      const double2 v0 = a[b0 + T.off[c]];
+      const double2 v1 = a[b1 + T.off[c]];
+      float h0, l0, h1, l1;
+      dfx::split(v0.x, h0, l0, bad);
+      dfx::split(v1.x, h1, l1, bad);
+      X[2 * c] = f2::pack(h0, h1);
+      XL[2 * c] = f2::pack(l0, l1);
+      dfx::split(v0.y, h0, l0, bad);
+      dfx::split(v1.y, h1, l1, bad);
+      X[2 * c + 1] = f2::pack(h0, h1);
+      XL[2 * c + 1] = f2::pack(l0, l1);
     }
-#pragma unroll 1
+#pragma unroll(K >= 3 ? 1 : D)
     for (int r = 0; r < D; ++r) {
-      float p, e;
-      dot_smem<M>(&sc[(2 * r) * M], xh, xl, p, e);
-      const double yr = dfx::join(p, e);
-      dot_smem<M>(&sc[(2 * r + 1) * M], xh, xl, p, e);
-      a[base + T.off[r]] = make_double2(yr, dfx::join(p, e));
+      f2::P p, e;
+      float p0, p1, e0, e1;
+      dot2<M>(&sc[2 * (2 * r) * M], X, XL, p, e);
+      f2::unpack(p, p0, p1);
+      f2::unpack(e, e0, e1);
+      const double re0 = dfx::join(p0, e0), re1 = dfx::join(p1, e1);
+      dot2<M>(&sc[2 * (2 * r + 1) * M], X, XL, p, e);
+      f2::unpack(p, p0, p1);
+      f2::unpack(e, e0, e1);
+      a[b0 + T.off[r]] = make_double2(re0, dfx::join(p0, e0));
+      if (two) a[b1 + T.off[r]] = make_double2(re1, dfx::join(p1, e1));
     }
   }
   if (bad) atomicOr(flag, 1u);
@@ -511,10 +545,12 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
           u.c[(2 * row + 1) * M + 2 * c] = dfx::make_coef(ui);       // im += Im(u) Re(x)
           u.c[(2 * row + 1) * M + 2 * c + 1] = dfx::make_coef(ur);   // im += Re(u) Im(x)
         }
-      if constexpr (K >= 3)
-        k_kgate_c128_df_rows<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
-      else
+      if constexpr (K >= 2) {
+        const unsigned grid2 = grid_for((n_groups + 1) / 2, 1, 8);
+        k_kgate_c128_df2<K><<<grid2, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
+      } else {
         k_kgate_c128_df<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
+      }
       return launched(1);
     }
   }
