@@ -111,6 +111,12 @@ def cpu_baseline(args):
                       f"{dt:.1f} s"}
 
 
+def sweep_workload(n: int) -> str:
+    N = 1 << n
+    return (f"single-state gate sweep, {n}-qubit complex128 ({N * 16 / 2**30:.0f} GiB): apply_1q(Haar U) on "
+            f"q=0..{n-1} + {N_CNOT} CNOT + all-qubit P(1) + Pauli expectation + norm")
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -124,10 +130,12 @@ def reference_arm(args):
     line = {"metric": METRIC, "value": round(v, 3), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"gate sweep through the FP64 CPU oracle, {n}-qubit complex128 sample of the "
-                                   f"30-qubit sweep", "qubits": n},
+            "config": {"workload": sweep_workload(args.qubits), "qubits": args.qubits,
+                       "sample": f"each step runs the sweep's gate mix through the FP64 CPU oracle on a {n}-qubit "
+                                 f"complex128 state (a bounded sample of the {args.qubits}-qubit workload); GB/s "
+                                 f"counts that sample's algorithmic bytes"},
             "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n}-qubit complex128 state, full sweep per step"},
+                             "sample": f"{n}-qubit complex128 state, full sweep per step, numpy FP64, one thread"},
             "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -773,9 +781,7 @@ def main(argv=None):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 storage, double-float arithmetic" if args.math != "native" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"single-state gate sweep, {n}-qubit complex128 "
-                                   f"({N * 16 / 2**30:.0f} GiB): apply_1q(Haar U) on q=0..{n-1} + {N_CNOT} CNOT "
-                                   f"+ all-qubit P(1) + Pauli expectation + norm",
+            "config": {"workload": sweep_workload(n),
                        "qubits": n, "math": args.math, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (state 16 GiB >> 129 MB)"},
             "roofline": {"kernel": kernel_key, "bound": "hbm", "achieved": round(achieved, 1),
