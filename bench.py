@@ -289,6 +289,19 @@ def sweep_c64(iqs, torch, dev, n: int, steps: int, warmup: int):
             "error_bound": "FP32 gate arithmetic: <= 8 * 2^-24 per gate on unit-norm states (tests/test_gpu_parity.py)"}
 
 
+def median_call_s(torch, fn, runs: int = 5) -> float:
+    """Median wall-clock seconds of ``runs`` calls of a synchronous API call
+    (each returns after its own stream has finished), after the caller's
+    warm-up, with the device idle before each call."""
+    ts = []
+    for _ in range(runs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return float(np.median(ts))
+
+
 def random_circuit_section(iqs, torch):
     """Config 1: the 12-qubit complex128 random circuit (20 layers of Haar
     one-qubit gates on every qubit plus the CNOT brick, 350 gates) from
@@ -313,31 +326,23 @@ def random_circuit_section(iqs, torch):
                 reg.apply_c1q(op[1], op[2], X)
         return reg.probabilities()
 
-    gates()
-    t0 = time.perf_counter()
+    p_gates = gates()
     reps = 20
-    for _ in range(reps):
-        p_gates = gates()
-    dt_gates = (time.perf_counter() - t0) / reps
+    dt_gates = median_call_s(torch, gates, reps)
     reg.close()
     U = brick_unitaries(ops, n)
     pool = iqs.Pool(n, "complex128", batch_max=1, depth_max=depth)
-    pool.run_brick(U)
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        p_pool, _ = pool.run_brick(U)
-    dt_pool = (time.perf_counter() - t0) / reps
+    p_pool, _ = pool.run_brick(U)
+    dt_pool = median_call_s(torch, lambda: pool.run_brick(U), reps)
     pool.set_engine("cluster")  # the whole circuit in one launch, the state resident on chip
-    pool.run_brick(U)
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        p_cl, _ = pool.run_brick(U)
-    dt_cl = (time.perf_counter() - t0) / reps
+    p_cl, _ = pool.run_brick(U)
+    dt_cl = median_call_s(torch, lambda: pool.run_brick(U), reps)
     pool.close()
     t0 = time.perf_counter()
     ref = oe.all_probabilities(oe.run_ops(n, ops))
     dt_cpu = time.perf_counter() - t0
     return {"workload": f"{n}-qubit complex128 random circuit, {depth} layers, {len(ops)} gates, |0> to P(1) of every qubit",
+            "timing": f"median of {reps} synchronous calls after a warm-up",
             "gate_by_gate_us": round(dt_gates * 1e6, 1), "pool_tiled_passes_us": round(dt_pool * 1e6, 1),
             "pool_cluster_one_launch_us": round(dt_cl * 1e6, 1),
             "cpu_oracle_us": round(dt_cpu * 1e6, 1),
@@ -354,7 +359,8 @@ def kq_measure_section(iqs, torch, dev):
     amplitudes per shot)."""
     import workloads as W
     out = {"workload": "apply_kq (Haar 2^k x 2^k) on the lowest and highest k qubits, "
-                       "10-qubit marginal, 2^20-shot sampling"}
+                       "10-qubit marginal, 2^20-shot sampling",
+           "timing": "median of 5 calls, each bracketed by CUDA events on the register's stream, after a warm-up"}
     g = W.rng(77)
     for n, dt, name, ks in ((30, torch.complex128, "c128_30q", (2, 3, 4)), (32, torch.complex64, "c64_32q", (2, 3, 4, 5))):
         N = 1 << n
@@ -369,16 +375,19 @@ def kq_measure_section(iqs, torch, dev):
         stream.synchronize()
         reg = iqs.Register.wrap(st, stream=stream)
 
-        def timed(fn, reps=3):
+        def timed(fn, reps=5):
+            # median of ``reps`` calls, each bracketed by CUDA events on the register's stream
             fn()
             torch.cuda.synchronize(dev)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            ts = []
             for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
                 fn()
-            b.record(stream)
-            b.synchronize()
-            return a.elapsed_time(b) / reps
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            return float(np.median(ts))
 
         rows = []
         for k in ks:
@@ -410,29 +419,33 @@ def qaoa_section(iqs, torch):
     large-adjoint configuration."""
     import workloads as W
     out = {"workload": "QAOA Max-Cut on random 3-regular graphs, p=4, 256 (gamma, beta) sets per graph; "
-                       "energy <C> + adjoint gradient", "rows": []}
+                       "energy <C> + adjoint gradient", "rows": [],
+           "timing": "median of 5 synchronous engine calls after a warm-up (plain complex128: median over 8 sets)"}
     p, B = 4, 256
     for n in (16, 20, 24):
         edges = W.random_3regular_graph(n, 1000 + n)
         gm, bt = W.qaoa_parameter_sets(p, B, 2000 + n)
         eng = iqs.QAOA(n, edges, "complex64", batch_max=B)
         tuned = eng.autotune(B, p)  # project autotuner picks the tile shape (untimed)
-        eng.run(gm, bt)  # capture the graph
-        reps = 2
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            E64, _, _ = eng.run(gm, bt)
-        dt = (time.perf_counter() - t0) / reps
+        E64, dg64, db64 = eng.run(gm, bt)  # capture the graph
+        dt = median_call_s(torch, lambda: eng.run(gm, bt))
         eng.close()
         plain = iqs.QAOA(n, edges, "complex128", batch_max=1)
         k = 8
         plain.run(gm[:1], bt[:1])
         E128 = np.empty(k)
-        t0 = time.perf_counter()
+        G128 = np.empty((k, 2 * p))
+        tp = []
         for i in range(k):
-            E128[i] = plain.run(gm[i:i + 1], bt[i:i + 1])[0][0]
-        dtp = (time.perf_counter() - t0) / k
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e1, g1, b1 = plain.run(gm[i:i + 1], bt[i:i + 1])
+            tp.append(time.perf_counter() - t0)
+            E128[i] = e1[0]
+            G128[i] = np.concatenate([g1[0], b1[0]])
+        dtp = float(np.median(tp))
         plain.close()
+        g_err = float(np.max(np.abs(np.concatenate([dg64[:k], db64[:k]], axis=1) - G128)))
         torch.cuda.empty_cache()
         model = (12 * p + 2) * 8 * (1 << n) * B
         out["rows"].append({"n": n, "p": p, "batch": B, "tile_choice": {k: tuned[k] for k in ("row_bits", "grid_mult")},
@@ -440,20 +453,39 @@ def qaoa_section(iqs, torch):
                             "plain_c128_evals_per_s": round(1 / dtp, 1),
                             "ratio": round((B / dt) * dtp, 2),
                             "energy_err_c64_vs_c128_max": float(np.max(np.abs(E64[:k] - E128))),
+                            "grad_err_c64_vs_c128_max": g_err,
                             "batched_model_GBs": round(model / dt / 1e9, 1)})
     # large adjoint: 28 qubits, p = 4, one parameter set, complex64 with FP64 reductions
     n = 28
     edges = W.random_3regular_graph(n, 28)
     gm, bt = W.qaoa_parameter_sets(4, 1, 29)
     eng = iqs.QAOA(n, edges, "complex64", batch_max=1, renorm_every=2)
-    eng.run(gm, bt)
-    t0 = time.perf_counter()
     E, dg, db = eng.run(gm, bt)
-    dt = time.perf_counter() - t0
+    dt = median_call_s(torch, lambda: eng.run(gm, bt))
     eng.close()
     torch.cuda.empty_cache()
+    # errors: the energy against the complex128 engine, the gradient against
+    # central differences (h = 1e-4) of complex128 energies
+    ref = iqs.QAOA(n, edges, "complex128", batch_max=1)
+    E128 = ref.run(gm, bt, grad=False)[0]
+    h = 1e-4
+    fd = np.empty(8)
+    for j in range(8):
+        gp, bp, gmn, bmn = gm.copy(), bt.copy(), gm.copy(), bt.copy()
+        if j < 4:
+            gp[0, j] += h
+            gmn[0, j] -= h
+        else:
+            bp[0, j - 4] += h
+            bmn[0, j - 4] -= h
+        fd[j] = (ref.run(gp, bp, grad=False)[0] - ref.run(gmn, bmn, grad=False)[0]) / (2 * h)
+    ref.close()
+    torch.cuda.empty_cache()
+    adj_err = {"energy_err_vs_c128": float(abs(E[0] - E128)),
+               "grad_err_vs_central_diff_c128_max": float(np.max(np.abs(np.concatenate([dg[0], db[0]]) - fd))),
+               "central_diff": "h = 1e-4 on complex128 energies (truncation error of order h^2)"}
     out["adjoint_28q"] = {"n": 28, "p": 4, "dtype": "complex64 storage, FP64-equivalent reductions",
-                          "ms_per_energy_and_gradient": round(dt * 1e3, 2), "energy": float(E[0]),
+                          "ms_per_energy_and_gradient": round(dt * 1e3, 2), "energy": float(E[0]), **adj_err,
                           "model_GBs": round((12 * 4 + 2) * 8 * 2 ** 28 / dt / 1e9, 1)}
     best = out["rows"][1]
     out["headline"] = {"n": best["n"], "p": best["p"], "batched_c64_evals_per_s": best["batched_c64_evals_per_s"],
@@ -514,15 +546,13 @@ def ensemble_section(iqs, torch):
     Us = [brick_unitaries(c["ops"], n) for c in ens]
     out = {"workload": f"{circuits} circuits x {traj} trajectories, {n} qubits, depth {min(depths)}..{max(depths)} "
                        f"(uniform 40..120), noise RX.RZ N(0, 0.02^2) after every gate",
-           "depths": depths}
+           "depths": depths, "timing": "median of 5 runs of the whole ensemble (synchronous calls) after a warm-up"}
     means = {}
     for dtype in ("complex64", "complex128"):
         pool = iqs.Pool(n, dtype, batch_max=traj, depth_max=max(depths))
         pool.run_brick(Us[0][:2], ens[0]["angles"][:, :iqs.pool.noise_count(n, 2)])  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
         m = [pool.run_brick(Us[i], ens[i]["angles"])[1] for i in range(circuits)]
-        dt = time.perf_counter() - t0
+        dt = median_call_s(torch, lambda: [pool.run_brick(Us[i], ens[i]["angles"]) for i in range(circuits)])
         pool.close()
         torch.cuda.empty_cache()
         means[dtype] = np.array(m)
@@ -534,11 +564,8 @@ def ensemble_section(iqs, torch):
     for dtype in ("complex64", "complex128"):
         pm = iqs.PoolMany(dtype)
         circs = [(Us[i], ens[i]["angles"]) for i in range(circuits)]
-        pm.run(circs)  # warm-up (grows the workspace to its full size)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = pm.run(circs)
-        dt = time.perf_counter() - t0
+        res = pm.run(circs)  # warm-up (grows the workspace to its full size)
+        dt = median_call_s(torch, lambda: pm.run(circs))
         pm.close()
         torch.cuda.empty_cache()
         m = np.array([r[1] for r in res])
@@ -551,11 +578,7 @@ def ensemble_section(iqs, torch):
         pool.set_noise_t1t2(500.0, 250.0, 1.0)
         draws = [W.noise_draws(traj, iqs.pool.noise_count(n, c["depth"]), 5000 + i) for i, c in enumerate(ens)]
         pool.run_brick(Us[0][:2], draws[0][:, :iqs.pool.noise_count(n, 2)])  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(circuits):
-            pool.run_brick(Us[i], draws[i])
-        dt = time.perf_counter() - t0
+        dt = median_call_s(torch, lambda: [pool.run_brick(Us[i], draws[i]) for i in range(circuits)])
         pool.close()
         torch.cuda.empty_cache()
         out[dtype]["t1t2"] = {"trajectories_per_s": round(circuits * traj / dt, 1), "seconds": round(dt, 3),
