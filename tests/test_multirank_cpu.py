@@ -59,5 +59,9 @@ def test_reference_arm_prints_on_rank0_only(rank):
         d = json.loads(lines[-1])
         assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["n_gpus"] == 2
         assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+        import bench
+        # the reference arm reports the GPU arm's workload; the bounded sample is stated beside it
+        assert d["config"]["workload"] == bench.sweep_workload(30) and "8-qubit" in d["config"]["sample"]
+        assert d["metric"] == bench.METRIC and d["higher_is_better"] is True
     else:
         assert lines == []
