@@ -25,7 +25,7 @@ def lib():
     return _lib
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_register_calls():
     names = declared_functions()
     for required in ("iqs_create", "iqs_destroy", "iqs_apply_1q", "iqs_apply_c1q", "iqs_apply_zz_phase",
                      "iqs_probability", "iqs_expectation"):
