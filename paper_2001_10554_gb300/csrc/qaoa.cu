@@ -30,6 +30,7 @@
 #include <thread>
 #include <new>
 #include <tuple>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -226,6 +227,47 @@ __global__ void __launch_bounds__(kThreads) k_mixer(typename TR::V* __restrict__
 // is a high pass whose gate bits start at s.  Since swz() is linear over
 // GF(2), the shared-memory index of (base | j << POS) is swz(base) ^ swz(j << POS),
 // one XOR with a compile-time constant per element.
+// The gates of one register round on a register block of 2^GB amplitudes
+// (element j differs from element 0 in the round's bits by j), with the
+// adjoint pass's gradient terms: complex64 sums a round's terms in FP32 before
+// the double-float accumulator, complex128 adds every term to it.
+template <class TR, bool ADJ, int GB>
+__device__ __forceinline__ void round_in_regs(typename TR::W* a, typename TR::W* y, const typename TR::RX& k,
+                                              dfx::Acc& acc) {
+  constexpr int RB = 1 << GB;
+  float rsum = 0.f;
+#pragma unroll
+  for (int bit = 0; bit < GB; ++bit) {
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      if (!(j & (1 << bit))) {
+        const int j1 = j | (1 << bit);
+        if (ADJ) {
+          if constexpr (TR::kBlockSum) {
+            rsum = qops::im_conj_mul_fma(y[j], a[j1], rsum);
+            rsum = qops::im_conj_mul_fma(y[j1], a[j], rsum);
+          } else {
+            float p, e;
+            qops::im_conj_mul(y[j], a[j1], p, e);
+            acc.add(p, e);
+            qops::im_conj_mul(y[j1], a[j], p, e);
+            acc.add(p, e);
+          }
+          TR::rx(y[j], y[j1], k);
+        }
+        TR::rx(a[j], a[j1], k);
+      }
+    }
+  }
+  if (ADJ && TR::kBlockSum) acc.add(rsum, 0.f);
+}
+
+// First element of register block sb in a round whose gate bits start at POS.
+template <int POS, int GB>
+__device__ __forceinline__ unsigned block_base(unsigned sb) {
+  return ((sb >> POS) << (POS + GB)) | (sb & ((1u << POS) - 1u));
+}
+
 template <class TR, bool ADJ, int C, int POS, int GB>
 __device__ __forceinline__ void mixer_round(typename TR::W* sp, typename TR::W* sl, const typename TR::RX& k,
                                             float& rsum_out, dfx::Acc& acc) {
@@ -234,8 +276,7 @@ __device__ __forceinline__ void mixer_round(typename TR::W* sp, typename TR::W* 
   constexpr unsigned NSUB = 1u << (K - GB);
   constexpr int RB = 1 << GB;
   for (unsigned sb = threadIdx.x; sb < NSUB; sb += blockDim.x) {
-    const unsigned base = ((sb >> POS) << (POS + GB)) | (sb & ((1u << POS) - 1u));
-    const unsigned sbase = swz<TR>(base);
+    const unsigned sbase = swz<TR>(block_base<POS, GB>(sb));
     W a[RB];
     W y[ADJ ? RB : 1];
 #pragma unroll
@@ -244,31 +285,7 @@ __device__ __forceinline__ void mixer_round(typename TR::W* sp, typename TR::W* 
       a[j] = sp[idx];
       if (ADJ) y[j] = sl[idx];
     }
-    float rsum = 0.f;
-#pragma unroll
-    for (int bit = 0; bit < GB; ++bit) {
-#pragma unroll
-      for (int j = 0; j < RB; ++j) {
-        if (!(j & (1 << bit))) {
-          const int j1 = j | (1 << bit);
-          if (ADJ) {
-            if constexpr (TR::kBlockSum) {
-              rsum = qops::im_conj_mul_fma(y[j], a[j1], rsum);
-              rsum = qops::im_conj_mul_fma(y[j1], a[j], rsum);
-            } else {
-              float p, e;
-              qops::im_conj_mul(y[j], a[j1], p, e);
-              acc.add(p, e);
-              qops::im_conj_mul(y[j1], a[j], p, e);
-              acc.add(p, e);
-            }
-            TR::rx(y[j], y[j1], k);
-          }
-          TR::rx(a[j], a[j1], k);
-        }
-      }
-    }
-    if (ADJ && TR::kBlockSum) acc.add(rsum, 0.f);
+    round_in_regs<TR, ADJ, GB>(a, y, k, acc);
 #pragma unroll
     for (int j = 0; j < RB; ++j) {
       const unsigned idx = sbase ^ swz<TR>((unsigned)j << POS);
@@ -279,17 +296,34 @@ __device__ __forceinline__ void mixer_round(typename TR::W* sp, typename TR::W* 
   (void)rsum_out;
 }
 
-template <class TR, bool ADJ, int C, int POS>
-__device__ __forceinline__ void mixer_rounds(typename TR::W* sp, typename TR::W* sl, const typename TR::RX& k,
-                                             dfx::Acc& acc) {
-  constexpr int K = TR::kTileBits;
-  if constexpr (POS < K) {
-    constexpr int GB = (K - POS) < TR::kRegBits ? (K - POS) : TR::kRegBits;
+// Register rounds in shared memory for the gate bits [POS, END), each followed
+// by a block barrier.
+template <class TR, bool ADJ, int C, int POS, int END>
+__device__ __forceinline__ void mixer_rounds_to(typename TR::W* sp, typename TR::W* sl, const typename TR::RX& k,
+                                                dfx::Acc& acc) {
+  if constexpr (POS < END) {
+    constexpr int GB = (TR::kTileBits - POS) < TR::kRegBits ? (TR::kTileBits - POS) : TR::kRegBits;
     float dummy = 0.f;
     mixer_round<TR, ADJ, C, POS, GB>(sp, sl, k, dummy, acc);
     __syncthreads();
-    mixer_rounds<TR, ADJ, C, POS + GB>(sp, sl, k, acc);
+    mixer_rounds_to<TR, ADJ, C, POS + GB, END>(sp, sl, k, acc);
   }
+}
+
+template <class TR, bool ADJ, int C, int POS>
+__device__ __forceinline__ void mixer_rounds(typename TR::W* sp, typename TR::W* sl, const typename TR::RX& k,
+                                             dfx::Acc& acc) {
+  mixer_rounds_to<TR, ADJ, C, POS, TR::kTileBits>(sp, sl, k, acc);
+}
+
+// Global index of tile element l: C = 0 tiles are 2^K contiguous amplitudes,
+// C > 0 tiles are rows of 2^C contiguous amplitudes, 2^s apart.
+template <int C>
+__device__ __forceinline__ uint64_t fast_x(uint64_t tbase, unsigned l, int s) {
+  if constexpr (C == 0)
+    return tbase + l;
+  else
+    return tbase + ((uint64_t)(l >> C) << s) + (l & ((1u << C) - 1u));
 }
 
 // Renormalisation fused into the adjoint passes (complex64 only).  With
@@ -305,13 +339,10 @@ struct RenormFuse {
 };
 constexpr int kRnCol = 2432;
 
-// PH = 1 (forward, low pass): the layer's cost phase T_b[C(x)] is applied to
-// each amplitude as the tile is loaded.  PH = 2 (adjoint, last pass): after the
-// mixer uncompute, each amplitude contributes C(x) Im(conj(lambda) phi) to the
-// phase gradient (partials_g) and both vectors are multiplied by
-// conj(T_b[C(x)]) as they are stored.  Either way one full pass per layer is saved.
+// The pass with every register round in shared memory, a staged load before
+// and a staged store after (used for the fused-phase adjoint pass, PH = 2).
 template <class TR, bool ADJ, int C, int PH>
-__device__ __forceinline__ void mixer_fast_body(typename TR::V* __restrict__ phi,
+__device__ __forceinline__ void mixer_fast_body_staged(typename TR::V* __restrict__ phi,
                                                          typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
                                                          const typename TR::RX* __restrict__ rx,
                                                          double* __restrict__ partials, int part_stride, unsigned* flag,
@@ -467,6 +498,186 @@ __device__ __forceinline__ void mixer_fast_body(typename TR::V* __restrict__ phi
   }
 }
 
+
+// PH = 1 (forward, low pass): the layer's cost phase T_b[C(x)] is applied to
+// each amplitude as the tile is loaded.  PH = 2 (adjoint, last pass): after the
+// mixer uncompute, each amplitude contributes C(x) Im(conj(lambda) phi) to the
+// phase gradient (partials_g) and both vectors are multiplied by
+// conj(T_b[C(x)]) as they are stored.  Either way one full pass per layer is saved.
+template <class TR, bool ADJ, int C, int PH>
+__device__ __forceinline__ void mixer_fast_body(typename TR::V* __restrict__ phi,
+                                                         typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
+                                                         const typename TR::RX* __restrict__ rx,
+                                                         double* __restrict__ partials, int part_stride, unsigned* flag,
+                                                         const uint8_t* __restrict__ cut,
+                                                         const typename TR::PH* __restrict__ tables, int tsize,
+                                                         double* __restrict__ partials_g, int per_graph,
+                                                         const RenormFuse rn) {
+  using W = typename TR::W;
+  using PHT = typename TR::PH;
+  constexpr bool kRn = ADJ && TR::kBlockSum;  // fused renormalisation: complex64 adjoint passes
+  __shared__ PHT st[PH ? kEdgeChunk + 1 : 1];
+  __shared__ float rn_f[2];
+  bool scale_in = false;
+  float f_phi = 1.f, f_lam = 1.f;
+  if constexpr (kRn) {
+    if (rn.norms) {
+      if (threadIdx.x == 0) {
+        const unsigned b = blockIdx.y;
+        const double np = rn.norms[b], tl = rn.norms[rn.stride + b];
+        const double tp = rn.norms[2 * rn.stride + b], nl = rn.norms[3 * rn.stride + b];
+        rn_f[0] = (float)(np > 0.0 ? sqrt(tp / np) : 1.0);
+        rn_f[1] = (float)(nl > 0.0 ? sqrt(tl / nl) : 1.0);
+      }
+      __syncthreads();
+      scale_in = true;
+      f_phi = rn_f[0];
+      f_lam = rn_f[1];
+    }
+  }
+  if (PH) {
+    cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
+    for (int i = threadIdx.x; i < tsize; i += blockDim.x) {
+      const PHT tt = tables[(uint64_t)blockIdx.y * tsize + i];
+      st[i] = PH == 2 ? TR::conj(tt) : tt;
+    }
+    __syncthreads();
+  }
+  constexpr int K = TR::kTileBits;
+  constexpr int M = K - C;
+  constexpr unsigned T = 1u << K;
+  constexpr unsigned PER = T / kThreads;  // elements per thread in a staged load or store
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* sp = reinterpret_cast<W*>(smem_raw);
+  W* sl = sp + T;
+  const unsigned b = blockIdx.y;
+  typename TR::V* P = phi + (uint64_t)b * N;
+  typename TR::V* L = ADJ ? lam + (uint64_t)b * N : nullptr;
+  const typename TR::RX k = ADJ ? TR::rx_inv(rx[b]) : rx[b];
+  const uint64_t tiles = N >> K;
+  const unsigned tid = threadIdx.x;
+  const int s = C == 0 ? 0 : s_bits;
+  const int mid = s - C;
+  // staged element l = tid + kThreads * i sits at fast_x(l); for C <= 8 that is
+  // tbase + off0 + i * step (kThreads = 2^8 carries no bit into the row)
+  const uint64_t off0 = C == 0 ? tid : ((uint64_t)(tid >> C) << s) | (tid & ((1u << C) - 1u));
+  const uint64_t step = C == 0 ? kThreads : ((uint64_t)(kThreads >> (C <= 8 ? C : 8)) << s);
+  // Register rounds of the pass: NR rounds of up to kRegBits gate bits.  The
+  // last round, from bit POSL, writes its results straight to HBM, and high
+  // passes (C > 0) also load their first round straight from HBM (a warp's
+  // register blocks cover whole 2^C-amplitude rows, so the loads stay
+  // coalesced); the low pass stages its tile through coalesced loads first.
+  // That halves the shared-memory sweeps of a tile: the passes ran 10-13%
+  // faster than with every round in shared memory.  The fused-phase adjoint
+  // pass (PH = 2) runs mixer_fast_body_staged instead: with its epilogue in
+  // the last round it ran up to 45% slower.
+  static_assert(PH != 2, "fused-phase adjoint passes use mixer_fast_body_staged");
+  constexpr int R = TR::kRegBits;
+  constexpr int NR = (M + R - 1) / R;
+  constexpr int POSL = C + R * (NR - 1);
+  constexpr int GBL = K - POSL;
+  constexpr int GB0 = M < R ? M : R;
+  constexpr bool kDirect = C > 0;
+  unsigned bad = 0;
+  dfx::Acc acc;
+  // one register block of 2^G amplitudes (gate bits from POS) to HBM
+  auto store_block = [&](const W* a, const W* y, unsigned base, uint64_t tbase, auto pos_c, auto gb_c) {
+    constexpr int POS = decltype(pos_c)::value;
+    constexpr int G = decltype(gb_c)::value;
+#pragma unroll
+    for (int j = 0; j < (1 << G); ++j) {
+      const uint64_t x = fast_x<C>(tbase, base | ((unsigned)j << POS), s);
+      P[x] = TR::store(a[j]);
+      if (ADJ) L[x] = TR::store(y[j]);
+    }
+  };
+  // load one amplitude of each vector from HBM, with the fused phase (PH = 1)
+  // or renormalisation factors applied
+  auto load_amp = [&](uint64_t x, W& av, W& yv) {
+    if (PH == 1) {
+      av = TR::mul(st[cut[x]], TR::load(P[x], bad));
+    } else {
+      av = TR::load(P[x], bad);
+      if constexpr (kRn) {
+        if (scale_in) av = qops::scale_int(av, f_phi);
+      }
+    }
+    if (ADJ) {
+      yv = TR::load(L[x], bad);
+      if constexpr (kRn) {
+        if (scale_in) yv = qops::scale_int(yv, f_lam);
+      }
+    }
+  };
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
+    if constexpr (!kDirect) {
+      // staged load: element l = tid + kThreads * i, coalesced across the warp
+#pragma unroll
+      for (unsigned i = 0; i < PER; ++i) {
+        const unsigned l = tid + kThreads * i;
+        const unsigned idx = swz<TR>(l);
+        W av, yv;
+        load_amp(C <= 8 ? tbase + off0 + step * i : fast_x<C>(tbase, l, s), av, yv);
+        sp[idx] = av;
+        if (ADJ) sl[idx] = yv;
+      }
+      __syncthreads();
+      mixer_rounds_to<TR, ADJ, C, C, POSL>(sp, sl, k, acc);
+    } else {
+      constexpr unsigned NSUB0 = 1u << (K - GB0);
+      for (unsigned sb = tid; sb < NSUB0; sb += kThreads) {
+        const unsigned base = block_base<C, GB0>(sb);
+        W a[1 << GB0];
+        W y[ADJ ? (1 << GB0) : 1];
+#pragma unroll
+        for (int j = 0; j < (1 << GB0); ++j) {
+          W yv;
+          load_amp(fast_x<C>(tbase, base | ((unsigned)j << C), s), a[j], yv);
+          if (ADJ) y[ADJ ? j : 0] = yv;
+        }
+        round_in_regs<TR, ADJ, GB0>(a, y, k, acc);
+        if constexpr (NR == 1) {
+          store_block(a, y, base, tbase, std::integral_constant<int, C>(), std::integral_constant<int, GB0>());
+        } else {
+          const unsigned sbase = swz<TR>(base);
+#pragma unroll
+          for (int j = 0; j < (1 << GB0); ++j) {
+            const unsigned idx = sbase ^ swz<TR>((unsigned)j << C);
+            sp[idx] = a[j];
+            if (ADJ) sl[idx] = y[ADJ ? j : 0];
+          }
+        }
+      }
+      if constexpr (NR > 1) {
+        __syncthreads();
+        mixer_rounds_to<TR, ADJ, C, C + GB0, POSL>(sp, sl, k, acc);
+      }
+    }
+    if constexpr (!kDirect || NR > 1) {
+      // last round: shared memory -> registers -> HBM
+      constexpr unsigned NSUBL = 1u << (K - GBL);
+      for (unsigned sb = tid; sb < NSUBL; sb += kThreads) {
+        const unsigned base = block_base<POSL, GBL>(sb);
+        const unsigned sbase = swz<TR>(base);
+        W a[1 << GBL];
+        W y[ADJ ? (1 << GBL) : 1];
+#pragma unroll
+        for (int j = 0; j < (1 << GBL); ++j) {
+          const unsigned idx = sbase ^ swz<TR>((unsigned)j << POSL);
+          a[j] = sp[idx];
+          if (ADJ) y[ADJ ? j : 0] = sl[idx];
+        }
+        round_in_regs<TR, ADJ, GBL>(a, y, k, acc);
+        store_block(a, y, base, tbase, std::integral_constant<int, POSL>(), std::integral_constant<int, GBL>());
+      }
+      __syncthreads();  // the next tile reuses shared memory
+    }
+  }
+  if (bad) atomicOr(flag, 1u);
+  if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+}
+
 // The shape-specialised pass kernels.  The adjoint ones are held to 128
 // registers (two 256-thread blocks per SM); the forward ones are left to the
 // compiler's default, which keeps them near 80-100.
@@ -483,7 +694,10 @@ __global__ void __launch_bounds__(kThreads) k_mixer_fast_fwd(IQS_MIXER_FAST_PARA
 }
 template <class TR, int C, int PH>
 __global__ void __launch_bounds__(kThreads, 2) k_mixer_fast_adj(IQS_MIXER_FAST_PARAMS) {
-  mixer_fast_body<TR, true, C, PH>(IQS_MIXER_FAST_ARGS);
+  if constexpr (PH == 2)
+    mixer_fast_body_staged<TR, true, C, PH>(IQS_MIXER_FAST_ARGS);
+  else
+    mixer_fast_body<TR, true, C, PH>(IQS_MIXER_FAST_ARGS);
 }
 #undef IQS_MIXER_FAST_PARAMS
 #undef IQS_MIXER_FAST_ARGS

@@ -234,7 +234,13 @@ def test_autotuner_keeps_results_and_persists_choice(gpu_lib, tmp_path):
                                      ("complex128", 11), ("complex128", 13), ("complex128", 16)])
 def test_qaoa_tma_staged_passes_match(gpu_lib, dtype, n):
     """TMA-staged mixer tiles (forward only, forward + adjoint) give the same
-    energies and gradients as the register-loaded tiles, and match the oracle."""
+    energies and gradients as the register-loaded tiles, and match the oracle.
+    Mode 1 changes only the forward kernels, and every result agrees to
+    rounding. Mode 2 runs the adjoint on the TMA kernel body: the same
+    operations, but in another kernel, where the compiler may fuse a complex
+    product differently (one FP32 rounding in a stored state). So complex64
+    gradients in mode 2 agree to complex64 rounding, below 1e-6 absolute.
+    Energies and every complex128 result agree to rounding."""
     p, B = 3, 3
     edges = W.random_3regular_graph(n if n % 2 == 0 else n - 1, 500 + n)
     gm, bt = W.qaoa_parameter_sets(p, B, 600 + n)
@@ -245,9 +251,11 @@ def test_qaoa_tma_staged_passes_match(gpu_lib, dtype, n):
         eng.set_tma(mode)
         assert eng.tuning()["tma_available"] and eng.tuning()["tma_mode"] == mode
         E, dg, db = eng.run(gm, bt)
+        loose = dtype == "complex64" and mode == 2
+        rtol_g, atol_g = (2e-6, 1e-6) if loose else (1e-9, 1e-11)
         np.testing.assert_allclose(E, E0, rtol=1e-12, atol=1e-13)
-        np.testing.assert_allclose(dg, dg0, rtol=1e-9, atol=1e-11)
-        np.testing.assert_allclose(db, db0, rtol=1e-9, atol=1e-11)
+        np.testing.assert_allclose(dg, dg0, rtol=rtol_g, atol=atol_g)
+        np.testing.assert_allclose(db, db0, rtol=rtol_g, atol=atol_g)
     if n <= 16:
         Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
         tol_e, tol_g = (1e-11, 1e-9) if dtype == "complex128" else (2e-6, 1e-4)
