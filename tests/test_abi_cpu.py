@@ -32,6 +32,27 @@ def test_header_declares_the_core_register_calls():
         assert required in names
 
 
+def test_every_declaration_is_documented():
+    """Each declared call sits right under a comment (its own, or one shared
+    by a short group of related calls) stating what it computes."""
+    lines = open(HEADER).read().splitlines()
+    decl = re.compile(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(iqs_[a-z0-9_]+)\s*\(")
+    last_comment_end, in_comment, seen = -100, False, 0
+    for i, ln in enumerate(lines):
+        if "/*" in ln:
+            in_comment = True
+        if "*/" in ln:
+            in_comment, last_comment_end = False, i
+            continue
+        if in_comment:
+            continue
+        m = decl.match(ln)
+        if m:
+            seen += 1
+            assert i - last_comment_end <= 6, f"{m.group(1)} (line {i + 1}) has no comment above it"
+    assert seen == len(declared_functions())
+
+
 def test_library_exports_every_declared_symbol(lib):
     names = declared_functions()
     assert len(names) >= 20
