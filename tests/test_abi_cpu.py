@@ -86,3 +86,19 @@ def test_mat8_is_row_major_re_im():
     from paper_2001_10554_gb300.register import mat8
     U = np.array([[1 + 2j, 3 + 4j], [5 + 6j, 7 + 8j]])
     assert list(mat8(U)) == [1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0]
+
+
+@pytest.mark.parametrize("n,depth", [(2, 1), (5, 4), (13, 6), (16, 101)])
+def test_pool_noise_count_and_brick_layout_without_gpu(lib, n, depth):
+    """The host-side pool helpers: the noise-rotation count per trajectory
+    (one per one-qubit gate, two per CNOT of the brick) and the (depth, n)
+    unitary layout built from a layered op list."""
+    import workloads as W
+    from paper_2001_10554_gb300.pool import brick_unitaries, noise_count
+    ops = W.random_circuit_layers(n, depth, seed=n + depth)
+    assert noise_count(n, depth) == sum(1 if op[0] == "1q" else 2 for op in ops)
+    U = brick_unitaries(ops, n)
+    assert U.shape == (depth, n, 2, 2)
+    one_q = [op for op in ops if op[0] == "1q"]
+    for k, op in enumerate(one_q):
+        assert np.array_equal(U[k // n, op[1]], op[2])
