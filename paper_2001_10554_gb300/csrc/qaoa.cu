@@ -340,7 +340,11 @@ struct RenormFuse {
 constexpr int kRnCol = 2432;
 
 // The pass with every register round in shared memory, a staged load before
-// and a staged store after (used for the fused-phase adjoint pass, PH = 2).
+// and a staged store after; used for the fused-phase adjoint pass (PH = 2).
+// PH = 2: after the mixer uncompute, each amplitude contributes
+// C(x) Im(conj(lambda) phi) to the phase gradient (partials_g), and both
+// vectors are multiplied by conj(T_b[C(x)]) as they are stored, which saves
+// a full pass per layer.
 template <class TR, bool ADJ, int C, int PH>
 __device__ __forceinline__ void mixer_fast_body_staged(typename TR::V* __restrict__ phi,
                                                          typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
@@ -499,11 +503,10 @@ __device__ __forceinline__ void mixer_fast_body_staged(typename TR::V* __restric
 }
 
 
-// PH = 1 (forward, low pass): the layer's cost phase T_b[C(x)] is applied to
-// each amplitude as the tile is loaded.  PH = 2 (adjoint, last pass): after the
-// mixer uncompute, each amplitude contributes C(x) Im(conj(lambda) phi) to the
-// phase gradient (partials_g) and both vectors are multiplied by
-// conj(T_b[C(x)]) as they are stored.  Either way one full pass per layer is saved.
+// A mixer pass of a full tile shape, forward or adjoint.  PH = 1 (forward, low
+// pass): the layer's cost phase T_b[C(x)] is applied to each amplitude as the
+// tile is loaded, which saves a full pass per layer.  (PH = 2, the adjoint
+// pass with the fused phase epilogue, is mixer_fast_body_staged.)
 template <class TR, bool ADJ, int C, int PH>
 __device__ __forceinline__ void mixer_fast_body(typename TR::V* __restrict__ phi,
                                                          typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
