@@ -34,6 +34,9 @@ worked by hand, or the paper's own worked listing.  Two noise models are
 pinned statistically and by quadrature: ``ensemble.noisy_trajectory_ops``
 (X then Z rotations with Gaussian angles, against a density-matrix channel
 written in the test) and ``noise.t1t2_trajectory_ops`` (against the decay
-laws exp(-t/T1), exp(-t/T2) that T1 and T2 name).
+laws exp(-t/T1), exp(-t/T2) that T1 and T2 name, and to a density-matrix
+circuit with that channel after every touched qubit).  ``renormalise``,
+the rotation matrices, the placement and scaling of every noise draw and the
+ensemble mean have hand-worked and matrix-exponential pins of their own.
 """
 from . import statevector, qaoa, ensemble, noise, pso  # noqa: F401

@@ -598,3 +598,175 @@ def test_t1t2_trajectories_converge_to_the_decay_of_coherence():
     for vals, target in ((xs, np.exp(-k * t / T2)), (zs, np.exp(-k * t / T1))):
         m, se = np.mean(vals), np.std(vals) / np.sqrt(traj)
         assert abs(m - target) < 5 * se
+
+
+# ---------------------------------------------------------------- renormalisation, rotations, noise placement
+def _expm_rotation(sigma_literal, theta):
+    """exp(-i theta sigma / 2) by scipy's matrix exponential of a Pauli
+    matrix typed out here (not the oracle's table)."""
+    return scipy.linalg.expm(-0.5j * theta * np.asarray(sigma_literal, dtype=np.complex128))
+
+
+_X_LIT = [[0, 1], [1, 0]]
+_Y_LIT = [[0, -1j], [1j, 0]]
+_Z_LIT = [[1, 0], [0, -1]]
+
+
+def test_renormalise_divides_by_the_norm_not_its_square():
+    """A hand example and scaled random states: psi / ||psi||, with ||.||
+    from numpy's 2-norm.  Dividing by norm2 (the square) fails every case
+    whose norm is not 1."""
+    np.testing.assert_allclose(sv.renormalise(np.array([3.0, 4.0j])), [0.6, 0.8j], rtol=0, atol=2e-16)
+    g = W.rng(701)
+    for scale in (3.0, 1e-3, 1e3):
+        psi = scale * rand_state(5, g)
+        out = sv.renormalise(psi)
+        assert abs(np.sum(np.abs(out) ** 2) - 1.0) < 1e-15
+        np.testing.assert_allclose(out, psi / np.linalg.norm(psi), rtol=0, atol=1e-15)
+        assert abs(np.vdot(out, psi).imag) < 1e-12 and np.vdot(out, psi).real > 0   # same direction
+
+
+def test_rotations_match_matrix_exponentials_and_hand_values():
+    """RY(pi/2)|0> = (|0> + |1>)/sqrt(2) and RY(pi)|0> = |1> by hand (a sign
+    flip of theta gives -|1>/sqrt(2) terms); every rotation against
+    scipy.linalg.expm(-i theta sigma / 2), for both signs of theta."""
+    from oracle import noise
+    r = 1 / np.sqrt(2.0)
+    np.testing.assert_allclose(noise.rot_y(np.pi / 2) @ [1, 0], [r, r], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(noise.rot_y(np.pi) @ [1, 0], [0, 1], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(oe.rot("X", np.pi) @ [1, 0], [0, -1j], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(oe.rot("Z", np.pi / 2) @ [r, r], [0.5 - 0.5j, 0.5 + 0.5j], rtol=0, atol=1e-15)
+    for theta in (0.3, -1.1, 2.9):
+        np.testing.assert_allclose(noise.rot_y(theta), _expm_rotation(_Y_LIT, theta), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(oe.rot("X", theta), _expm_rotation(_X_LIT, theta), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(oe.rot("Z", theta), _expm_rotation(_Z_LIT, theta), rtol=0, atol=1e-14)
+
+
+def test_noise_gate_is_rz_ry_rx_with_rx_first():
+    """The three rotations do not commute, so the order is visible: the
+    product of matrix exponentials with RX applied first."""
+    from oracle import noise
+    tx, ty, tz = 0.7, -0.4, 1.3
+    want = _expm_rotation(_Z_LIT, tz) @ _expm_rotation(_Y_LIT, ty) @ _expm_rotation(_X_LIT, tx)
+    np.testing.assert_allclose(noise.noise_gate_matrix((tx, ty, tz)), want, rtol=0, atol=1e-14)
+    wrong = _expm_rotation(_X_LIT, tx) @ _expm_rotation(_Y_LIT, ty) @ _expm_rotation(_Z_LIT, tz)
+    assert np.max(np.abs(want - wrong)) > 0.1
+
+
+def test_t1t2_trajectory_ops_places_and_scales_each_draw():
+    """A one-qubit gate on qubit 1 and a CNOT(0, 1) get three noise gates:
+    on qubit 1 after the one-qubit gate, then on the control 0 and the target
+    1 after the CNOT.  With a single nonzero draw z[k] = e_axis, the list
+    holds the rotation about that axis by s_axis (the sigma of the law) at
+    position k and identities elsewhere: this fixes the order, the qubits
+    and the scaling s * z."""
+    from oracle import noise
+    T1, T2, t = 8.0, 5.0, 1.0
+    s = np.sqrt([t / T1, t / T1, 2 * t / T2 - t / T1])       # the law written out: s_x^2 = s_y^2 = t/T1
+    U = W.haar_u2(W.rng(702))
+    ops = [("1q", 1, U), ("cx", 0, 1)]
+    lits = (_X_LIT, _Y_LIT, _Z_LIT)
+    for k in range(3):
+        for axis in range(3):
+            z = np.zeros((3, 3))
+            z[k, axis] = 1.0
+            out = noise.t1t2_trajectory_ops(ops, z, T1, T2, t)
+            assert [o[0] for o in out] == ["1q", "1q", "cx", "1q", "1q"]
+            assert out[0] is ops[0] and out[2] is ops[1]
+            assert [o[1] for o in (out[1], out[3], out[4])] == [1, 0, 1]
+            for slot, pos in enumerate((1, 3, 4)):
+                want = _expm_rotation(lits[axis], s[axis]) if slot == k else np.eye(2)
+                np.testing.assert_allclose(out[pos][2], want, rtol=0, atol=1e-14)
+    with pytest.raises(ValueError):
+        noise.t1t2_trajectory_ops(ops, np.zeros((4, 3)), T1, T2, t)   # a draw left over
+
+
+def _pauli_channel_density(n, ops, lam):
+    """Exact mean state of T1/T2 trajectories: each noise gate averages to
+    the Pauli channel with Bloch factors lam = (l_x, l_y, l_z), i.e.
+    rho -> sum_P p_P P rho P with p_I = (1 + l_x + l_y + l_z) / 4,
+    p_X = (1 + l_x - l_y - l_z) / 4, p_Y = (1 - l_x + l_y - l_z) / 4,
+    p_Z = (1 - l_x - l_y + l_z) / 4, applied after every gate to each
+    qubit it touched (control then target for a CNOT)."""
+    lx, ly, lz = lam
+    probs = {"I": (1 + lx + ly + lz) / 4, "X": (1 + lx - ly - lz) / 4,
+             "Y": (1 - lx + ly - lz) / 4, "Z": (1 - lx - ly + lz) / 4}
+    lit = {"I": I2, "X": np.array(_X_LIT, dtype=complex), "Y": np.array(_Y_LIT, dtype=complex),
+           "Z": np.array(_Z_LIT, dtype=complex)}
+    rho = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    rho[0, 0] = 1
+    for op in ops:
+        if op[0] == "1q":
+            M = kron_all([op[2] if k == op[1] else I2 for k in range(n)])
+        else:
+            c, t = op[1], op[2]
+            M = kron_all([P0 if k == c else I2 for k in range(n)]) + \
+                kron_all([P1 if k == c else (lit["X"] if k == t else I2) for k in range(n)])
+        rho = M @ rho @ M.conj().T
+        for q in ((op[1],) if op[0] == "1q" else (op[1], op[2])):
+            new = np.zeros_like(rho)
+            for name, pr in probs.items():
+                S = kron_all([lit[name] if k == q else I2 for k in range(n)])
+                new += pr * S @ rho @ S
+            rho = new
+    return np.real(np.diag(rho))
+
+
+def test_t1t2_trajectory_mean_converges_to_the_decay_channel_circuit():
+    """Trajectories of a 3-qubit circuit with one-qubit gates and CNOTs,
+    averaged, approach the density-matrix circuit in which every touched
+    qubit of every gate goes through the decay channel (factors exp(-t/T2),
+    exp(-t/T2), exp(-t/T1)), within 5 standard errors per qubit.  Noise
+    on the wrong qubit of a CNOT, or on the target only, moves P(1) of the
+    control by many standard errors at this noise strength."""
+    from oracle import noise
+    n, T1, T2, t, T = 3, 3.0, 2.0, 1.0, 3000
+    g = W.rng(703)
+    ops = [("1q", q, W.haar_u2(g)) for q in range(n)] + [("cx", 0, 1), ("cx", 2, 1), ("1q", 0, W.haar_u2(g))]
+    n_noise = sum(1 if op[0] == "1q" else 2 for op in ops)
+    z = g.standard_normal((T, n_noise, 3))
+    per = np.array([oe.all_probabilities(oe.run_ops(n, noise.t1t2_trajectory_ops(ops, zz, T1, T2, t)))
+                    for zz in z])
+    mean = per.mean(axis=0)
+    diag = _pauli_channel_density(n, ops, (np.exp(-t / T2), np.exp(-t / T2), np.exp(-t / T1)))
+    x = np.arange(1 << n)
+    exact = np.array([diag[(x >> q) & 1 == 1].sum() for q in range(n)])
+    stderr = per.std(axis=0) / np.sqrt(T)
+    assert np.all(np.abs(mean - exact) < 5 * stderr + 1e-12)
+
+
+def test_ensemble_probabilities_is_the_mean_of_dense_trajectories():
+    """Three trajectories of a 3-qubit noisy circuit, each built here as one
+    dense 8x8 product of Kronecker-expanded gates and expm rotations applied
+    to |000>, their P(q = 1) summed over the index bits and averaged by hand,
+    equal ensemble_probabilities."""
+    n = 3
+    g = W.rng(704)
+    ops = [("1q", 0, W.haar_u2(g)), ("1q", 2, W.haar_u2(g)), ("cx", 2, 0), ("1q", 1, W.haar_u2(g))]
+    n_noise = 1 + 1 + 2 + 1
+    angle_sets = g.normal(0, 0.4, size=(3, n_noise, 2))
+    X = np.array(_X_LIT, dtype=complex)
+
+    def on(q, A):
+        return kron_all([A if k == q else I2 for k in range(n)])
+
+    want = np.zeros(n)
+    for angles in angle_sets:
+        M = np.eye(1 << n, dtype=complex)
+        k = 0
+        for op in ops:
+            if op[0] == "1q":
+                M = on(op[1], op[2]) @ M
+                touched = (op[1],)
+            else:
+                c, t = op[1], op[2]
+                M = (kron_all([P0 if j == c else I2 for j in range(n)]) +
+                     kron_all([P1 if j == c else (X if j == t else I2) for j in range(n)])) @ M
+                touched = (c, t)
+            for q in touched:
+                M = on(q, _expm_rotation(_Z_LIT, angles[k, 1])) @ on(q, _expm_rotation(_X_LIT, angles[k, 0])) @ M
+                k += 1
+        psi = M[:, 0]
+        w = np.abs(psi) ** 2
+        want += np.array([sum(w[i] for i in range(1 << n) if (i >> q) & 1) for q in range(n)]) / 3.0
+    np.testing.assert_allclose(oe.ensemble_probabilities(n, ops, angle_sets), want, rtol=0, atol=1e-14)
