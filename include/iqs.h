@@ -438,8 +438,11 @@ iqs_status iqs_pool_many_run(iqs_pool_many* w, int n_circuits, const iqs_circuit
  * Scratch is one static device array of about 320 KiB that every GPU loading
  * the library keeps until exit.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture on that device.  All calls share the array:
- * calls that overlap on the GPU race and must be ordered by the caller.
+ * before any stream capture on that device.  The address is cached with the
+ * id of the CUDA context it belongs to; after the context is destroyed and
+ * created again (cudaDeviceReset), the next call looks it up again, and that
+ * call too should precede any capture.  All calls share the array: calls
+ * that overlap on the GPU race and must be ordered by the caller.
  * Never calls cudaMalloc, cudaFree or any allocating routine. */
 iqs_status iqs_probabilities_noalloc(const void* state, int n, int dtype, void* stream, double* out);
 

@@ -18,8 +18,12 @@
 //     IQS_EINVAL before any work is queued.
 //   - Host code cannot use the array's name as a device address.  The first
 //     call on each device looks the address up with cudaGetSymbolAddress (with
-//     that device current) and caches it; that first call should therefore
-//     come before any stream capture on that device.
+//     that device current) and caches it, together with the unique id of the
+//     CUDA context it belongs to; that first call should therefore come before
+//     any stream capture on that device.  A later call whose current context
+//     has another id (the context was destroyed and created again, e.g. by
+//     cudaDeviceReset) looks the address up again instead of using a stale
+//     one; the first call after such a reset should again precede any capture.
 //   - Every call on a device shares the same array, and the array keeps the
 //     last call's contents.  The partial sums are fully rewritten by each call
 //     before they are read; the flag, which must start at zero, is cleared at
@@ -28,6 +32,8 @@
 //     results; order them on one stream or with events.
 //   - No call here allocates: no cudaMalloc, cudaFree or allocating library
 //     routine.
+#include <cuda.h>  // CUcontext and CUresult types; driver functions are resolved through the runtime
+
 #include <cmath>
 #include <mutex>
 
@@ -46,18 +52,57 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-double* g_addr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+struct ScratchAddress {
+  double* addr = nullptr;
+  bool ctx_known = false;       // whether ctx_id identifies the context addr belongs to
+  unsigned long long ctx_id = 0;
+};
+ScratchAddress g_addr[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id (for the life of the process) of the calling thread's current
+// context; false when there is none yet or the driver cannot tell.
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult r;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &r) == cudaSuccess &&
+        r == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &r) == cudaSuccess &&
+        r == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  if (get_current == nullptr || get_id == nullptr) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || c == nullptr) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_noalloc_scratch in the current context of device
+// ``dev``: cached per device and looked up again when the context changed
+// (or cannot be identified).
 cudaError_t scratch_address(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (g_addr[dev] == nullptr) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
+  ScratchAddress& c = g_addr[dev];
+  unsigned long long id = 0;
+  if (c.addr != nullptr && c.ctx_known && current_context_id(&id) && id == c.ctx_id) {
+    *out = c.addr;
+    return cudaSuccess;
   }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  c.addr = static_cast<double*>(p);  // the lookup has made the device's context current
+  c.ctx_known = current_context_id(&c.ctx_id);
+  *out = c.addr;
   return cudaSuccess;
 }
 

@@ -21,3 +21,14 @@ def gpu_lib():
         pytest.skip("no CUDA device")
     import paper_2001_10554_gb300 as iqs
     return iqs
+
+
+# Run last: the allocation-free call's tests, so that a run which stops at its
+# first failure has already run every other test.
+RUN_LAST = ("test_probabilities_noalloc.py",)
+
+
+def pytest_collection_modifyitems(session, config, items):
+    last = [it for it in items if it.fspath.basename in RUN_LAST]
+    if last:
+        items[:] = [it for it in items if it.fspath.basename not in RUN_LAST] + last
