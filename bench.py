@@ -48,11 +48,14 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["iqs", "reference"], default="iqs")
     ap.add_argument("--qubits", type=int, default=30)
     ap.add_argument("--math", choices=["auto", "emulated", "native"], default="auto")
-    ap.add_argument("--cpu-qubits", type=int, default=24, help="state size of the CPU-oracle sample")
+    ap.add_argument("--cpu-qubits", type=int, default=23, help="state size of the CPU-oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the complex64 32q sweep and the QAOA sections")
+    ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 one-qubit gate row")
+    ap.add_argument("--details", default=None, metavar="FILE",
+                    help="also write every section's full record to FILE (always printed to stderr)")
     ap.add_argument("--pso-graphs", type=int, default=64, help="graphs of the particle-swarm section (0 skips it)")
     ap.add_argument("--profile-pool", default=None, metavar="N,TRAJ,DEPTH",
                     help="one noisy brick circuit of TRAJ complex64 trajectories on the cluster-resident engine (for ncu)")
@@ -106,9 +109,7 @@ def cpu_baseline(args):
     n = args.cpu_qubits
     dt = run_oracle_sample(n)
     return {"value": round(oracle_bytes(n) / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"one sweep pass (n 1q gates + {N_CNOT} CNOT + all P(1) + Pauli expectation + norm) "
-                      f"on a {n}-qubit complex128 state instead of 30 qubits; numpy FP64, single thread, "
-                      f"{dt:.1f} s"}
+            "sample": f"one sweep pass on a {n}-qubit complex128 state (not 30); numpy FP64, 1 thread, {dt:.1f} s"}
 
 
 def sweep_workload(n: int) -> str:
@@ -280,13 +281,35 @@ def sweep_c64(iqs, torch, dev, n: int, steps: int, warmup: int):
     ms = t0.elapsed_time(t1) / steps
     avg1q = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     byt = n * 2 * 8 * N + N_CNOT * 2 * 8 * (N // 2)
+    # untimed: every one-qubit gate once more, 4096 gathered pairs per target
+    # before and after; the FP64 oracle's pair update with the FP64 matrix on
+    # the gathered (upcast) inputs is the expected output
+    from oracle import statevector as sv
+    g = np.random.Generator(np.random.PCG64(SEED_STATE + 1))
+    err_abs, err_rel = 0.0, 0.0
+    for q in range(n):
+        k = g.integers(0, N // 2, size=4096)
+        i0 = ((k >> q) << (q + 1)) | (k & ((1 << q) - 1))
+        idx = torch.as_tensor(np.concatenate([i0, i0 | (1 << q)]), device=dev)
+        x = st[idx].cpu().numpy().astype(np.complex128)
+        _lib.check(L.iqs_apply_1q(h, q, U8[q]), "iqs_apply_1q")
+        stream.synchronize()
+        y = st[idx].cpu().numpy().astype(np.complex128)
+        e0, e1 = sv.pair_update(x[:4096], x[4096:], Us[q])
+        d = np.abs(y - np.concatenate([e0, e1]))
+        scale = np.maximum(np.abs(x[:4096]), np.abs(x[4096:]))
+        err_abs = max(err_abs, float(d.max()))
+        err_rel = max(err_rel, float((d / np.concatenate([scale, scale])).max()))
     reg.close()
     del st
     torch.cuda.empty_cache()
     return {"workload": f"{n}-qubit complex64 sweep ({N * 8 / 2**30:.0f} GiB): apply_1q on q=0..{n-1} + {N_CNOT} CNOT",
             "value": round(byt / (ms * 1e-3) / 1e9, 1), "unit": "GB/s", "ms_per_step": round(ms, 3),
             "avg_1q_launch_ms": round(avg1q, 4), "avg_1q_GBs": round(2 * 8 * N / (avg1q * 1e-3) / 1e9, 1),
-            "error_bound": "FP32 gate arithmetic: <= 8 * 2^-24 per gate on unit-norm states (tests/test_gpu_parity.py)"}
+            "err_vs_oracle": {"max_abs": err_abs, "max_rel_to_pair": err_rel,
+                              "how": "per target, 4096 gathered pairs: GPU complex64 gate vs the FP64 oracle pair "
+                                     "update with the FP64 matrix on the same (upcast) inputs; amplitudes ~2^-16.5"},
+            "error_bound": "FP32 gate arithmetic: <= 8 * 2^-24 of the pair's largest amplitude per gate"}
 
 
 def median_call_s(torch, fn, runs: int = 5) -> float:
@@ -412,12 +435,28 @@ def kq_measure_section(iqs, torch, dev):
     return out
 
 
+GOLDEN_QAOA = os.path.join(ROOT, "tests", "golden", "qaoa_oracle.json")
+
+
+def load_qaoa_golden():
+    """FP64 oracle energies and gradients of the QAOA rows and the 28-qubit
+    case, written by tests/golden/make_qaoa_oracle.py (oracle calls only)."""
+    try:
+        with open(GOLDEN_QAOA) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
 def qaoa_section(iqs, torch):
     """Batched complex64 QAOA energy + adjoint gradient (256 parameter sets per
     graph, one engine call) against the plain complex128 path (one parameter
     set per call), on seeded random 3-regular graphs; plus the 28-qubit
-    large-adjoint configuration."""
+    large-adjoint configuration.  Errors are stated against the FP64 oracle's
+    stored-state adjoint (sets 0, 85, 170, 255 of each row) and, at 28 qubits,
+    against the oracle's energy and central differences of oracle energies."""
     import workloads as W
+    gold = load_qaoa_golden()
     out = {"workload": "QAOA Max-Cut on random 3-regular graphs, p=4, 256 (gamma, beta) sets per graph; "
                        "energy <C> + adjoint gradient", "rows": [],
            "timing": "median of 5 synchronous engine calls after a warm-up (plain complex128: median over 8 sets)"}
@@ -431,30 +470,42 @@ def qaoa_section(iqs, torch):
         dt = median_call_s(torch, lambda: eng.run(gm, bt))
         eng.close()
         plain = iqs.QAOA(n, edges, "complex128", batch_max=1)
-        k = 8
+        sets = [0, 85, 170, 255, 1, 2, 3, 4]
         plain.run(gm[:1], bt[:1])
-        E128 = np.empty(k)
-        G128 = np.empty((k, 2 * p))
+        res128 = {}
         tp = []
-        for i in range(k):
+        for i in sets:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             e1, g1, b1 = plain.run(gm[i:i + 1], bt[i:i + 1])
             tp.append(time.perf_counter() - t0)
-            E128[i] = e1[0]
-            G128[i] = np.concatenate([g1[0], b1[0]])
+            res128[i] = (e1[0], np.concatenate([g1[0], b1[0]]))
         dtp = float(np.median(tp))
         plain.close()
-        g_err = float(np.max(np.abs(np.concatenate([dg64[:k], db64[:k]], axis=1) - G128)))
         torch.cuda.empty_cache()
         model = (12 * p + 2) * 8 * (1 << n) * B
-        out["rows"].append({"n": n, "p": p, "batch": B, "tile_choice": {k: tuned[k] for k in ("row_bits", "grid_mult")},
-                            "batched_c64_evals_per_s": round(B / dt, 1),
-                            "plain_c128_evals_per_s": round(1 / dtp, 1),
-                            "ratio": round((B / dt) * dtp, 2),
-                            "energy_err_c64_vs_c128_max": float(np.max(np.abs(E64[:k] - E128))),
-                            "grad_err_c64_vs_c128_max": g_err,
-                            "batched_model_GBs": round(model / dt / 1e9, 1)})
+        row = {"n": n, "p": p, "batch": B, "tile_choice": {k: tuned[k] for k in ("row_bits", "grid_mult")},
+               "batched_c64_evals_per_s": round(B / dt, 1), "plain_c128_evals_per_s": round(1 / dtp, 1),
+               "ratio": round((B / dt) * dtp, 2), "batched_model_GBs": round(model / dt / 1e9, 1)}
+        g = (gold or {}).get("rows", {}).get(str(n))
+        ok = g is not None and g["edges"] == edges.tolist() and len(g["sets"]) > 0
+        if ok:
+            e64, gr64, e128, gr128 = [], [], [], []
+            for s_, r in g["sets"].items():
+                i = int(s_)
+                assert g["params"][s_]["gammas"] == gm[i].tolist()
+                go = np.concatenate([r["grad_gammas"], r["grad_betas"]])
+                e64.append(abs(E64[i] - r["energy"]))
+                gr64.append(np.max(np.abs(np.concatenate([dg64[i], db64[i]]) - go)))
+                e128.append(abs(res128[i][0] - r["energy"]))
+                gr128.append(np.max(np.abs(res128[i][1] - go)))
+            row["err_vs_oracle"] = {"sets": sorted(int(k) for k in g["sets"]),
+                                    "energy_c64_max": float(max(e64)), "grad_c64_max": float(max(gr64)),
+                                    "energy_c128_max": float(max(e128)), "grad_c128_max": float(max(gr128)),
+                                    "oracle": "stored-state adjoint, FP64 (tests/golden/qaoa_oracle.json)"}
+        else:
+            row["err_vs_oracle"] = None
+        out["rows"].append(row)
     # large adjoint: 28 qubits, p = 4, one parameter set, complex64 with FP64 reductions
     n = 28
     edges = W.random_3regular_graph(n, 28)
@@ -464,32 +515,32 @@ def qaoa_section(iqs, torch):
     dt = median_call_s(torch, lambda: eng.run(gm, bt))
     eng.close()
     torch.cuda.empty_cache()
-    # errors: the energy against the complex128 engine, the gradient against
-    # central differences (h = 1e-4) of complex128 energies
-    ref = iqs.QAOA(n, edges, "complex128", batch_max=1)
-    E128 = ref.run(gm, bt, grad=False)[0]
-    h = 1e-4
-    fd = np.empty(8)
-    for j in range(8):
-        gp, bp, gmn, bmn = gm.copy(), bt.copy(), gm.copy(), bt.copy()
-        if j < 4:
-            gp[0, j] += h
-            gmn[0, j] -= h
-        else:
-            bp[0, j - 4] += h
-            bmn[0, j - 4] -= h
-        fd[j] = (ref.run(gp, bp, grad=False)[0] - ref.run(gmn, bmn, grad=False)[0]) / (2 * h)
-    ref.close()
-    torch.cuda.empty_cache()
-    adj_err = {"energy_err_vs_c128": float(abs(E[0] - E128)),
-               "grad_err_vs_central_diff_c128_max": float(np.max(np.abs(np.concatenate([dg[0], db[0]]) - fd))),
-               "central_diff": "h = 1e-4 on complex128 energies (truncation error of order h^2)"}
-    out["adjoint_28q"] = {"n": 28, "p": 4, "dtype": "complex64 storage, FP64-equivalent reductions",
-                          "ms_per_energy_and_gradient": round(dt * 1e3, 2), "energy": float(E[0]), **adj_err,
-                          "model_GBs": round((12 * 4 + 2) * 8 * 2 ** 28 / dt / 1e9, 1)}
-    best = out["rows"][1]
-    out["headline"] = {"n": best["n"], "p": best["p"], "batched_c64_evals_per_s": best["batched_c64_evals_per_s"],
-                       "plain_c128_evals_per_s": best["plain_c128_evals_per_s"], "ratio": best["ratio"]}
+    adj = {"n": 28, "p": 4, "dtype": "complex64 storage, FP64-equivalent reductions, renormalised every 2 layers",
+           "ms_per_energy_and_gradient": round(dt * 1e3, 2), "energy": float(E[0]),
+           "model_GBs": round((12 * 4 + 2) * 8 * 2 ** 28 / dt / 1e9, 1)}
+    lg = (gold or {}).get("large")
+    if lg and lg.get("edges") == edges.tolist() and "energy" in lg:
+        adj["energy_err_vs_oracle"] = float(abs(E[0] - lg["energy"]))
+        ours = np.concatenate([dg[0], db[0]])
+        fd = np.array(lg.get("grad_gammas", [None] * 4) + lg.get("grad_betas", [None] * 4), dtype=object)
+        have = [j for j in range(8) if fd[j] is not None]
+        if have:
+            adj["grad_err_vs_oracle_central_diff_max"] = float(max(abs(ours[j] - fd[j]) for j in have))
+            adj["grad_components_compared"] = len(have)
+            adj["oracle"] = ("oracle energy; gradient by central differences (h = 1e-5) of oracle energies "
+                             "(tests/golden/qaoa_oracle.json)")
+    out["adjoint_28q"] = adj
+    rows = {r["n"]: r for r in out["rows"]}
+    h24 = rows[24]
+    ev = h24["err_vs_oracle"] or {}
+    out["headline"] = {"n": 24, "p": p, "batch": B, "batched_c64_evals_per_s": h24["batched_c64_evals_per_s"],
+                       "plain_c128_evals_per_s": h24["plain_c128_evals_per_s"], "ratio": h24["ratio"],
+                       "energy_err_c64_vs_oracle_max": ev.get("energy_c64_max"),
+                       "grad_err_c64_vs_oracle_max": ev.get("grad_c64_max"),
+                       "by_n": {str(r["n"]): [r["batched_c64_evals_per_s"], r["plain_c128_evals_per_s"], r["ratio"],
+                                              (r["err_vs_oracle"] or {}).get("energy_c64_max")]
+                                for r in out["rows"]},
+                       "by_n_fields": "batched c64 evals/s, plain c128 evals/s, ratio, c64 energy error vs oracle"}
     return out
 
 
@@ -547,11 +598,13 @@ def ensemble_section(iqs, torch):
     out = {"workload": f"{circuits} circuits x {traj} trajectories, {n} qubits, depth {min(depths)}..{max(depths)} "
                        f"(uniform 40..120), noise RX.RZ N(0, 0.02^2) after every gate",
            "depths": depths, "timing": "median of 5 runs of the whole ensemble (synchronous calls) after a warm-up"}
-    means = {}
+    means, first = {}, {}
     for dtype in ("complex64", "complex128"):
         pool = iqs.Pool(n, dtype, batch_max=traj, depth_max=max(depths))
         pool.run_brick(Us[0][:2], ens[0]["angles"][:, :iqs.pool.noise_count(n, 2)])  # warm-up
-        m = [pool.run_brick(Us[i], ens[i]["angles"])[1] for i in range(circuits)]
+        res = [pool.run_brick(Us[i], ens[i]["angles"]) for i in range(circuits)]
+        m = [r[1] for r in res]
+        first[dtype] = res[0][0]
         dt = median_call_s(torch, lambda: [pool.run_brick(Us[i], ens[i]["angles"]) for i in range(circuits)])
         pool.close()
         torch.cuda.empty_cache()
@@ -587,11 +640,104 @@ def ensemble_section(iqs, torch):
     from oracle import ensemble as oe
     t0 = time.perf_counter()
     k = 2
-    for t in range(k):
-        oe.all_probabilities(oe.run_ops(n, oe.noisy_trajectory_ops(ens[0]["ops"], ens[0]["angles"][t])))
+    ref = [oe.all_probabilities(oe.run_ops(n, oe.noisy_trajectory_ops(ens[0]["ops"], ens[0]["angles"][t])))
+           for t in range(k)]
     dt = time.perf_counter() - t0
     out["cpu_oracle"] = {"trajectories_per_s": round(k / dt, 4), "cores": 1,
                          "sample": f"{k} trajectories of circuit 0 (depth {depths[0]}), numpy FP64"}
+    out["err_vs_oracle"] = {dt_: float(np.max(np.abs(first[dt_][:k] - np.array(ref)))) for dt_ in first}
+    out["err_vs_oracle"]["how"] = (f"P(1) of every qubit of trajectories 0..{k - 1} of circuit 0, GPU vs the FP64 "
+                                   f"oracle on the same angles")
+    return out
+
+
+def native_row(iqs, torch, state, reg, stream, U8, n: int):
+    """The sweep's one-qubit gates in native FP64 (DFMA) on a copy of the
+    state, beside the headline's double-float arithmetic on the original: GB/s
+    of the native kernel (CUDA events on the register's stream) and the
+    largest amplitude difference between the two after all n gates."""
+    from paper_2001_10554_gb300 import _lib
+    L = _lib.lib
+    with torch.cuda.stream(stream):
+        copy = state.clone()
+    stream.synchronize()
+    nat = iqs.Register.wrap(copy, stream=stream)
+    nat.set_math("native")
+    ev = []
+    for q in range(n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _lib.check(L.iqs_apply_1q(reg.handle, q, U8[q]), "iqs_apply_1q")
+        a.record(stream)
+        _lib.check(L.iqs_apply_1q(nat.handle, q, U8[q]), "iqs_apply_1q")
+        b.record(stream)
+        ev.append((a, b))
+    stream.synchronize()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    diff = 0.0
+    chunk = 1 << 26
+    with torch.cuda.stream(stream):
+        for i in range(0, state.numel(), chunk):
+            diff = max(diff, float((state[i:i + chunk] - copy[i:i + chunk]).abs().max()))
+    nat.close()
+    del copy
+    torch.cuda.empty_cache()
+    N = 1 << n
+    return {"kernel": "k_c128_native", "avg_1q_launch_ms": round(ms, 4),
+            "GBs": round(2 * 16 * N / (ms * 1e-3) / 1e9, 1),
+            "max_abs_diff_vs_double_float": diff,
+            "note": "median over the n targets; same inputs and matrices as the headline's double-float gates"}
+
+
+def sig3(x):
+    """A float to three significant digits (None stays None)."""
+    return None if x is None else float(f"{x:.3g}")
+
+
+def compact(extra: dict, native) -> dict:
+    """Short summaries of the sections for the one stdout line (the full
+    records go to stderr).  ``by_n`` lists, per QAOA row, batched complex64
+    evaluations/s, plain complex128 evaluations/s, their ratio and the
+    complex64 energy error against the oracle."""
+    out = {}
+    q = extra.get("qaoa")
+    if q:
+        h = dict(q["headline"])
+        h.pop("by_n_fields", None)
+        for k in ("energy_err_c64_vs_oracle_max", "grad_err_c64_vs_oracle_max"):
+            h[k] = sig3(h.get(k))
+        h["by_n"] = {n: [v[0], v[1], v[2], sig3(v[3])] for n, v in h["by_n"].items()}
+        out["qaoa_headline"] = h
+        a = q["adjoint_28q"]
+        out["adjoint_28q"] = {k: (sig3(a[k]) if "err" in k else a[k])
+                              for k in ("ms_per_energy_and_gradient", "model_GBs", "energy_err_vs_oracle",
+                                        "grad_err_vs_oracle_central_diff_max", "grad_components_compared")
+                              if k in a}
+    c = extra.get("c64_32q")
+    if c:
+        out["c64_32q"] = {"GBs": c["value"], "avg_1q_GBs": c["avg_1q_GBs"],
+                          "err_vs_oracle_max_abs": sig3(c["err_vs_oracle"]["max_abs"]),
+                          "err_vs_oracle_max_rel": sig3(c["err_vs_oracle"]["max_rel_to_pair"])}
+    if native:
+        out["native_fp64_1q"] = {"GBs": native["GBs"], "avg_1q_launch_ms": native["avg_1q_launch_ms"],
+                                 "max_abs_diff_vs_double_float": sig3(native["max_abs_diff_vs_double_float"])}
+    e = extra.get("noise_ensemble")
+    if e:
+        out["noise_ensemble"] = {"c64_traj_per_s": e["complex64"]["trajectories_per_s"],
+                                 "c64_one_launch_traj_per_s": e["complex64"]["one_launch"]["trajectories_per_s"],
+                                 "c128_traj_per_s": e["complex128"]["trajectories_per_s"],
+                                 "p1_err_vs_oracle": {k: sig3(v) for k, v in e["err_vs_oracle"].items() if k != "how"}}
+    r = extra.get("random_circuit_12q")
+    if r:
+        out["random_circuit_12q_us"] = {"gate_by_gate": r["gate_by_gate_us"], "pool_passes": r["pool_tiled_passes_us"],
+                                        "cpu_oracle": r["cpu_oracle_us"],
+                                        "p1_err_vs_oracle": sig3(r["max_p1_err_vs_oracle"])}
+    k = extra.get("kq_measure")
+    if k:
+        out["kq_high_GBs"] = {nm: {str(row["k"]): row["GBs"] for row in k[nm]["apply_kq"] if row["targets"] == "high"}
+                              for nm in ("c128_30q", "c64_32q")}
+    ps = extra.get("pso_qaoa")
+    if ps:
+        out["pso_evals_per_s"] = round(float(np.mean([row["evaluations_per_s"] for row in ps["rows"]])), 1)
     return out
 
 
@@ -775,7 +921,7 @@ def main(argv=None):
             dt = time.perf_counter() - t0
             e2e = {"value": round(world * bytes_step * args.e2e_steps / dt / 1e9, 2), "unit": "GB/s",
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * (n + 2),
-                   "steps": args.e2e_steps, "path": "iqs_upload (pinned host) + sweep + iqs_download (pinned host)"}
+                   "steps": args.e2e_steps, "path": "iqs_upload + sweep + iqs_download, pinned host"}
             del host_in, host_out
         except RuntimeError as exc:
             e2e = {"value": None, "unit": "GB/s", "error": str(exc)[:200]}
@@ -783,6 +929,10 @@ def main(argv=None):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args)
+
+    native = None
+    if not args.no_native and args.math != "native":
+        native = native_row(iqs, torch, state, reg, stream, U8, n)
 
     reg.close()
     del state
@@ -810,12 +960,20 @@ def main(argv=None):
             "roofline": {"kernel": kernel_key, "bound": "hbm", "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": kernel_traffic(kernel_key),
-                         "bytes_per_launch": sb["1q"] // n, "avg_launch_ms": round(avg_1q_ms, 4),
-                         "per_target_ms": [round(float(x), 3) for x in per_q]},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "check": {"norm2": nn, "expectation": ex, "p_mean": float(np.mean(probs))},
+                         "bytes_per_launch": sb["1q"] // n, "avg_launch_ms": round(avg_1q_ms, 4)},
         }
-        line.update(extra)
+        line.update(compact(extra, native))
+        line.update({"cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+                     "check": {"norm2": nn, "expectation": ex, "p_mean": float(np.mean(probs))}})
+        details = dict(extra)
+        details["roofline_per_target_ms"] = [round(float(x), 3) for x in per_q]
+        if native:
+            details["native_fp64_1q"] = native
+        blob = json.dumps({"bench_details": details})
+        print(blob, file=sys.stderr, flush=True)
+        if args.details:
+            with open(args.details, "w") as f:
+                f.write(blob + "\n")
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -21,10 +21,11 @@ are checked on samples the oracle computes one by one:
   weight;
 * the 32-qubit complex64 sweep state (32 GiB) on sampled pairs, with the FP32
   bound of the other parity tests;
-* the QAOA rows (n = 24, p = 4, 256 sets; sampled sets against the oracle),
-  the 28-qubit adjoint (gradient against central differences of the
-  complex128 engine's energies) and the noise ensemble (16 qubits, sampled
-  trajectories against the oracle).
+* the QAOA rows (n = 24, p = 4, 256 sets; four sets against the oracle's
+  stored-state adjoint, with and without fused renormalisation), the 28-qubit
+  adjoint (energy against the oracle, gradient against central differences
+  of oracle energies; both stored by tests/golden/make_qaoa_oracle.py) and the
+  noise ensemble (16 qubits, sampled trajectories against the oracle).
 """
 import numpy as np
 import pytest
@@ -208,52 +209,66 @@ def test_sweep_gate_32q_c64_sampled(gpu_lib, dev):
     torch.cuda.empty_cache()
 
 
-def test_qaoa_rows_full_size_sampled(gpu_lib):
-    """n = 24, p = 4, 256 parameter sets in one call (the benchmark's row); two
-    sampled sets against the oracle: energy within 2e-6 (complex64 engine with
-    FP64-equivalent reductions) and gradient within 1e-4 + 1e-4 |g|."""
+def _qaoa_golden():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "qaoa_oracle.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("renorm", [0, 2])
+def test_qaoa_rows_full_size_vs_oracle(gpu_lib, renorm):
+    """n = 24, p = 4, 256 parameter sets in one call (the benchmark's row, with
+    forward TMA staging, the default; and renormalised every 2 layers, which
+    fuses the FP64 renormalisation into the adjoint passes); sets 0, 85, 170
+    and 255 against the FP64 oracle's stored-state adjoint
+    (tests/golden/qaoa_oracle.json, written by make_qaoa_oracle.py): energy
+    within 2e-6 (complex64 engine with FP64-equivalent reductions; the target
+    is 1e-5) and every derivative within 1e-4 + 1e-4 |g|."""
     n, p, B = 24, 4, 256
+    gold = _qaoa_golden()["rows"][str(n)]
     edges = W.random_3regular_graph(n, 1000 + n)
     gm, bt = W.qaoa_parameter_sets(p, B, 2000 + n)
-    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=B)
+    assert gold["edges"] == edges.tolist()
+    eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=B, renorm_every=renorm)
     E, dg, db = eng.run(gm, bt)
     eng.close()
-    Eo = oq.qaoa_energy(n, edges, gm[0], bt[0])
-    assert abs(E[0] - Eo) <= 2e-6
-    Eo, go, bo = oq.qaoa_energy_grad_stored(n, edges, gm[173], bt[173])
-    assert abs(E[173] - Eo) <= 2e-6
-    assert np.all(np.abs(dg[173] - go) <= 1e-4 + 1e-4 * np.abs(go))
-    assert np.all(np.abs(db[173] - bo) <= 1e-4 + 1e-4 * np.abs(bo))
+    assert len(gold["sets"]) >= 4
+    for s_, r in gold["sets"].items():
+        i = int(s_)
+        assert gold["params"][s_]["gammas"] == gm[i].tolist() and gold["params"][s_]["betas"] == bt[i].tolist()
+        go, bo = np.array(r["grad_gammas"]), np.array(r["grad_betas"])
+        assert abs(E[i] - r["energy"]) <= 2e-6, i
+        assert np.all(np.abs(dg[i] - go) <= 1e-4 + 1e-4 * np.abs(go)), i
+        assert np.all(np.abs(db[i] - bo) <= 1e-4 + 1e-4 * np.abs(bo)), i
     assert np.all((E >= -1e-9) & (E <= len(edges) + 1e-9))     # 0 <= <C> <= |E|
     torch.cuda.empty_cache()
 
 
-def test_adjoint_28q_gradient_vs_central_differences(gpu_lib):
-    """The 28-qubit adjoint row (complex64, renormalised every 2 layers): its
-    gradient against central differences of the complex128 engine's energies."""
+def test_adjoint_28q_vs_oracle(gpu_lib):
+    """The 28-qubit adjoint row (complex64, renormalised every 2 layers): the
+    energy against the FP64 oracle's energy (within 1e-5, the stated target)
+    and every derivative against central differences (h = 1e-5) of oracle
+    energies (within 1e-4 + 1e-4 |g|), both stored in
+    tests/golden/qaoa_oracle.json by make_qaoa_oracle.py."""
     n = 28
+    gold = _qaoa_golden()["large"]
     edges = W.random_3regular_graph(n, 28)
     gm, bt = W.qaoa_parameter_sets(4, 1, 29)
+    assert gold["edges"] == edges.tolist() and gold["gammas"] == gm[0].tolist()
     eng = gpu_lib.QAOA(n, edges, "complex64", batch_max=1, renorm_every=2)
     E, dg, db = eng.run(gm, bt)
     eng.close()
     torch.cuda.empty_cache()
-    ref = gpu_lib.QAOA(n, edges, "complex128", batch_max=1)
-    E128 = ref.run(gm, bt)[0][0]
-    assert abs(E[0] - E128) <= 1e-5
-    h = 1e-4
-    for which, arr, grad in (("g", gm, dg), ("b", bt, db)):
-        for l in (0, 3):
-            plus, minus = arr.copy(), arr.copy()
-            plus[0, l] += h
-            minus[0, l] -= h
-            if which == "g":
-                fd = (ref.run(plus, bt)[0][0] - ref.run(minus, bt)[0][0]) / (2 * h)
-            else:
-                fd = (ref.run(gm, plus)[0][0] - ref.run(gm, minus)[0][0]) / (2 * h)
-            assert abs(grad[0, l] - fd) <= 1e-4 + 1e-4 * abs(fd), (which, l)
-    ref.close()
-    torch.cuda.empty_cache()
+    assert abs(E[0] - gold["energy"]) <= 1e-5
+    checked = 0
+    for ours, fd in ((dg[0], gold["grad_gammas"]), (db[0], gold["grad_betas"])):
+        for l in range(4):
+            if fd[l] is not None:
+                assert abs(ours[l] - fd[l]) <= 1e-4 + 1e-4 * abs(fd[l]), l
+                checked += 1
+    assert checked >= 4
 
 
 def test_noise_ensemble_full_size_sampled(gpu_lib):
