@@ -266,8 +266,28 @@ iqs_status iqs_qaoa_tuning(const iqs_qaoa* q, int* row_bits, int* grid_mult);
 iqs_status iqs_qaoa_set_tma(iqs_qaoa* q, int mode);
 iqs_status iqs_qaoa_get_tma(const iqs_qaoa* q, int* mode, int* available);
 
-/* Copy the final state phi of parameter set ``index`` (after the last forward
- * pass, or after the uncompute when a gradient was computed) to host memory. */
+/* Pass schedule of the tiled engine.  0 (default): chained segments.  The
+ * RX factors of a mixer commute and the cost phase is diagonal, so layer l
+ * visits its tile passes forwards when l is even and backwards when l is odd;
+ * the last pass of one layer, the next layer's phase and that layer's first
+ * pass then run in one tile residency.  The turnaround (energy, lambda = C phi)
+ * and the first adjoint pass share the forward's last tile, the first pass
+ * starts from |+> generated on chip, and the last adjoint pass stores nothing.
+ * With m tile passes per mixer a gradient evaluation moves each vector
+ * 3 p (m - 1) + 1 times instead of 3 p m + 2.  It needs every pass to be a full
+ * tile (n >= 12 for complex64, 11 for complex128); elsewhere, and with
+ * schedule 1, one pass sequence per layer runs, with the energy and lambda in
+ * a pass of their own (this schedule alone uses TMA staging).  With one pass
+ * per mixer the whole evaluation is one tile residency, and renorm_every has
+ * no effect.  ``chained_available`` (may be NULL) reports whether the current
+ * plan can run chained.  Results agree within rounding. */
+iqs_status iqs_qaoa_set_schedule(iqs_qaoa* q, int schedule);
+iqs_status iqs_qaoa_get_schedule(const iqs_qaoa* q, int* schedule, int* chained_available);
+
+/* Copy the state phi of parameter set ``index`` to host memory: after an
+ * energy-only run, the final state.  After a run with a gradient on the
+ * chained schedule the vector holds an intermediate state of the uncompute
+ * (the last adjoint pass stores nothing); on schedule 1, the uncomputed state. */
 iqs_status iqs_qaoa_download_state(iqs_qaoa* q, int index, void* host, size_t bytes);
 
 /* Several graphs in one workspace (Section 4: the swarm experiment averages

@@ -713,6 +713,492 @@ constexpr auto k_mixer_fast() {
     return k_mixer_fast_fwd<TR, C, PH>;
 }
 
+// Merged adjoint tile of the chained schedule: layer A's RX^dagger on the
+// tile's bits (gradient sums to partials), then layer A's adjoint phase (its
+// gradient term C Im(conj(lambda) phi) to partials_g, then conj(T[C]) on both
+// vectors), then layer B's RX^dagger on the same bits (sums to partials_b2).
+// Loads and stores follow mixer_fast_body: a high pass loads its first round
+// straight from HBM, the low pass stages its tile; the last round of layer B
+// writes straight to HBM.
+template <class TR, int C>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_mixer_merged_adj(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
+                       const typename TR::RX* __restrict__ rxA, const typename TR::RX* __restrict__ rxB,
+                       double* __restrict__ partials, double* __restrict__ partials_b2,
+                       double* __restrict__ partials_g, int part_stride, unsigned* flag,
+                       const uint8_t* __restrict__ cut, const typename TR::PH* __restrict__ tables, int tsize,
+                       int per_graph) {
+  using W = typename TR::W;
+  using PHT = typename TR::PH;
+  __shared__ PHT st[kEdgeChunk + 1];
+  cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
+  for (int i = threadIdx.x; i < tsize; i += blockDim.x) st[i] = TR::conj(tables[(uint64_t)blockIdx.y * tsize + i]);
+  __syncthreads();
+  constexpr int K = TR::kTileBits;
+  constexpr int M = K - C;
+  constexpr unsigned T = 1u << K;
+  constexpr unsigned PER = T / kThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* sp = reinterpret_cast<W*>(smem_raw);
+  W* sl = sp + T;
+  const unsigned b = blockIdx.y;
+  typename TR::V* P = phi + (uint64_t)b * N;
+  typename TR::V* L = lam + (uint64_t)b * N;
+  const typename TR::RX kA = TR::rx_inv(rxA[b]);
+  const typename TR::RX kB = TR::rx_inv(rxB[b]);
+  const uint64_t tiles = N >> K;
+  const unsigned tid = threadIdx.x;
+  const int s = C == 0 ? 0 : s_bits;
+  const int mid = s - C;
+  const uint64_t off0 = C == 0 ? tid : ((uint64_t)(tid >> C) << s) | (tid & ((1u << C) - 1u));
+  const uint64_t step = C == 0 ? kThreads : ((uint64_t)(kThreads >> (C <= 8 ? C : 8)) << s);
+  constexpr int R = TR::kRegBits;
+  constexpr int NR = (M + R - 1) / R;
+  constexpr int POSL = C + R * (NR - 1);
+  constexpr int GBL = K - POSL;
+  constexpr int GB0 = M < R ? M : R;
+  constexpr bool kDirect = C > 0;
+  unsigned bad = 0;
+  dfx::Acc accA, accB, accg;
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
+    // layer A: every round, the first one loading from HBM (high pass) or from a staged tile (low pass)
+    if constexpr (!kDirect) {
+#pragma unroll
+      for (unsigned i = 0; i < PER; ++i) {
+        const unsigned l = tid + kThreads * i;
+        const uint64_t x = C <= 8 ? tbase + off0 + step * i : fast_x<C>(tbase, l, s);
+        sp[swz<TR>(l)] = TR::load(P[x], bad);
+        sl[swz<TR>(l)] = TR::load(L[x], bad);
+      }
+      __syncthreads();
+      mixer_rounds_to<TR, true, C, C, K>(sp, sl, kA, accA);
+    } else {
+      constexpr unsigned NSUB0 = 1u << (K - GB0);
+      for (unsigned sb = tid; sb < NSUB0; sb += kThreads) {
+        const unsigned base = block_base<C, GB0>(sb);
+        W a[1 << GB0], y[1 << GB0];
+#pragma unroll
+        for (int j = 0; j < (1 << GB0); ++j) {
+          const uint64_t x = fast_x<C>(tbase, base | ((unsigned)j << C), s);
+          a[j] = TR::load(P[x], bad);
+          y[j] = TR::load(L[x], bad);
+        }
+        round_in_regs<TR, true, GB0>(a, y, kA, accA);
+        const unsigned sbase = swz<TR>(base);
+#pragma unroll
+        for (int j = 0; j < (1 << GB0); ++j) {
+          const unsigned idx = sbase ^ swz<TR>((unsigned)j << C);
+          sp[idx] = a[j];
+          sl[idx] = y[j];
+        }
+      }
+      __syncthreads();
+      mixer_rounds_to<TR, true, C, C + GB0, K>(sp, sl, kA, accA);
+    }
+    // layer A's adjoint phase and its gradient term
+    {
+      float gsum = 0.f;
+#pragma unroll
+      for (unsigned i = 0; i < PER; ++i) {
+        const unsigned l = tid + kThreads * i;
+        const uint64_t x = C <= 8 ? tbase + off0 + step * i : fast_x<C>(tbase, l, s);
+        const unsigned idx = swz<TR>(l);
+        const int c = cut[x];
+        const W xv = sp[idx], yv = sl[idx];
+        const float cf = (float)c;
+        if constexpr (TR::kBlockSum) {
+          gsum = fmaf(cf, qops::im_conj_mul_fma(yv, xv, 0.f), gsum);
+        } else {
+          float pp, ee;
+          qops::im_conj_mul(yv, xv, pp, ee);
+          const float qq = cf * pp;
+          accg.add(qq, fmaf(cf, pp, -qq) + cf * ee);
+        }
+        sp[idx] = TR::mul(st[c], xv);
+        sl[idx] = TR::mul(st[c], yv);
+      }
+      if (TR::kBlockSum) accg.add(gsum, 0.f);
+    }
+    __syncthreads();
+    // layer B: rounds in shared memory, the last one straight to HBM
+    mixer_rounds_to<TR, true, C, C, POSL>(sp, sl, kB, accB);
+    constexpr unsigned NSUBL = 1u << (K - GBL);
+    for (unsigned sb = tid; sb < NSUBL; sb += kThreads) {
+      const unsigned base = block_base<POSL, GBL>(sb);
+      const unsigned sbase = swz<TR>(base);
+      W a[1 << GBL], y[1 << GBL];
+#pragma unroll
+      for (int j = 0; j < (1 << GBL); ++j) {
+        const unsigned idx = sbase ^ swz<TR>((unsigned)j << POSL);
+        a[j] = sp[idx];
+        y[j] = sl[idx];
+      }
+      round_in_regs<TR, true, GBL>(a, y, kB, accB);
+#pragma unroll
+      for (int j = 0; j < (1 << GBL); ++j) {
+        const uint64_t x = fast_x<C>(tbase, base | ((unsigned)j << POSL), s);
+        P[x] = TR::store(a[j]);
+        L[x] = TR::store(y[j]);
+      }
+    }
+    __syncthreads();  // the next tile reuses shared memory
+  }
+  if (bad) atomicOr(flag, 1u);
+  block_partial(accA.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+  block_partial(accB.value(), partials_b2 + (uint64_t)b * part_stride + blockIdx.x);
+  block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
+}
+
+// ---------------------------------------------------------------- chained segments
+// A second schedule of the same evaluation (forward, energy and lambda, adjoint
+// by uncompute) that moves each vector through HBM fewer times.  All RX
+// factors of a mixer commute and the cost phase is diagonal, so the mixer of
+// layer l may visit its passes (tile geometries g_0..g_{m-1}) in either order:
+// even layers go 0..m-1, odd layers m-1..0.  The last pass of layer l and the
+// first pass of layer l+1 then share a geometry, and the phase between them is
+// an element-wise step, so the three run in ONE tile residency: RX_l on the
+// tile's bits, phase_{l+1}, RX_{l+1} on the same bits.  The evaluation becomes
+// one list of operations (phases, RX on one geometry, the turnaround that forms
+// the energy and lambda = C phi, and the mirrored adjoint operations), cut into
+// segments of consecutive operations on one geometry; each segment is one
+// launch of k_seg.
+//   - The first segment starts from |+>^n generated in registers (no fill, no load).
+//   - The turnaround segment runs RX_{p-1} on its bits, forms E, |phi|^2,
+//     lambda = C phi and |lambda|^2, then the adjoint RX^dagger_{p-1} on the
+//     same bits; phi then equals the segment's input (up to rounding), so only
+//     lambda is stored.
+//   - The last adjoint segment stores nothing: only its gradient terms are needed.
+// For m passes per mixer and depth p, one evaluation with gradient moves
+// 3 p (m - 1) + 1 vector read-write pairs, against 3 p m + 2 for one pass
+// sequence per layer (for m = 3, p = 4: 101 GB instead of 159 GB at 28 qubits).
+enum : uint8_t { kOpRX = 0, kOpPhase = 1, kOpTurn = 2, kOpEnergy = 3 };
+constexpr int kMaxSegOps = 2 * kMaxP + 3;  // a one-pass plan holds every operation in one segment
+
+struct SegOp {
+  uint8_t kind;
+  uint8_t layer;
+  uint8_t red;   // first per-thread accumulator slot of the op's sums (kSegTileSums: unused)
+  uint8_t pad;
+  uint16_t col;  // first partial column block (units of the launch's grid width) of the op's sums
+};
+constexpr uint16_t kNoCol = 0xffffu;  // an op without sums (forward RX and phase)
+// Per-thread double-float accumulators of a segment's sums, kept in shared
+// memory across the block's tiles and reduced once at the end (an FP64 block
+// reduction per op and tile would run on the slow FP64 pipe).  A segment with
+// more sums than slots (one tile pass per mixer at depth >= 3, where every
+// block holds a single tile) reduces each op's sums over the block per tile.
+constexpr int kSegRed = 8;
+
+enum : uint32_t {
+  kSegGen = 1u,        // phi = |+>^n, not loaded
+  kSegAdjIn = 2u,      // the segment starts in the adjoint part: lambda is loaded too
+  kSegStorePhi = 4u,
+  kSegStoreLam = 8u,
+  kSegRnScale = 16u,   // rescale phi and lambda on load (fused renormalisation)
+  kSegRnSum = 32u,     // sum |phi|^2 and |lambda|^2 of the stored values
+  kSegTileSums = 64u,  // per-tile block reductions instead of the accumulator slots
+};
+
+struct SegParams {
+  int nops;
+  int bmax;    // per-layer row stride of rx and tables
+  int tsize;   // phase-table entries per state
+  int per_graph;
+  uint32_t flags;
+  int rn_col;  // column blocks of the stored norms (|phi|^2, |lambda|^2 at rn_col + 1)
+  int rn_red;  // accumulator slots of the stored norms
+  int rn_stride;  // norms: [4][rn_stride] = current |phi|^2, lambda target, phi target, current |lambda|^2
+  float amp;      // 2^(-n/2) (complex64 start value; complex128 uses amp64)
+  double amp64;
+  SegOp ops[kMaxSegOps];
+};
+
+// FP64 sums of one value per thread over the block, added to slot[0..NV) in a
+// fixed order (thread 0).
+template <int NV>
+__device__ __forceinline__ void block_accumulate(const double (&v)[NV], double* slot, double (*red)[kThreads / 32]) {
+  double w[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    w[k] = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[k][threadIdx.x >> 5] = w[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int q = 0; q < kThreads / 32; ++q) s += red[k][q];
+      slot[k] += s;
+    }
+  }
+  __syncthreads();
+}
+
+template <class V>
+__device__ __forceinline__ V scale_v(V v, double f) {
+  using S = decltype(v.x);
+  v.x = (S)(v.x * (S)f);
+  v.y = (S)(v.y * (S)f);
+  return v;
+}
+
+// One segment on tiles of C row bits and K - C gate bits (the full-tile pass
+// shapes of k_mixer_fast).  ANYADJ: the segment may hold the turnaround or
+// start in the adjoint part (two vectors in shared memory); forward-only
+// segments use the lighter instantiation.
+template <class TR, int C, bool ANYADJ>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_seg(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
+          const typename TR::RX* __restrict__ rx, const typename TR::PH* __restrict__ tables,
+          const uint8_t* __restrict__ cut, double* __restrict__ partials, int part_stride,
+          const double* __restrict__ norms, unsigned* flag, const __grid_constant__ SegParams P) {
+  using V = typename TR::V;
+  using W = typename TR::W;
+  using PHT = typename TR::PH;
+  constexpr int K = TR::kTileBits;
+  constexpr int M = K - C;
+  constexpr unsigned T = 1u << K;
+  constexpr unsigned PER = T / kThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  W* sp = reinterpret_cast<W*>(smem_raw);
+  W* sl = sp + T;
+  __shared__ uint8_t cs[T];                       // cut counts of the tile's elements
+  __shared__ PHT st[kEdgeChunk + 1];              // phase table of the current phase op
+  __shared__ double slot[3 * kMaxSegOps + 2];     // per-op sums over this block's tiles (kSegTileSums)
+  __shared__ double red[3][kThreads / 32];
+  __shared__ dfx::Acc tacc[kSegRed][kThreads];    // per-thread sums over this block's tiles
+  __shared__ double rn_f[2];
+  const unsigned tid = threadIdx.x;
+  const unsigned b = blockIdx.y;
+  const bool tile_sums = (P.flags & kSegTileSums) != 0;
+  for (int i = tid; i < 3 * P.nops + 2; i += kThreads) slot[i] = 0.0;
+#pragma unroll
+  for (int r = 0; r < kSegRed; ++r) tacc[r][tid] = dfx::Acc();
+  // add this thread's sums of one op on the current tile
+  auto put = [&](const SegOp& op, int o, int nv, const dfx::Acc* a) {
+    if (tile_sums) {
+      double v[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < nv; ++k) v[k] = a[k].value();
+      block_accumulate<3>(v, &slot[3 * o], red);
+    } else {
+      for (int k = 0; k < nv; ++k) tacc[op.red + k][tid].add(a[k].h, a[k].l);
+    }
+  };
+  const uint8_t* cutb = cut + (uint64_t)(b / (unsigned)P.per_graph) * N;
+  V* Pv = phi + (uint64_t)b * N;
+  V* Lv = ANYADJ ? lam + (uint64_t)b * N : nullptr;
+  bool need_cut = false;
+  for (int o = 0; o < P.nops; ++o) need_cut |= P.ops[o].kind != kOpRX;
+  const bool gen = (P.flags & kSegGen) != 0;
+  const bool adj_in = ANYADJ && (P.flags & kSegAdjIn) != 0;
+  const bool st_phi = (P.flags & kSegStorePhi) != 0;
+  const bool st_lam = ANYADJ && (P.flags & kSegStoreLam) != 0;
+  const bool rn_scale = (P.flags & kSegRnScale) != 0;
+  const bool rn_sum = (P.flags & kSegRnSum) != 0;
+  if (rn_scale && tid == 0) {
+    const double np = norms[b], tl = norms[P.rn_stride + b];
+    const double tp = norms[2 * P.rn_stride + b], nl = norms[3 * P.rn_stride + b];
+    rn_f[0] = np > 0.0 ? sqrt(tp / np) : 1.0;
+    rn_f[1] = nl > 0.0 ? sqrt(tl / nl) : 1.0;
+  }
+  __syncthreads();
+  unsigned bad = 0;
+  V v0;
+  v0.x = (decltype(v0.x))(sizeof(v0.x) == 8 ? P.amp64 : (double)P.amp);
+  v0.y = 0;
+  const W w0 = TR::load(v0, bad);
+  const double f_phi = rn_scale ? rn_f[0] : 1.0, f_lam = rn_scale ? rn_f[1] : 1.0;
+  const uint64_t tiles = N >> K;
+  const int s = C == 0 ? 0 : s_bits;
+  const int mid = s - C;
+  const uint64_t off0 = C == 0 ? tid : ((uint64_t)(tid >> C) << s) | (tid & ((1u << C) - 1u));
+  const uint64_t step = C == 0 ? kThreads : ((uint64_t)(kThreads >> (C <= 8 ? C : 8)) << s);
+  const unsigned sw0 = swz<TR>(tid);
+  auto gx_of = [&](uint64_t tbase, unsigned i) -> uint64_t {
+    return C <= 8 ? tbase + off0 + step * i : fast_x<C>(tbase, tid + kThreads * i, s);
+  };
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
+    // load (coalesced: element l = tid + kThreads i)
+#pragma unroll
+    for (unsigned i = 0; i < PER; ++i) {
+      const unsigned l = tid + kThreads * i;
+      const uint64_t x = gx_of(tbase, i);
+      const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
+      if (gen) {
+        sp[idx] = w0;
+      } else {
+        V v = Pv[x];
+        if (rn_scale) v = scale_v(v, f_phi);
+        sp[idx] = TR::load(v, bad);
+      }
+      if constexpr (ANYADJ) {
+        if (adj_in) {
+          V v = Lv[x];
+          if (rn_scale) v = scale_v(v, f_lam);
+          sl[idx] = TR::load(v, bad);
+        }
+      }
+      if (need_cut) cs[l] = cutb[x];
+    }
+    __syncthreads();
+    bool adj = adj_in;
+    for (int o = 0; o < P.nops; ++o) {
+      const SegOp op = P.ops[o];
+      if (op.kind == kOpRX) {
+        const typename TR::RX k = rx[(uint64_t)op.layer * P.bmax + b];
+        dfx::Acc acc;
+        if constexpr (ANYADJ) {
+          if (adj) {
+            mixer_rounds<TR, true, C, C>(sp, sl, TR::rx_inv(k), acc);
+            put(op, o, 1, &acc);
+            continue;
+          }
+        }
+        mixer_rounds<TR, false, C, C>(sp, sl, k, acc);
+      } else if (op.kind == kOpPhase) {
+        const PHT* tb = tables + ((uint64_t)op.layer * P.bmax + b) * P.tsize;
+        for (int i = tid; i < P.tsize; i += kThreads) st[i] = adj ? TR::conj(tb[i]) : tb[i];
+        __syncthreads();
+        if (ANYADJ && adj) {
+          float gsum = 0.f;
+          dfx::Acc accg;
+#pragma unroll
+          for (unsigned i = 0; i < PER; ++i) {
+            const unsigned l = tid + kThreads * i;
+            const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
+            const int c = cs[l];
+            const W xv = sp[idx], yv = sl[idx];
+            const float cf = (float)c;
+            if constexpr (TR::kBlockSum) {
+              gsum = fmaf(cf, qops::im_conj_mul_fma(yv, xv, 0.f), gsum);
+            } else {
+              float pp, ee;
+              qops::im_conj_mul(yv, xv, pp, ee);
+              const float qq = cf * pp;
+              accg.add(qq, fmaf(cf, pp, -qq) + cf * ee);
+            }
+            sp[idx] = TR::mul(st[c], xv);
+            sl[idx] = TR::mul(st[c], yv);
+          }
+          if (TR::kBlockSum) accg.add(gsum, 0.f);
+          put(op, o, 1, &accg);
+          __syncthreads();  // element writes before the next op
+        } else {
+#pragma unroll
+          for (unsigned i = 0; i < PER; ++i) {
+            const unsigned l = tid + kThreads * i;
+            const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
+            sp[idx] = TR::mul(st[cs[l]], sp[idx]);
+          }
+          __syncthreads();
+        }
+      } else {  // kOpTurn / kOpEnergy: E = sum C |phi|^2, |phi|^2, and (turnaround) lambda = C phi, |lambda|^2
+        dfx::Acc acce, accn, accl;
+        const bool turn = ANYADJ && op.kind == kOpTurn;
+#pragma unroll
+        for (unsigned i = 0; i < PER; ++i) {
+          const unsigned l = tid + kThreads * i;
+          const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
+          const float cf = (float)cs[l];
+          const W xv = sp[idx];
+          float p, e;
+          qops::abs2(xv, p, e);
+          accn.add(p, e);
+          const float q = cf * p;
+          acce.add(q, fmaf(cf, p, -q) + cf * e);
+          if constexpr (ANYADJ) {
+            if (turn) {
+              const float c2 = cf * cf;  // <= 255^2: exact
+              const float q2 = c2 * p;
+              accl.add(q2, fmaf(c2, p, -q2) + c2 * e);
+              sl[idx] = qops::scale_int(xv, cf);
+            }
+          }
+        }
+        const dfx::Acc a3[3] = {acce, accn, accl};
+        put(op, o, turn ? 3 : 2, a3);
+        __syncthreads();  // lambda writes before the next op
+        if (turn) adj = true;
+      }
+    }
+    // store
+    dfx::Acc an, al;
+#pragma unroll
+    for (unsigned i = 0; i < PER; ++i) {
+      const uint64_t x = gx_of(tbase, i);
+      const unsigned idx = sw0 ^ swz<TR>(kThreads * i);
+      if (st_phi) {
+        const W w = sp[idx];
+        if (rn_sum) {
+          float p, e;
+          qops::abs2(w, p, e);
+          an.add(p, e);
+        }
+        Pv[x] = TR::store(w);
+      }
+      if constexpr (ANYADJ) {
+        if (st_lam) {
+          const W w = sl[idx];
+          if (rn_sum) {
+            float p, e;
+            qops::abs2(w, p, e);
+            al.add(p, e);
+          }
+          Lv[x] = TR::store(w);
+        }
+      }
+    }
+    if (rn_sum) {
+      if (tile_sums) {
+        const double v[2] = {an.value(), al.value()};
+        block_accumulate<2>(v, &slot[3 * P.nops], red);
+      } else {
+        tacc[P.rn_red][tid].add(an.h, an.l);
+        tacc[P.rn_red + 1][tid].add(al.h, al.l);
+      }
+    }
+    __syncthreads();  // the next tile reuses shared memory
+  }
+  if (bad) atomicOr(flag, 1u);
+  // this block's sums to its column of each op's partial blocks
+  const uint64_t row = (uint64_t)b * part_stride + blockIdx.x;
+  const uint64_t w = gridDim.x;
+  if (tile_sums) {
+    if (tid == 0) {
+      for (int o = 0; o < P.nops; ++o) {
+        const SegOp op = P.ops[o];
+        if (op.col == kNoCol) continue;
+        const int nv = (op.kind == kOpTurn) ? 3 : (op.kind == kOpEnergy ? 2 : 1);
+        for (int k = 0; k < nv; ++k) partials[row + ((uint64_t)op.col + k) * w] = slot[3 * o + k];
+      }
+      if (rn_sum) {
+        partials[row + (uint64_t)P.rn_col * w] = slot[3 * P.nops];
+        partials[row + ((uint64_t)P.rn_col + 1) * w] = slot[3 * P.nops + 1];
+      }
+    }
+  } else {
+    for (int o = 0; o < P.nops; ++o) {
+      const SegOp op = P.ops[o];
+      if (op.col == kNoCol) continue;
+      const int nv = (op.kind == kOpTurn) ? 3 : (op.kind == kOpEnergy ? 2 : 1);
+      for (int k = 0; k < nv; ++k)
+        block_partial(tacc[op.red + k][tid].value(), partials + row + ((uint64_t)op.col + k) * w);
+    }
+    if (rn_sum) {
+      block_partial(tacc[P.rn_red][tid].value(), partials + row + (uint64_t)P.rn_col * w);
+      block_partial(tacc[P.rn_red + 1][tid].value(), partials + row + ((uint64_t)P.rn_col + 1) * w);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- TMA-staged mixer pass
 // The same pass with its tiles moved by the Tensor Memory Accelerator: one
 // thread issues cp.async.bulk.tensor loads (completion counted on an
@@ -774,6 +1260,9 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 constexpr uint32_t kMbarSpinLimit = 1u << 26;  // try_wait rounds before a wait is declared failed
 
+// PH = 3 (forward only, chained schedule): layer A's RX on the tile's bits,
+// then layer B's cost phase on every element, then layer B's RX (rx2) on the
+// same bits, in one tile residency.
 template <class TR, bool ADJ, int C, int PH>
 __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ CUtensorMap tm_phi,
                                                         const __grid_constant__ CUtensorMap tm_lam, uint64_t N,
@@ -781,7 +1270,9 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
                                                         double* __restrict__ partials, int part_stride, unsigned* flag,
                                                         const uint8_t* __restrict__ cut,
                                                         const typename TR::PH* __restrict__ tables, int tsize,
-                                                        double* __restrict__ partials_g, unsigned* err, int per_graph) {
+                                                        double* __restrict__ partials_g, unsigned* err, int per_graph,
+                                                        const typename TR::RX* __restrict__ rx2) {
+  static_assert(PH != 3 || !ADJ, "merged tiles of the TMA kernel are forward only");
   if (PH) cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
   using TT = TmaTraits<TR>;
   using V = typename TR::V;
@@ -875,6 +1366,17 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
       __syncthreads();
     }
     mixer_rounds<TT, ADJ, C, C>(sp, sl, k, acc);
+    if constexpr (PH == 3) {
+#pragma unroll
+      for (unsigned i = 0; i < PER; ++i) {
+        const unsigned l = tid + kThreads * i;
+        const unsigned idx = swz<TT>(l);
+        const uint64_t x = tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
+        sp[idx] = TR::mul(st[cut[x]], sp[idx]);
+      }
+      __syncthreads();
+      mixer_rounds<TT, ADJ, C, C>(sp, sl, rx2[b], acc);
+    }
     if (CONVERT || PH == 2) {
       float gsum = 0.f;
 #pragma unroll
@@ -1100,6 +1602,10 @@ struct iqs_qaoa {
   std::vector<CUtensorMap> tm_phi, tm_lam;  // one per mixer pass (valid when tma_ok)
   bool tma_ok = false;
   unsigned* tma_err = nullptr;              // device word: a TMA wait gave up
+  // Pass schedule: 0 chained segments (default where every pass is a full tile),
+  // 1 one pass sequence per layer with separate energy and lambda passes.
+  int schedule = 0;
+  size_t partials_cap = 0;  // doubles allocated at partials
 };
 
 namespace iqs {
@@ -1169,6 +1675,10 @@ struct PhaseFuse {
   double* partials_g = nullptr;
   int per_graph = 1 << 30;  // state b uses cut table b / per_graph
   RenormFuse rn;            // fused renormalisation (adjoint, complex64, shape-specialised passes)
+  // mode 3 (chained schedule): RX of layer A, the phase, RX of layer B (rx2) in one tile;
+  // adjoint: layer B's gradient sums go to partials_b2
+  const typename TR::RX* rx2 = nullptr;
+  double* partials_b2 = nullptr;
 };
 
 template <class TR, bool ADJ, int C>
@@ -1256,13 +1766,15 @@ void launch_tma1(dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename T
                  unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta) {
   k_mixer_tma<TR, ADJ, C, PH><<<grid, kThreads, tma_smem<TR>(ADJ), s>>>(
       *ta.phi, ADJ ? *ta.lam : *ta.phi, N, sb, ta.hi_bits, rx, partials, ps, flag, f.cut, f.tables, f.tsize,
-      f.partials_g, ta.err, f.per_graph);
+      f.partials_g, ta.err, f.per_graph, f.rx2);
 }
 
 template <class TR, bool ADJ, int C>
 void launch_tma_c(dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename TR::RX* rx, double* partials, int ps,
                   unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta) {
-  if (!ADJ && f.mode == 1 && C == 0)
+  if (!ADJ && f.mode == 3)
+    launch_tma1<TR, ADJ, C, ADJ ? 0 : 3>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
+  else if (!ADJ && f.mode == 1 && C == 0)
     launch_tma1<TR, ADJ, C, (!ADJ && C == 0) ? 1 : 0>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
   else if (ADJ && f.mode == 2)
     launch_tma1<TR, ADJ, C, ADJ ? 2 : 0>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
@@ -1288,6 +1800,7 @@ cudaError_t set_tma_attrs_c(std::integer_sequence<int, Cs...>) {
   cudaError_t e = cudaSuccess;
   ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, 0>, a, bytes) : e), ...);
   if (ADJ) ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, ADJ ? 2 : 0>, a, bytes) : e), ...);
+  if (!ADJ) ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, ADJ ? 0 : 3>, a, bytes) : e), ...);
   return e;
 }
 
@@ -1296,6 +1809,7 @@ cudaError_t set_tma_attrs() {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 0>, a, (int)tma_smem<TR>(false));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 1>, a, (int)tma_smem<TR>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 3>, a, (int)tma_smem<TR>(false));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, true, 0, 0>, a, (int)tma_smem<TR>(true));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, true, 0, 2>, a, (int)tma_smem<TR>(true));
   const auto seq = std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{};
@@ -1485,6 +1999,317 @@ cudaError_t enqueue(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- chained-segment schedule (host)
+struct HostOp {
+  uint8_t kind;
+  int layer;
+  int geo;  // mixer pass index (RX only)
+  int sub;  // position of the pass within its layer (RX only)
+};
+
+struct HostSeg {
+  int geo = -1;
+  bool adj_in = false;
+  bool has_turn = false;
+  std::vector<HostOp> ops;
+};
+
+// The evaluation as one operation list cut into segments of one geometry each
+// (see k_seg).  Layer l visits passes 0..m-1 when l is even, m-1..0 when odd.
+std::vector<HostSeg> chain_segments(int m, int p, bool grad) {
+  std::vector<HostOp> fwd;
+  for (int l = 0; l < p; ++l) {
+    fwd.push_back(HostOp{kOpPhase, l, -1, 0});
+    for (int j = 0; j < m; ++j) fwd.push_back(HostOp{kOpRX, l, (l % 2 == 0) ? j : m - 1 - j, j});
+  }
+  std::vector<HostOp> ops = fwd;
+  ops.push_back(HostOp{grad ? kOpTurn : kOpEnergy, p - 1, -1, 0});
+  if (grad)
+    for (int i = (int)fwd.size() - 1; i >= 0; --i) ops.push_back(fwd[i]);
+  std::vector<HostSeg> segs;
+  bool adj = false;
+  for (const HostOp& o : ops) {
+    if (segs.empty() || (o.kind == kOpRX && segs.back().geo >= 0 && segs.back().geo != o.geo)) {
+      segs.push_back(HostSeg());
+      segs.back().adj_in = adj;
+    }
+    if (o.kind == kOpRX && segs.back().geo < 0) segs.back().geo = o.geo;
+    segs.back().ops.push_back(o);
+    if (o.kind == kOpTurn) {
+      adj = true;
+      segs.back().has_turn = true;
+    }
+  }
+  return segs;
+}
+
+// Partial column blocks per state: beta sums of layer l, pass j at l m + j;
+// gamma sums of layer l at p m + l; energy, |phi|^2, |lambda|^2 at p (m + 1)
+// + 0..2; the stored norms of the renormalisation at p (m + 1) + 3, 4.
+inline int chain_cols(int m, int p) { return p * (m + 1) + 5; }
+
+bool chain_available(const iqs_qaoa* q) {
+  if (q->passes.empty()) return false;
+  for (const Geo& g : q->passes) {
+    const bool ok = q->dtype == IQS_C128 ? fast_shape<T128>(g) : fast_shape<T64>(g);
+    if (!ok) return false;
+  }
+  return true;
+}
+
+template <class TR, int C>
+void launch_merged_adj1(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam,
+                        uint64_t N, int sb, const typename TR::RX* rxA, const typename TR::RX* rxB, double* pA,
+                        double* pB, double* pG, int ps, unsigned* flag, const uint8_t* cut,
+                        const typename TR::PH* tab, int tsize, int per_graph) {
+  k_mixer_merged_adj<TR, C><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rxA, rxB, pA, pB, pG, ps, flag, cut, tab,
+                                                         tsize, per_graph);
+}
+
+template <class TR, int... Cs>
+void dispatch_merged_adj(int c, dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam,
+                         uint64_t N, int sb, const typename TR::RX* rxA, const typename TR::RX* rxB, double* pA,
+                         double* pB, double* pG, int ps, unsigned* flag, const uint8_t* cut,
+                         const typename TR::PH* tab, int tsize, int per_graph, std::integer_sequence<int, Cs...>) {
+  if (c == 0) {
+    launch_merged_adj1<TR, 0>(grid, smem, s, phi, lam, N, sb, rxA, rxB, pA, pB, pG, ps, flag, cut, tab, tsize,
+                              per_graph);
+    return;
+  }
+  bool done = false;
+  ((c == Cs + TR::kRowBits && !done
+        ? (launch_merged_adj1<TR, Cs + TR::kRowBits>(grid, smem, s, phi, lam, N, sb, rxA, rxB, pA, pB, pG, ps, flag,
+                                                     cut, tab, tsize, per_graph),
+           done = true)
+        : false),
+   ...);
+}
+
+template <class TR, int... Cs>
+cudaError_t set_merged_attrs_c(int bytes, std::integer_sequence<int, Cs...>) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_mixer_merged_adj<TR, 0>, a, bytes);
+  ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_merged_adj<TR, Cs + TR::kRowBits>, a, bytes) : e), ...);
+  return e;
+}
+
+template <class TR, bool ANYADJ, int C>
+void launch_seg1(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N, int sb,
+                 const typename TR::RX* rx, const typename TR::PH* tab, const uint8_t* cut, double* partials, int ps,
+                 const double* norms, unsigned* flag, const SegParams& P) {
+  k_seg<TR, C, ANYADJ><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rx, tab, cut, partials, ps, norms, flag, P);
+}
+
+template <class TR, bool ANYADJ, int... Cs>
+void dispatch_seg(int c, dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N,
+                  int sb, const typename TR::RX* rx, const typename TR::PH* tab, const uint8_t* cut, double* partials,
+                  int ps, const double* norms, unsigned* flag, const SegParams& P, std::integer_sequence<int, Cs...>) {
+  if (c == 0) {
+    launch_seg1<TR, ANYADJ, 0>(grid, smem, s, phi, lam, N, sb, rx, tab, cut, partials, ps, norms, flag, P);
+    return;
+  }
+  bool done = false;
+  ((c == Cs + TR::kRowBits && !done
+        ? (launch_seg1<TR, ANYADJ, Cs + TR::kRowBits>(grid, smem, s, phi, lam, N, sb, rx, tab, cut, partials, ps,
+                                                     norms, flag, P),
+           done = true)
+        : false),
+   ...);
+}
+
+template <class TR, bool ANYADJ, int... Cs>
+cudaError_t set_seg_attrs_c(int bytes, std::integer_sequence<int, Cs...>) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_seg<TR, 0, ANYADJ>, a, bytes);
+  ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_seg<TR, Cs + TR::kRowBits, ANYADJ>, a, bytes) : e), ...);
+  return e;
+}
+
+template <class TR>
+cudaError_t set_seg_attrs() {
+  const auto seq = std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{};
+  const int one = (1 << TR::kTileBits) * (int)sizeof(typename TR::W);
+  cudaError_t e = set_seg_attrs_c<TR, false>(one, seq);
+  if (e == cudaSuccess) e = set_seg_attrs_c<TR, true>(2 * one, seq);
+  if (e == cudaSuccess) e = set_merged_attrs_c<TR>(2 * one, seq);
+  return e;
+}
+
+// Enqueue one evaluation on the chained schedule.  Segments of one RX, and
+// merged [RX, phase, RX] segments, run on the tuned pass kernels (TMA-staged
+// forward tiles, adjoint tiles with direct HBM rounds); the first segment,
+// the turnaround, the last segment and the renormalising ones run on k_seg.
+template <class TR>
+cudaError_t enqueue_chain(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
+  using V = typename TR::V;
+  const uint64_t N = q->N;
+  cudaStream_t s = q->stream;
+  V* phi = (V*)q->phi;
+  V* lam = (V*)q->lam;
+  const auto* rx = (const typename TR::RX*)q->rx;
+  const auto* tab = (const typename TR::PH*)q->tables;
+  const int m = (int)q->passes.size();
+  const uint64_t tiles = N >> TR::kTileBits;
+  const int gx = (int)std::min<uint64_t>(tiles, (uint64_t)blocks_per_state(q, B));
+  const int ncols = chain_cols(m, p);
+  const int ps = gx * ncols;
+  if ((size_t)B * ps > q->partials_cap) return cudaErrorInvalidValue;
+  const int out_stride = 1 + 2 * kMaxP;
+  const int E0 = p * (m + 1);  // energy column block
+  const int R = grad ? q->renorm_every : 0;
+  double* phi_norm = q->norms + 2 * q->bmax;
+  std::vector<HostSeg> segs = chain_segments(m, p, grad);
+  const int S = (int)segs.size();
+  // renormalisation (gradient runs, more than one segment): after the adjoint
+  // phase of layer l > 0 with (p - l) % R == 0 the segment holding that phase
+  // sums the norms of what it stores and the next segment rescales on load
+  std::vector<int> rn_sum(S, 0);
+  if (R > 0 && S > 1)
+    for (int i = 0; i + 1 < S; ++i)
+      if (segs[i].adj_in)  // with more than one segment, adjoint phases sit only in such segments
+        for (const HostOp& o : segs[i].ops)
+          if (o.kind == kOpPhase && o.layer > 0 && ((p - o.layer) % R) == 0) rn_sum[i] = 1;
+  int launches = 0;
+  const dim3 grid(gx, B);
+  for (int i = 0; i < S; ++i) {
+    const HostSeg& sg = segs[i];
+    const Geo& g = q->passes[sg.geo];
+    SegParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.nops = (int)sg.ops.size();
+    P.bmax = q->bmax;
+    P.tsize = q->n_edges + 1;
+    P.per_graph = q->per_graph;
+    P.rn_stride = q->bmax;
+    P.rn_col = E0 + 3;
+    P.amp64 = std::pow(2.0, -q->n / 2.0);
+    P.amp = (float)P.amp64;
+    const bool last = i + 1 == S;
+    const bool anyadj = sg.adj_in || sg.has_turn;
+    uint32_t fl = 0;
+    if (i == 0) fl |= kSegGen;
+    if (sg.adj_in) fl |= kSegAdjIn;
+    if (!grad || (!anyadj) || (sg.adj_in && !last)) fl |= kSegStorePhi;
+    if (grad && anyadj && !last) fl |= kSegStoreLam;
+    if (i > 0 && rn_sum[i - 1]) fl |= kSegRnScale;
+    if (rn_sum[i]) fl |= kSegRnSum;
+    P.flags = fl;
+    bool adj = sg.adj_in;
+    int nred = 0;
+    for (int o = 0; o < P.nops; ++o) {
+      const HostOp& h = sg.ops[o];
+      SegOp so;
+      so.kind = h.kind;
+      so.layer = (uint8_t)h.layer;
+      so.col = kNoCol;
+      so.red = 0;
+      so.pad = 0;
+      int nv = 0;
+      if (h.kind == kOpRX && adj) so.col = (uint16_t)(h.layer * m + h.sub), nv = 1;
+      if (h.kind == kOpPhase && adj) so.col = (uint16_t)(p * m + h.layer), nv = 1;
+      if (h.kind == kOpTurn) so.col = (uint16_t)E0, nv = 3;
+      if (h.kind == kOpEnergy) so.col = (uint16_t)E0, nv = 2;
+      if (h.kind == kOpTurn) adj = true;
+      so.red = (uint8_t)std::min(nred, 255);
+      nred += nv;
+      P.ops[o] = so;
+    }
+    P.rn_red = nred;
+    if (rn_sum[i]) nred += 2;
+    if (nred > kSegRed) P.flags |= kSegTileSums;
+    const size_t smem = (size_t)(anyadj ? 2 : 1) * ((size_t)1 << TR::kTileBits) * sizeof(typename TR::W);
+    const auto seq = std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{};
+    const int nop = (int)sg.ops.size();
+    const bool plain = (fl & (kSegGen | kSegRnScale | kSegRnSum)) == 0 && !sg.has_turn;
+    const bool single = plain && nop == 1 && sg.ops[0].kind == kOpRX;
+    const bool merged = plain && nop == 3 && sg.ops[0].kind == kOpRX && sg.ops[1].kind == kOpPhase &&
+                        sg.ops[2].kind == kOpRX;
+    const size_t tsz = (size_t)(q->n_edges + 1);
+    TmaArgs ta;
+    ta.use = q->tma_ok && q->tma_mode >= 1;
+    ta.phi = &q->tm_phi[sg.geo];
+    ta.lam = &q->tm_lam[sg.geo];
+    ta.hi_bits = q->n - g.s - g.m;
+    ta.err = q->tma_err;
+    if (single && !sg.adj_in) {
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)sg.ops[0].layer * q->bmax, nullptr, 0,
+                              q->flag, PhaseFuse<TR>(), ta);
+    } else if (single && sg.adj_in && !last) {
+      TmaArgs tadj = ta;
+      tadj.use = q->tma_ok && q->tma_mode >= 2;
+      launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx + (uint64_t)sg.ops[0].layer * q->bmax,
+                             q->partials + (size_t)P.ops[0].col * gx, ps, q->flag, PhaseFuse<TR>(), tadj);
+    } else if (merged && !sg.adj_in && ta.use) {
+      PhaseFuse<TR> f;
+      f.mode = 3;
+      f.cut = q->cut;
+      f.per_graph = q->per_graph;
+      f.tables = tab + (uint64_t)sg.ops[1].layer * q->bmax * tsz;
+      f.tsize = (int)tsz;
+      f.rx2 = rx + (uint64_t)sg.ops[2].layer * q->bmax;
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)sg.ops[0].layer * q->bmax, nullptr, 0,
+                              q->flag, f, ta);
+    } else if (merged && sg.adj_in && !last) {
+      dispatch_merged_adj<TR>(g.c, grid, smem, s, phi, lam, N, g.s, rx + (uint64_t)sg.ops[0].layer * q->bmax,
+                              rx + (uint64_t)sg.ops[2].layer * q->bmax, q->partials + (size_t)P.ops[0].col * gx,
+                              q->partials + (size_t)P.ops[2].col * gx, q->partials + (size_t)P.ops[1].col * gx, ps,
+                              q->flag, q->cut, tab + (uint64_t)sg.ops[0].layer * q->bmax * tsz, (int)tsz,
+                              q->per_graph, seq);
+    } else if (anyadj) {
+      dispatch_seg<TR, true>(g.c, grid, smem, s, phi, lam, N, g.s, rx, tab, q->cut, q->partials, ps, q->norms,
+                             q->flag, P, seq);
+    } else {
+      dispatch_seg<TR, false>(g.c, grid, smem, s, phi, lam, N, g.s, rx, tab, q->cut, q->partials, ps, q->norms,
+                              q->flag, P, seq);
+    }
+    ++launches;
+    if (sg.has_turn || (!grad && last)) {
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + (size_t)E0 * gx, gx, ps, 1.0, q->results, out_stride, 0);
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + (size_t)(E0 + 1) * gx, gx, ps, 1.0, phi_norm, 1, 0);
+      launches += 2;
+      if (sg.has_turn && R > 0) {  // |lambda|^2 at the turnaround: the target of later rescaling
+        k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + (size_t)(E0 + 2) * gx, gx, ps, 1.0,
+                                                q->norms + q->bmax, 1, 0);
+        ++launches;
+      }
+    }
+    if (rn_sum[i]) {
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + (size_t)(E0 + 3) * gx, gx, ps, 1.0, q->norms, 1, 0);
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + (size_t)(E0 + 4) * gx, gx, ps, 1.0,
+                                              q->norms + 3 * q->bmax, 1, 0);
+      launches += 2;
+    }
+  }
+  if (grad) {
+    for (int l = 0; l < p; ++l) {
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + (size_t)(l * m) * gx, m * gx, ps, 2.0, q->results,
+                                              out_stride, 1 + p + l);
+      k_finalize_batch<<<B, kThreads, 0, s>>>(q->partials + (size_t)(p * m + l) * gx, gx, ps, 2.0, q->results,
+                                              out_stride, 1 + l);
+      launches += 2;
+    }
+  }
+  k_divide_results<<<B, 32, 0, s>>>(q->results, out_stride, grad ? 1 + 2 * p : 1, phi_norm);
+  ++launches;
+  *n_launches = launches;
+  return cudaGetLastError();
+}
+
+// The chained schedule where it applies (every pass a full tile, partial sums
+// allocated, not the cluster-resident energy engine), else one pass sequence per layer.
+cudaError_t enqueue_any(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
+  const bool chain = q->schedule == 0 && chain_available(q) && !(!grad && use_cluster(q)) &&
+                     (size_t)B * (size_t)std::min<uint64_t>(q->N >> (q->dtype == IQS_C128 ? T128::kTileBits
+                                                                                         : T64::kTileBits),
+                                                             (uint64_t)blocks_per_state(q, B)) *
+                             chain_cols((int)q->passes.size(), p) <=
+                         q->partials_cap;
+  if (chain)
+    return q->dtype == IQS_C128 ? enqueue_chain<T128>(q, B, p, grad, n_launches)
+                                : enqueue_chain<T64>(q, B, p, grad, n_launches);
+  return q->dtype == IQS_C128 ? enqueue<T128>(q, B, p, grad, n_launches) : enqueue<T64>(q, B, p, grad, n_launches);
+}
+
 // Host-side parameters: RX(2 beta) coefficients and exp(-i gamma k) tables, FP64-built.
 void fill_params_c64(iqs_qaoa* q, int B, int p, const double* gam, const double* bet) {
   float2* rx = (float2*)q->host_params;
@@ -1572,6 +2397,19 @@ void replan(iqs_qaoa* q) {
   q->passes = plan_mixer(q->n, K, rows);
   for (auto& kv : q->graphs) cudaGraphExecDestroy(kv.second.first);
   q->graphs.clear();
+  // the chained schedule's partial sums: B x blocks per state <= max(bmax, 4 x 2432) rows
+  // of chain_cols(m, p) column blocks (a failed growth leaves that schedule unavailable)
+  const size_t need = (size_t)std::max(q->bmax, 4 * 2432) * chain_cols((int)q->passes.size(), kMaxP);
+  if (need > q->partials_cap) {
+    double* grown = nullptr;
+    if (cudaMalloc(&grown, sizeof(double) * need) == cudaSuccess) {
+      cudaFree(q->partials);
+      q->partials = grown;
+      q->partials_cap = need;
+    } else {
+      cudaGetLastError();
+    }
+  }
   // tensor maps for the TMA-staged passes (full tiles only)
   const int amp = q->dtype == IQS_C128 ? 16 : 8;
   q->tm_phi.assign(q->passes.size(), CUtensorMap{});
@@ -1696,6 +2534,7 @@ iqs_status iqs_qaoa_create_multi(int n, int dtype, int n_graphs, int per_graph, 
             cudaMalloc(&q->cut, q->N * (size_t)n_graphs) == cudaSuccess && cudaMalloc(&q->rx, q->rx_bytes) == cudaSuccess &&
             cudaMalloc(&q->tables, q->table_bytes) == cudaSuccess &&
             cudaMalloc(&q->partials, sizeof(double) * (size_t)ps * batch_max) == cudaSuccess &&
+            ((q->partials_cap = (size_t)ps * batch_max), true) &&
             cudaMalloc(&q->results, sizeof(double) * (size_t)batch_max * (1 + 2 * kMaxP)) == cudaSuccess &&
             cudaMalloc(&q->norms, sizeof(double) * 4 * (size_t)batch_max) == cudaSuccess &&
             cudaMalloc(&q->flag, sizeof(unsigned)) == cudaSuccess &&
@@ -1727,6 +2566,7 @@ iqs_status iqs_qaoa_create_multi(int n, int dtype, int n_graphs, int per_graph, 
   if (e == cudaSuccess) e = cudaMemsetAsync(q->flag, 0, sizeof(unsigned), q->stream);
   if (e == cudaSuccess) e = dtype == IQS_C128 ? set_smem_attrs<T128>() : set_smem_attrs<T64>();
   if (e == cudaSuccess) e = dtype == IQS_C128 ? set_tma_attrs<T128>() : set_tma_attrs<T64>();
+  if (e == cudaSuccess) e = dtype == IQS_C128 ? set_seg_attrs<T128>() : set_seg_attrs<T64>();
   if (e == cudaSuccess) e = cudaMemsetAsync(q->tma_err, 0, sizeof(unsigned), q->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
   if (e != cudaSuccess) {
@@ -1834,8 +2674,7 @@ iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, con
       cudaGraph_t graph = nullptr;
       e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        const cudaError_t ee = q->dtype == IQS_C128 ? enqueue<T128>(q, batch, p, grad, &kernels)
-                                                    : enqueue<T64>(q, batch, p, grad, &kernels);
+        const cudaError_t ee = enqueue_any(q, batch, p, grad, &kernels);
         e = cudaStreamEndCapture(s, &graph);
         if (ee != cudaSuccess) e = ee;
       }
@@ -1848,7 +2687,7 @@ iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, con
     kernels = it->second.second;
     e = cudaGraphLaunch(it->second.first, s);
   } else {
-    e = q->dtype == IQS_C128 ? enqueue<T128>(q, batch, p, grad, &kernels) : enqueue<T64>(q, batch, p, grad, &kernels);
+    e = enqueue_any(q, batch, p, grad, &kernels);
   }
   if (e != cudaSuccess) return report(IQS_ECUDA, "QAOA launch: %s", cudaGetErrorString(e));
   note_launches(kernels);
@@ -1949,6 +2788,21 @@ iqs_status iqs_qaoa_autotune(iqs_qaoa* q, int batch, int p, double* best_ms) {
   if (st != IQS_OK) return st;
   save_tuning(q);
   if (best_ms) *best_ms = best;
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_set_schedule(iqs_qaoa* q, int schedule) {
+  if (q == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (schedule < 0 || schedule > 1) return iqs::report(IQS_EINVAL, "schedule must be 0 or 1");
+  q->schedule = schedule;
+  iqs::replan(q);
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_get_schedule(const iqs_qaoa* q, int* schedule, int* chained_available) {
+  if (q == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (schedule) *schedule = q->schedule;
+  if (chained_available) *chained_available = iqs::chain_available(q) ? 1 : 0;
   return IQS_OK;
 }
 

@@ -116,6 +116,16 @@ class QAOA:
         call("iqs_qaoa_get_tma", self._h, C.byref(tma), C.byref(avail))
         return {"row_bits": rows.value, "grid_mult": mult.value, "tma_mode": tma.value, "tma_available": bool(avail.value)}
 
+    def set_schedule(self, schedule: str = "chained") -> None:
+        """Pass schedule: "chained" (segments that merge the passes at layer boundaries, the default) or
+        "per_layer" (one pass sequence per layer; the only one with TMA staging)."""
+        call("iqs_qaoa_set_schedule", self._h, {"chained": 0, "per_layer": 1}[schedule])
+
+    def schedule(self) -> dict:
+        sch, avail = C.c_int(), C.c_int()
+        call("iqs_qaoa_get_schedule", self._h, C.byref(sch), C.byref(avail))
+        return {"schedule": ("chained", "per_layer")[sch.value], "chained_available": bool(avail.value)}
+
     def set_tma(self, mode: int) -> None:
         """Stage mixer tiles with TMA: 0 off, 1 forward passes (the default), 2 forward and adjoint passes."""
         call("iqs_qaoa_set_tma", self._h, int(mode))

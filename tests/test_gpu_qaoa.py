@@ -126,11 +126,11 @@ def test_qaoa_renormalisation_keeps_results(gpu_lib):
 
 @pytest.mark.parametrize("n,R", [(12, 1), (14, 2), (16, 1), (16, 3), (20, 2)])
 def test_qaoa_fused_renormalisation(gpu_lib, n, R):
-    """complex64 renormalisation inside the adjoint passes (norms summed by a
-    layer's last pass, rescaling on the next layer's first load): the same
-    energies and gradients as without renormalisation and as the oracle, and
-    as the separate norm and rescale kernels (TMA adjoint passes) when TMA is
-    available."""
+    """complex64 renormalisation fused into the passes (norms summed over what
+    one pass stores, rescaling on the next pass's load): the same energies and
+    gradients as without renormalisation and as the oracle, on the chained
+    schedule and on the per-layer one, and as the separate norm and rescale
+    kernels (TMA adjoint passes) when TMA is available."""
     p, B = 5, 3
     edges = W.random_3regular_graph(n, 40 + n)
     gm, bt = W.qaoa_parameter_sets(p, B, 41 + n)
@@ -144,6 +144,10 @@ def test_qaoa_fused_renormalisation(gpu_lib, n, R):
         Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
         assert np.max(np.abs(E1 - Eo)) <= 2e-6
         assert np.max(np.abs(dg1 - dgo)) <= 1e-4 and np.max(np.abs(db1 - dbo)) <= 1e-4
+    eng.set_schedule("per_layer")  # renormalisation fused into the per-layer adjoint passes
+    E3, dg3, db3 = eng.run(gm, bt)
+    assert np.max(np.abs(E3 - E1)) <= 2e-6
+    assert np.max(np.abs(dg3 - dg1)) <= 1e-4 and np.max(np.abs(db3 - db1)) <= 1e-4
     if eng.tuning()["tma_available"]:
         eng.set_tma(2)
         E2, dg2, db2 = eng.run(gm, bt)
@@ -245,6 +249,7 @@ def test_qaoa_tma_staged_passes_match(gpu_lib, dtype, n):
     edges = W.random_3regular_graph(n if n % 2 == 0 else n - 1, 500 + n)
     gm, bt = W.qaoa_parameter_sets(p, B, 600 + n)
     eng = gpu_lib.QAOA(n, edges, dtype, batch_max=B)
+    eng.set_schedule("per_layer")  # TMA staging belongs to the per-layer schedule
     eng.set_tma(0)
     E0, dg0, db0 = eng.run(gm, bt)
     for mode in (1, 2):
@@ -290,3 +295,51 @@ def test_cluster_forward_matches_oracle_and_tiled(gpu_lib, n):
         assert abs(E[b] - oq.qaoa_energy(n, edges, gm[b], bt[b])) <= 2e-6
     ref = oq.qaoa_state(n, edges, gm[1], bt[1])
     assert np.max(np.abs(state - ref)) <= (n + 1) * p * 8 * 2.0 ** -24 * np.max(np.abs(ref)) * 4
+
+
+# ---------------------------------------------------------------- chained schedule
+# (dtype, n): one tile pass per mixer (the whole evaluation in one tile), two
+# and three passes per mixer, for both dtypes.
+CHAIN_CASES = [("complex64", 12), ("complex64", 13), ("complex64", 17), ("complex64", 21),
+               ("complex128", 11), ("complex128", 12), ("complex128", 16), ("complex128", 20)]
+
+
+@pytest.mark.parametrize("dtype,n", CHAIN_CASES)
+@pytest.mark.parametrize("p,R", [(1, 0), (2, 1), (3, 0), (5, 2)])
+def test_chained_schedule_matches_oracle_and_per_layer(gpu_lib, dtype, n, p, R):
+    """The chained schedule (layer boundaries merged into one tile pass, the
+    turnaround sharing the forward's last tile) gives the oracle's energies
+    and stored-state gradients (complex128: 1e-11 and 1e-9; complex64: 2e-6
+    and 1e-4), energy-only runs give the same energies, and the per-layer
+    schedule agrees."""
+    B = 2
+    edges = W.random_3regular_graph(n if n % 2 == 0 else n - 1, 700 + n)
+    gm, bt = W.qaoa_parameter_sets(p, B, 800 + n + p)
+    eng = gpu_lib.QAOA(n, edges, dtype, batch_max=B, renorm_every=R)
+    sch = eng.schedule()
+    assert sch["schedule"] == "chained" and sch["chained_available"]
+    E, dg, db = eng.run(gm, bt)
+    E1 = eng.run(gm, bt, grad=False)
+    eng.set_schedule("per_layer")
+    Ep, dgp, dbp = eng.run(gm, bt)
+    eng.close()
+    tol_e, tol_g = (1e-11, 1e-9) if dtype == "complex128" else (2e-6, 1e-4)
+    assert np.max(np.abs(E1 - E)) <= tol_e
+    assert np.max(np.abs(Ep - E)) <= tol_e
+    assert np.max(np.abs(dgp - dg)) <= tol_g and np.max(np.abs(dbp - db)) <= tol_g
+    if n <= 17:
+        Eo, dgo, dbo = oracle_batch(n, edges, gm, bt)
+        assert np.max(np.abs(E - Eo)) <= tol_e
+        assert np.max(np.abs(dg - dgo)) <= tol_g and np.max(np.abs(db - dbo)) <= tol_g
+
+
+def test_chained_energy_run_leaves_the_final_state(gpu_lib):
+    """An energy-only run on the chained schedule stores the final state."""
+    n, p = 13, 3
+    edges = W.random_3regular_graph(12, 21)
+    gm, bt = W.qaoa_parameter_sets(p, 2, 22)
+    eng = gpu_lib.QAOA(n, edges, "complex128", batch_max=2)
+    eng.run(gm, bt, grad=False)
+    for k in range(2):
+        assert np.max(np.abs(eng.state(k) - oq.qaoa_state(n, edges, gm[k], bt[k]))) <= 1e-12
+    eng.close()
