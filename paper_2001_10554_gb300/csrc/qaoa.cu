@@ -713,27 +713,66 @@ constexpr auto k_mixer_fast() {
     return k_mixer_fast_fwd<TR, C, PH>;
 }
 
-// Merged adjoint tile of the chained schedule: layer A's RX^dagger on the
-// tile's bits (gradient sums to partials), then layer A's adjoint phase (its
-// gradient term C Im(conj(lambda) phi) to partials_g, then conj(T[C]) on both
-// vectors), then layer B's RX^dagger on the same bits (sums to partials_b2).
-// Loads and stores follow mixer_fast_body: a high pass loads its first round
-// straight from HBM, the low pass stages its tile; the last round of layer B
-// writes straight to HBM.
-template <class TR, int C>
+// Tiles of the chained schedule that hold a layer boundary or the turnaround,
+// with the load and store scheme of mixer_fast_body (a high pass loads its
+// first round straight from HBM, the low pass stages its tile; the last round
+// writes straight to HBM):
+//   MODE kMgMerged: layer A's RX^dagger on the tile's bits (gradient sums to
+//     out.pA), layer A's adjoint phase (its gradient term C Im(conj(lambda)
+//     phi) to out.pG, then conj(T[C]) on both vectors), layer B's RX^dagger on
+//     the same bits (out.pB); phi and lambda stored.  complex64 may rescale on
+//     load and sum the stored norms (fused renormalisation, out.rn).
+//   MODE kMgLast: layer A's RX^dagger and the phase-gradient term only;
+//     nothing is stored (the last adjoint segment).
+//   MODE kMgTurn: phi only is loaded; layer A's RX on the tile's bits, then
+//     the turnaround (E to out.pE, |phi|^2 to out.pN, |lambda|^2 to out.pL,
+//     lambda = C phi), then RX^dagger of the same layer on both vectors (out.pB);
+//     only lambda is stored: phi equals the tile's input up to rounding.
+enum { kMgMerged = 0, kMgLast = 1, kMgTurn = 2 };
+
+struct MergedOut {
+  double* pA = nullptr;
+  double* pB = nullptr;
+  double* pG = nullptr;
+  double* pE = nullptr;
+  double* pN = nullptr;
+  double* pL = nullptr;
+  double* pRnP = nullptr;  // |phi|^2 and |lambda|^2 of the stored values (fused renormalisation), or NULL
+  double* pRnL = nullptr;
+  RenormFuse rn;           // rn.norms: rescale on load
+};
+
+template <class TR, int C, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_mixer_merged_adj(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
-                       const typename TR::RX* __restrict__ rxA, const typename TR::RX* __restrict__ rxB,
-                       double* __restrict__ partials, double* __restrict__ partials_b2,
-                       double* __restrict__ partials_g, int part_stride, unsigned* flag,
-                       const uint8_t* __restrict__ cut, const typename TR::PH* __restrict__ tables, int tsize,
-                       int per_graph) {
+    k_mixer_merged(typename TR::V* __restrict__ phi, typename TR::V* __restrict__ lam, uint64_t N, int s_bits,
+                   const typename TR::RX* __restrict__ rxA, const typename TR::RX* __restrict__ rxB,
+                   int part_stride, unsigned* flag, const uint8_t* __restrict__ cut,
+                   const typename TR::PH* __restrict__ tables, int tsize, int per_graph, const MergedOut out) {
   using W = typename TR::W;
   using PHT = typename TR::PH;
-  __shared__ PHT st[kEdgeChunk + 1];
+  constexpr bool kRn = MODE == kMgMerged && TR::kBlockSum;
+  constexpr bool ADJA = MODE != kMgTurn;  // layer A's rounds work on both vectors
+  __shared__ PHT st[MODE == kMgTurn ? 1 : kEdgeChunk + 1];
+  __shared__ float rn_f[2];
   cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
-  for (int i = threadIdx.x; i < tsize; i += blockDim.x) st[i] = TR::conj(tables[(uint64_t)blockIdx.y * tsize + i]);
+  if constexpr (MODE != kMgTurn)
+    for (int i = threadIdx.x; i < tsize; i += blockDim.x) st[i] = TR::conj(tables[(uint64_t)blockIdx.y * tsize + i]);
+  bool scale_in = false;
+  if constexpr (kRn) {
+    if (out.rn.norms) {
+      if (threadIdx.x == 0) {
+        const unsigned b = blockIdx.y;
+        const double np = out.rn.norms[b], tl = out.rn.norms[out.rn.stride + b];
+        const double tp = out.rn.norms[2 * out.rn.stride + b], nl = out.rn.norms[3 * out.rn.stride + b];
+        rn_f[0] = (float)(np > 0.0 ? sqrt(tp / np) : 1.0);
+        rn_f[1] = (float)(nl > 0.0 ? sqrt(tl / nl) : 1.0);
+      }
+      scale_in = true;
+    }
+  }
   __syncthreads();
+  const float f_phi = kRn && scale_in ? rn_f[0] : 1.f, f_lam = kRn && scale_in ? rn_f[1] : 1.f;
+  const bool norm_out = kRn && out.pRnP != nullptr;
   constexpr int K = TR::kTileBits;
   constexpr int M = K - C;
   constexpr unsigned T = 1u << K;
@@ -744,8 +783,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   const unsigned b = blockIdx.y;
   typename TR::V* P = phi + (uint64_t)b * N;
   typename TR::V* L = lam + (uint64_t)b * N;
-  const typename TR::RX kA = TR::rx_inv(rxA[b]);
-  const typename TR::RX kB = TR::rx_inv(rxB[b]);
+  const typename TR::RX kA = ADJA ? TR::rx_inv(rxA[b]) : rxA[b];
+  const typename TR::RX kB = MODE == kMgTurn ? TR::rx_inv(rxA[b]) : (MODE == kMgMerged ? TR::rx_inv(rxB[b]) : kA);
   const uint64_t tiles = N >> K;
   const unsigned tid = threadIdx.x;
   const int s = C == 0 ? 0 : s_bits;
@@ -759,44 +798,57 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int GB0 = M < R ? M : R;
   constexpr bool kDirect = C > 0;
   unsigned bad = 0;
-  dfx::Acc accA, accB, accg;
+  dfx::Acc accA, accB, accg, acce, accn, accl, rnp, rnl;
+  auto load_amp = [&](uint64_t x, W& av, W& yv) {
+    av = TR::load(P[x], bad);
+    if constexpr (kRn) {
+      if (scale_in) av = qops::scale_int(av, f_phi);
+    }
+    if constexpr (ADJA) {
+      yv = TR::load(L[x], bad);
+      if constexpr (kRn) {
+        if (scale_in) yv = qops::scale_int(yv, f_lam);
+      }
+    }
+  };
   for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
-    // layer A: every round, the first one loading from HBM (high pass) or from a staged tile (low pass)
+    // layer A: every round, the first one from HBM (high pass) or from a staged tile (low pass)
     if constexpr (!kDirect) {
 #pragma unroll
       for (unsigned i = 0; i < PER; ++i) {
         const unsigned l = tid + kThreads * i;
-        const uint64_t x = C <= 8 ? tbase + off0 + step * i : fast_x<C>(tbase, l, s);
-        sp[swz<TR>(l)] = TR::load(P[x], bad);
-        sl[swz<TR>(l)] = TR::load(L[x], bad);
+        W av, yv;
+        load_amp(C <= 8 ? tbase + off0 + step * i : fast_x<C>(tbase, l, s), av, yv);
+        sp[swz<TR>(l)] = av;
+        if (ADJA) sl[swz<TR>(l)] = yv;
       }
       __syncthreads();
-      mixer_rounds_to<TR, true, C, C, K>(sp, sl, kA, accA);
+      mixer_rounds_to<TR, ADJA, C, C, K>(sp, sl, kA, accA);
     } else {
       constexpr unsigned NSUB0 = 1u << (K - GB0);
       for (unsigned sb = tid; sb < NSUB0; sb += kThreads) {
         const unsigned base = block_base<C, GB0>(sb);
-        W a[1 << GB0], y[1 << GB0];
+        W a[1 << GB0], y[ADJA ? (1 << GB0) : 1];
 #pragma unroll
         for (int j = 0; j < (1 << GB0); ++j) {
-          const uint64_t x = fast_x<C>(tbase, base | ((unsigned)j << C), s);
-          a[j] = TR::load(P[x], bad);
-          y[j] = TR::load(L[x], bad);
+          W yv;
+          load_amp(fast_x<C>(tbase, base | ((unsigned)j << C), s), a[j], yv);
+          if (ADJA) y[ADJA ? j : 0] = yv;
         }
-        round_in_regs<TR, true, GB0>(a, y, kA, accA);
+        round_in_regs<TR, ADJA, GB0>(a, y, kA, accA);
         const unsigned sbase = swz<TR>(base);
 #pragma unroll
         for (int j = 0; j < (1 << GB0); ++j) {
           const unsigned idx = sbase ^ swz<TR>((unsigned)j << C);
           sp[idx] = a[j];
-          sl[idx] = y[j];
+          if (ADJA) sl[idx] = y[ADJA ? j : 0];
         }
       }
       __syncthreads();
-      mixer_rounds_to<TR, true, C, C + GB0, K>(sp, sl, kA, accA);
+      mixer_rounds_to<TR, ADJA, C, C + GB0, K>(sp, sl, kA, accA);
     }
-    // layer A's adjoint phase and its gradient term
+    // the element-wise step between the two layers
     {
       float gsum = 0.f;
 #pragma unroll
@@ -805,49 +857,89 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint64_t x = C <= 8 ? tbase + off0 + step * i : fast_x<C>(tbase, l, s);
         const unsigned idx = swz<TR>(l);
         const int c = cut[x];
-        const W xv = sp[idx], yv = sl[idx];
         const float cf = (float)c;
-        if constexpr (TR::kBlockSum) {
-          gsum = fmaf(cf, qops::im_conj_mul_fma(yv, xv, 0.f), gsum);
-        } else {
+        const W xv = sp[idx];
+        if constexpr (MODE == kMgTurn) {
           float pp, ee;
-          qops::im_conj_mul(yv, xv, pp, ee);
-          const float qq = cf * pp;
-          accg.add(qq, fmaf(cf, pp, -qq) + cf * ee);
+          qops::abs2(xv, pp, ee);
+          accn.add(pp, ee);
+          const float q = cf * pp;
+          acce.add(q, fmaf(cf, pp, -q) + cf * ee);
+          const float c2 = cf * cf;  // <= 255^2: exact
+          const float q2 = c2 * pp;
+          accl.add(q2, fmaf(c2, pp, -q2) + c2 * ee);
+          sl[idx] = qops::scale_int(xv, cf);
+        } else {
+          const W yv = sl[idx];
+          if constexpr (TR::kBlockSum) {
+            gsum = fmaf(cf, qops::im_conj_mul_fma(yv, xv, 0.f), gsum);
+          } else {
+            float pp, ee;
+            qops::im_conj_mul(yv, xv, pp, ee);
+            const float qq = cf * pp;
+            accg.add(qq, fmaf(cf, pp, -qq) + cf * ee);
+          }
+          if constexpr (MODE == kMgMerged) {
+            sp[idx] = TR::mul(st[c], xv);
+            sl[idx] = TR::mul(st[c], yv);
+          }
         }
-        sp[idx] = TR::mul(st[c], xv);
-        sl[idx] = TR::mul(st[c], yv);
       }
-      if (TR::kBlockSum) accg.add(gsum, 0.f);
+      if (MODE != kMgTurn && TR::kBlockSum) accg.add(gsum, 0.f);
     }
-    __syncthreads();
-    // layer B: rounds in shared memory, the last one straight to HBM
-    mixer_rounds_to<TR, true, C, C, POSL>(sp, sl, kB, accB);
-    constexpr unsigned NSUBL = 1u << (K - GBL);
-    for (unsigned sb = tid; sb < NSUBL; sb += kThreads) {
-      const unsigned base = block_base<POSL, GBL>(sb);
-      const unsigned sbase = swz<TR>(base);
-      W a[1 << GBL], y[1 << GBL];
+    if constexpr (MODE != kMgLast) {
+      __syncthreads();
+      // layer B: rounds in shared memory, the last one straight to HBM
+      mixer_rounds_to<TR, true, C, C, POSL>(sp, sl, kB, accB);
+      constexpr unsigned NSUBL = 1u << (K - GBL);
+      for (unsigned sb = tid; sb < NSUBL; sb += kThreads) {
+        const unsigned base = block_base<POSL, GBL>(sb);
+        const unsigned sbase = swz<TR>(base);
+        W a[1 << GBL], y[1 << GBL];
 #pragma unroll
-      for (int j = 0; j < (1 << GBL); ++j) {
-        const unsigned idx = sbase ^ swz<TR>((unsigned)j << POSL);
-        a[j] = sp[idx];
-        y[j] = sl[idx];
-      }
-      round_in_regs<TR, true, GBL>(a, y, kB, accB);
+        for (int j = 0; j < (1 << GBL); ++j) {
+          const unsigned idx = sbase ^ swz<TR>((unsigned)j << POSL);
+          a[j] = sp[idx];
+          y[j] = sl[idx];
+        }
+        round_in_regs<TR, true, GBL>(a, y, kB, accB);
 #pragma unroll
-      for (int j = 0; j < (1 << GBL); ++j) {
-        const uint64_t x = fast_x<C>(tbase, base | ((unsigned)j << POSL), s);
-        P[x] = TR::store(a[j]);
-        L[x] = TR::store(y[j]);
+        for (int j = 0; j < (1 << GBL); ++j) {
+          const uint64_t x = fast_x<C>(tbase, base | ((unsigned)j << POSL), s);
+          if constexpr (MODE == kMgMerged) {
+            if constexpr (kRn) {
+              if (norm_out) {
+                float pp, ee;
+                qops::abs2(a[j], pp, ee);
+                rnp.add(pp, ee);
+                qops::abs2(y[j], pp, ee);
+                rnl.add(pp, ee);
+              }
+            }
+            P[x] = TR::store(a[j]);
+          }
+          L[x] = TR::store(y[j]);
+        }
       }
     }
     __syncthreads();  // the next tile reuses shared memory
   }
   if (bad) atomicOr(flag, 1u);
-  block_partial(accA.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
-  block_partial(accB.value(), partials_b2 + (uint64_t)b * part_stride + blockIdx.x);
-  block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
+  const uint64_t row = (uint64_t)b * part_stride + blockIdx.x;
+  if (MODE != kMgTurn) block_partial(accA.value(), out.pA + row);
+  if (MODE != kMgLast) block_partial(accB.value(), out.pB + row);
+  if (MODE != kMgTurn) block_partial(accg.value(), out.pG + row);
+  if (MODE == kMgTurn) {
+    block_partial(acce.value(), out.pE + row);
+    block_partial(accn.value(), out.pN + row);
+    block_partial(accl.value(), out.pL + row);
+  }
+  if constexpr (kRn) {
+    if (norm_out) {
+      block_partial(rnp.value(), out.pRnP + row);
+      block_partial(rnl.value(), out.pRnL + row);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- chained segments
@@ -1260,9 +1352,16 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 constexpr uint32_t kMbarSpinLimit = 1u << 26;  // try_wait rounds before a wait is declared failed
 
-// PH = 3 (forward only, chained schedule): layer A's RX on the tile's bits,
-// then layer B's cost phase on every element, then layer B's RX (rx2) on the
-// same bits, in one tile residency.
+// Forward-only modes of the chained schedule:
+//   PH = 3: layer A's RX on the tile's bits, then layer B's cost phase on
+//           every element, then layer B's RX (rx2) on the same bits;
+//   PH = 4: RX, then the energy sums of the stored tile (sum C |phi|^2 to
+//           partials, |phi|^2 to partials_g): the last forward tile of an
+//           energy-only evaluation;
+//   PH = 5: the first tile of an evaluation: |+>^n (amplitude amp0) times the
+//           first cost phase is generated in shared memory, nothing is loaded.
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+
 template <class TR, bool ADJ, int C, int PH>
 __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ CUtensorMap tm_phi,
                                                         const __grid_constant__ CUtensorMap tm_lam, uint64_t N,
@@ -1271,8 +1370,9 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
                                                         const uint8_t* __restrict__ cut,
                                                         const typename TR::PH* __restrict__ tables, int tsize,
                                                         double* __restrict__ partials_g, unsigned* err, int per_graph,
-                                                        const typename TR::RX* __restrict__ rx2) {
-  static_assert(PH != 3 || !ADJ, "merged tiles of the TMA kernel are forward only");
+                                                        const typename TR::RX* __restrict__ rx2, double amp0) {
+  static_assert(PH < 3 || !ADJ, "merged, energy and generating tiles of the TMA kernel are forward only");
+  constexpr bool GEN = PH == 5;
   if (PH) cut += (uint64_t)(blockIdx.y / (unsigned)per_graph) * N;  // state b uses graph b / per_graph
   using TT = TmaTraits<TR>;
   using V = typename TR::V;
@@ -1293,7 +1393,7 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
   __shared__ PHT st[PH ? kEdgeChunk + 1 : 1];
   const unsigned tid = threadIdx.x;
   const unsigned b = blockIdx.y;
-  if (PH) {
+  if (PH && PH != 4) {
     for (int i = tid; i < tsize; i += blockDim.x) {
       const PHT tt = tables[(uint64_t)b * tsize + i];
       st[i] = PH == 2 ? TR::conj(tt) : tt;
@@ -1328,29 +1428,45 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
   unsigned phase0 = 0, phase1 = 0;
   unsigned bad = 0;
   dfx::Acc acc, accg;
+  V v0;
+  v0.x = (decltype(v0.x))amp0;
+  v0.y = 0;
+  const W w0 = TR::load(v0, bad);
   uint64_t t = blockIdx.x;
-  if (t < tiles && tid == 0) issue(t, 0);
+  if (!GEN && t < tiles && tid == 0) issue(t, 0);
   for (int it = 0; t < tiles; ++it, t += gridDim.x) {
     const int buf = it & 1;
     const uint64_t tn = t + gridDim.x;
-    if (tid == 0 && tn < tiles) {
-      bulk_wait_read0();  // the other buffer's previous store has read its shared memory
-      fence_proxy_async();
-      issue(tn, buf ^ 1);
-    }
-    unsigned& ph = buf ? phase1 : phase0;
-    bool ok = false;
-    for (uint32_t spin = 0; spin < kMbarSpinLimit; ++spin)
-      if (mbar_try_wait(&mbar[buf], ph)) { ok = true; break; }
-    ph ^= 1u;
-    if (__syncthreads_or(!ok)) {  // a tile never arrived: report and leave
-      if (tid == 0) atomicOr(err, 1u);
-      break;
-    }
     W* sp = reinterpret_cast<W*>(vbuf(buf, 0));
     W* sl = ADJ ? reinterpret_cast<W*>(vbuf(buf, 1)) : nullptr;
     const uint64_t tbase = C == 0 ? (t << K) : (((t >> mid) << (s + M)) | ((t & ((1ull << mid) - 1ull)) << C));
-    if (CONVERT || PH == 1) {
+    if constexpr (GEN) {
+      if (tid == 0) bulk_wait_read1();  // the store from this buffer two tiles ago has read its shared memory
+      __syncthreads();
+#pragma unroll
+      for (unsigned i = 0; i < PER; ++i) {
+        const unsigned l = tid + kThreads * i;
+        const uint64_t x = tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
+        sp[swz<TT>(l)] = TR::mul(st[cut[x]], w0);
+      }
+      __syncthreads();
+    } else {
+      if (tid == 0 && tn < tiles) {
+        bulk_wait_read0();  // the other buffer's previous store has read its shared memory
+        fence_proxy_async();
+        issue(tn, buf ^ 1);
+      }
+      unsigned& ph = buf ? phase1 : phase0;
+      bool ok = false;
+      for (uint32_t spin = 0; spin < kMbarSpinLimit; ++spin)
+        if (mbar_try_wait(&mbar[buf], ph)) { ok = true; break; }
+      ph ^= 1u;
+      if (__syncthreads_or(!ok)) {  // a tile never arrived: report and leave
+        if (tid == 0) atomicOr(err, 1u);
+        break;
+      }
+    }
+    if (!GEN && (CONVERT || PH == 1)) {
 #pragma unroll
       for (unsigned i = 0; i < PER; ++i) {
         const unsigned l = tid + kThreads * i;
@@ -1377,7 +1493,7 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
       __syncthreads();
       mixer_rounds<TT, ADJ, C, C>(sp, sl, rx2[b], acc);
     }
-    if (CONVERT || PH == 2) {
+    if (CONVERT || PH == 2 || PH == 4) {
       float gsum = 0.f;
 #pragma unroll
       for (unsigned i = 0; i < PER; ++i) {
@@ -1385,6 +1501,15 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
         const unsigned idx = swz<TT>(l);
         W xv = sp[idx];
         W yv = ADJ ? sl[idx] : xv;
+        if (PH == 4) {
+          const uint64_t x = tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
+          const float cf = (float)cut[x];
+          float pp, ee;
+          qops::abs2(xv, pp, ee);
+          accg.add(pp, ee);  // |phi|^2
+          const float q = cf * pp;
+          acc.add(q, fmaf(cf, pp, -q) + cf * ee);  // C |phi|^2 (forward RX rounds add nothing to acc)
+        }
         if (PH == 2) {
           const uint64_t x = tbase + (((uint64_t)(l >> C)) << s) + (l & ((1u << C) - 1u));
           const int c = cut[x];
@@ -1418,8 +1543,8 @@ __global__ void __launch_bounds__(kThreads) k_mixer_tma(const __grid_constant__ 
   if (tid == 0) bulk_wait0();
   __syncthreads();
   if (bad) atomicOr(flag, 1u);
-  if (ADJ) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
-  if (PH == 2) block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
+  if (ADJ || PH == 4) block_partial(acc.value(), partials + (uint64_t)b * part_stride + blockIdx.x);
+  if (PH == 2 || PH == 4) block_partial(accg.value(), partials_g + (uint64_t)b * part_stride + blockIdx.x);
 }
 
 // Cost phase: psi_x <- T_b[C(x)] psi_x.  When ADJ: accumulate Im conj(lambda) C phi
@@ -1679,6 +1804,7 @@ struct PhaseFuse {
   // adjoint: layer B's gradient sums go to partials_b2
   const typename TR::RX* rx2 = nullptr;
   double* partials_b2 = nullptr;
+  double amp0 = 0.0;  // mode 5: amplitude of |+>^n
 };
 
 template <class TR, bool ADJ, int C>
@@ -1766,7 +1892,7 @@ void launch_tma1(dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename T
                  unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta) {
   k_mixer_tma<TR, ADJ, C, PH><<<grid, kThreads, tma_smem<TR>(ADJ), s>>>(
       *ta.phi, ADJ ? *ta.lam : *ta.phi, N, sb, ta.hi_bits, rx, partials, ps, flag, f.cut, f.tables, f.tsize,
-      f.partials_g, ta.err, f.per_graph, f.rx2);
+      f.partials_g, ta.err, f.per_graph, f.rx2, f.amp0);
 }
 
 template <class TR, bool ADJ, int C>
@@ -1774,6 +1900,10 @@ void launch_tma_c(dim3 grid, cudaStream_t s, uint64_t N, int sb, const typename 
                   unsigned* flag, const PhaseFuse<TR>& f, const TmaArgs& ta) {
   if (!ADJ && f.mode == 3)
     launch_tma1<TR, ADJ, C, ADJ ? 0 : 3>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
+  else if (!ADJ && f.mode == 4)
+    launch_tma1<TR, ADJ, C, ADJ ? 0 : 4>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
+  else if (!ADJ && f.mode == 5)
+    launch_tma1<TR, ADJ, C, ADJ ? 0 : 5>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
   else if (!ADJ && f.mode == 1 && C == 0)
     launch_tma1<TR, ADJ, C, (!ADJ && C == 0) ? 1 : 0>(grid, s, N, sb, rx, partials, ps, flag, f, ta);
   else if (ADJ && f.mode == 2)
@@ -1801,6 +1931,8 @@ cudaError_t set_tma_attrs_c(std::integer_sequence<int, Cs...>) {
   ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, 0>, a, bytes) : e), ...);
   if (ADJ) ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, ADJ ? 2 : 0>, a, bytes) : e), ...);
   if (!ADJ) ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, ADJ ? 0 : 3>, a, bytes) : e), ...);
+  if (!ADJ) ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, ADJ ? 0 : 4>, a, bytes) : e), ...);
+  if (!ADJ) ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_tma<TR, ADJ, Cs + TR::kRowBits, ADJ ? 0 : 5>, a, bytes) : e), ...);
   return e;
 }
 
@@ -1810,6 +1942,8 @@ cudaError_t set_tma_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 0>, a, (int)tma_smem<TR>(false));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 1>, a, (int)tma_smem<TR>(false));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 3>, a, (int)tma_smem<TR>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 4>, a, (int)tma_smem<TR>(false));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, false, 0, 5>, a, (int)tma_smem<TR>(false));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, true, 0, 0>, a, (int)tma_smem<TR>(true));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mixer_tma<TR, true, 0, 2>, a, (int)tma_smem<TR>(true));
   const auto seq = std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{};
@@ -2057,39 +2191,37 @@ bool chain_available(const iqs_qaoa* q) {
   return true;
 }
 
-template <class TR, int C>
-void launch_merged_adj1(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam,
-                        uint64_t N, int sb, const typename TR::RX* rxA, const typename TR::RX* rxB, double* pA,
-                        double* pB, double* pG, int ps, unsigned* flag, const uint8_t* cut,
-                        const typename TR::PH* tab, int tsize, int per_graph) {
-  k_mixer_merged_adj<TR, C><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rxA, rxB, pA, pB, pG, ps, flag, cut, tab,
-                                                         tsize, per_graph);
+template <class TR, int MODE, int C>
+void launch_merged1(dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam, uint64_t N,
+                    int sb, const typename TR::RX* rxA, const typename TR::RX* rxB, int ps, unsigned* flag,
+                    const uint8_t* cut, const typename TR::PH* tab, int tsize, int per_graph, const MergedOut& out) {
+  k_mixer_merged<TR, C, MODE><<<grid, kThreads, smem, s>>>(phi, lam, N, sb, rxA, rxB, ps, flag, cut, tab, tsize,
+                                                           per_graph, out);
 }
 
-template <class TR, int... Cs>
-void dispatch_merged_adj(int c, dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam,
-                         uint64_t N, int sb, const typename TR::RX* rxA, const typename TR::RX* rxB, double* pA,
-                         double* pB, double* pG, int ps, unsigned* flag, const uint8_t* cut,
-                         const typename TR::PH* tab, int tsize, int per_graph, std::integer_sequence<int, Cs...>) {
+template <class TR, int MODE, int... Cs>
+void dispatch_merged(int c, dim3 grid, size_t smem, cudaStream_t s, typename TR::V* phi, typename TR::V* lam,
+                     uint64_t N, int sb, const typename TR::RX* rxA, const typename TR::RX* rxB, int ps,
+                     unsigned* flag, const uint8_t* cut, const typename TR::PH* tab, int tsize, int per_graph,
+                     const MergedOut& out, std::integer_sequence<int, Cs...>) {
   if (c == 0) {
-    launch_merged_adj1<TR, 0>(grid, smem, s, phi, lam, N, sb, rxA, rxB, pA, pB, pG, ps, flag, cut, tab, tsize,
-                              per_graph);
+    launch_merged1<TR, MODE, 0>(grid, smem, s, phi, lam, N, sb, rxA, rxB, ps, flag, cut, tab, tsize, per_graph, out);
     return;
   }
   bool done = false;
   ((c == Cs + TR::kRowBits && !done
-        ? (launch_merged_adj1<TR, Cs + TR::kRowBits>(grid, smem, s, phi, lam, N, sb, rxA, rxB, pA, pB, pG, ps, flag,
-                                                     cut, tab, tsize, per_graph),
+        ? (launch_merged1<TR, MODE, Cs + TR::kRowBits>(grid, smem, s, phi, lam, N, sb, rxA, rxB, ps, flag, cut, tab,
+                                                       tsize, per_graph, out),
            done = true)
         : false),
    ...);
 }
 
-template <class TR, int... Cs>
+template <class TR, int MODE, int... Cs>
 cudaError_t set_merged_attrs_c(int bytes, std::integer_sequence<int, Cs...>) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_mixer_merged_adj<TR, 0>, a, bytes);
-  ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_merged_adj<TR, Cs + TR::kRowBits>, a, bytes) : e), ...);
+  cudaError_t e = cudaFuncSetAttribute(k_mixer_merged<TR, 0, MODE>, a, bytes);
+  ((e = e == cudaSuccess ? cudaFuncSetAttribute(k_mixer_merged<TR, Cs + TR::kRowBits, MODE>, a, bytes) : e), ...);
   return e;
 }
 
@@ -2131,7 +2263,9 @@ cudaError_t set_seg_attrs() {
   const int one = (1 << TR::kTileBits) * (int)sizeof(typename TR::W);
   cudaError_t e = set_seg_attrs_c<TR, false>(one, seq);
   if (e == cudaSuccess) e = set_seg_attrs_c<TR, true>(2 * one, seq);
-  if (e == cudaSuccess) e = set_merged_attrs_c<TR>(2 * one, seq);
+  if (e == cudaSuccess) e = set_merged_attrs_c<TR, kMgMerged>(2 * one, seq);
+  if (e == cudaSuccess) e = set_merged_attrs_c<TR, kMgLast>(2 * one, seq);
+  if (e == cudaSuccess) e = set_merged_attrs_c<TR, kMgTurn>(2 * one, seq);
   return e;
 }
 
@@ -2221,25 +2355,53 @@ cudaError_t enqueue_chain(iqs_qaoa* q, int B, int p, bool grad, int* n_launches)
     const auto seq = std::make_integer_sequence<int, TR::kTileBits - TR::kRowBits>{};
     const int nop = (int)sg.ops.size();
     const bool plain = (fl & (kSegGen | kSegRnScale | kSegRnSum)) == 0 && !sg.has_turn;
-    const bool single = plain && nop == 1 && sg.ops[0].kind == kOpRX;
-    const bool merged = plain && nop == 3 && sg.ops[0].kind == kOpRX && sg.ops[1].kind == kOpPhase &&
-                        sg.ops[2].kind == kOpRX;
+    const bool rn_ok = std::is_same<TR, T64>::value;  // fused renormalisation in the tuned kernels: complex64
+    const bool no_gen = (fl & kSegGen) == 0;
+    const bool single = nop == 1 && sg.ops[0].kind == kOpRX;
+    const bool merged = nop == 3 && sg.ops[0].kind == kOpRX && sg.ops[1].kind == kOpPhase && sg.ops[2].kind == kOpRX;
+    const bool turn3 = nop == 3 && sg.ops[0].kind == kOpRX && sg.ops[1].kind == kOpTurn && sg.ops[2].kind == kOpRX;
+    const bool last2 = nop == 2 && sg.ops[0].kind == kOpRX && sg.ops[1].kind == kOpPhase;
     const size_t tsz = (size_t)(q->n_edges + 1);
+    auto col = [&](int o) { return q->partials + (size_t)P.ops[o].col * gx; };
     TmaArgs ta;
     ta.use = q->tma_ok && q->tma_mode >= 1;
     ta.phi = &q->tm_phi[sg.geo];
     ta.lam = &q->tm_lam[sg.geo];
     ta.hi_bits = q->n - g.s - g.m;
     ta.err = q->tma_err;
-    if (single && !sg.adj_in) {
-      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)sg.ops[0].layer * q->bmax, nullptr, 0,
-                              q->flag, PhaseFuse<TR>(), ta);
-    } else if (single && sg.adj_in && !last) {
+    const typename TR::RX* rx0 = rx + (uint64_t)sg.ops[0].layer * q->bmax;
+    const bool first2 = nop == 2 && sg.ops[0].kind == kOpPhase && sg.ops[1].kind == kOpRX;
+    const bool energy2 = nop == 2 && sg.ops[0].kind == kOpRX && sg.ops[1].kind == kOpEnergy;
+    if (plain && single && !sg.adj_in) {
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx0, nullptr, 0, q->flag, PhaseFuse<TR>(), ta);
+    } else if (ta.use && first2 && (fl & ~(uint32_t)(kSegGen | kSegStorePhi)) == 0 && (fl & kSegGen)) {
+      PhaseFuse<TR> f;
+      f.mode = 5;
+      f.cut = q->cut;
+      f.per_graph = q->per_graph;
+      f.tables = tab + (uint64_t)sg.ops[0].layer * q->bmax * tsz;
+      f.tsize = (int)tsz;
+      f.amp0 = P.amp64;
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)sg.ops[1].layer * q->bmax, nullptr, 0,
+                              q->flag, f, ta);
+    } else if (ta.use && energy2 && fl == kSegStorePhi) {
+      PhaseFuse<TR> f;
+      f.mode = 4;
+      f.cut = q->cut;
+      f.per_graph = q->per_graph;
+      f.partials_g = q->partials + (size_t)(E0 + 1) * gx;
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx0, q->partials + (size_t)E0 * gx, ps, q->flag, f, ta);
+    } else if (single && sg.adj_in && !last && no_gen && (fl & kSegRnSum) == 0 &&
+               ((fl & kSegRnScale) == 0 || rn_ok)) {
+      PhaseFuse<TR> f;
+      if (fl & kSegRnScale) {
+        f.rn.norms = q->norms;
+        f.rn.stride = q->bmax;
+      }
       TmaArgs tadj = ta;
-      tadj.use = q->tma_ok && q->tma_mode >= 2;
-      launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx + (uint64_t)sg.ops[0].layer * q->bmax,
-                             q->partials + (size_t)P.ops[0].col * gx, ps, q->flag, PhaseFuse<TR>(), tadj);
-    } else if (merged && !sg.adj_in && ta.use) {
+      tadj.use = q->tma_ok && q->tma_mode >= 2 && (fl & kSegRnScale) == 0;
+      launch_mixer<TR, true>(g, grid, s, phi, lam, N, rx0, col(0), ps, q->flag, f, tadj);
+    } else if (plain && merged && !sg.adj_in && ta.use) {
       PhaseFuse<TR> f;
       f.mode = 3;
       f.cut = q->cut;
@@ -2247,14 +2409,37 @@ cudaError_t enqueue_chain(iqs_qaoa* q, int B, int p, bool grad, int* n_launches)
       f.tables = tab + (uint64_t)sg.ops[1].layer * q->bmax * tsz;
       f.tsize = (int)tsz;
       f.rx2 = rx + (uint64_t)sg.ops[2].layer * q->bmax;
-      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx + (uint64_t)sg.ops[0].layer * q->bmax, nullptr, 0,
-                              q->flag, f, ta);
-    } else if (merged && sg.adj_in && !last) {
-      dispatch_merged_adj<TR>(g.c, grid, smem, s, phi, lam, N, g.s, rx + (uint64_t)sg.ops[0].layer * q->bmax,
-                              rx + (uint64_t)sg.ops[2].layer * q->bmax, q->partials + (size_t)P.ops[0].col * gx,
-                              q->partials + (size_t)P.ops[2].col * gx, q->partials + (size_t)P.ops[1].col * gx, ps,
-                              q->flag, q->cut, tab + (uint64_t)sg.ops[0].layer * q->bmax * tsz, (int)tsz,
-                              q->per_graph, seq);
+      launch_mixer<TR, false>(g, grid, s, phi, nullptr, N, rx0, nullptr, 0, q->flag, f, ta);
+    } else if (merged && sg.adj_in && !last && no_gen && ((fl & (kSegRnScale | kSegRnSum)) == 0 || rn_ok)) {
+      MergedOut mo;
+      mo.pA = col(0);
+      mo.pG = col(1);
+      mo.pB = col(2);
+      if (fl & kSegRnScale) {
+        mo.rn.norms = q->norms;
+        mo.rn.stride = q->bmax;
+      }
+      if (fl & kSegRnSum) {
+        mo.pRnP = q->partials + (size_t)(E0 + 3) * gx;
+        mo.pRnL = q->partials + (size_t)(E0 + 4) * gx;
+      }
+      dispatch_merged<TR, kMgMerged>(g.c, grid, smem, s, phi, lam, N, g.s, rx0,
+                                     rx + (uint64_t)sg.ops[2].layer * q->bmax, ps, q->flag, q->cut,
+                                     tab + (uint64_t)sg.ops[0].layer * q->bmax * tsz, (int)tsz, q->per_graph, mo, seq);
+    } else if (last2 && sg.adj_in && last && no_gen && (fl & (kSegRnScale | kSegRnSum)) == 0) {
+      MergedOut mo;
+      mo.pA = col(0);
+      mo.pG = col(1);
+      dispatch_merged<TR, kMgLast>(g.c, grid, smem, s, phi, lam, N, g.s, rx0, rx0, ps, q->flag, q->cut,
+                                   tab + (uint64_t)sg.ops[0].layer * q->bmax * tsz, (int)tsz, q->per_graph, mo, seq);
+    } else if (turn3 && !sg.adj_in && !last && no_gen && (fl & (kSegRnScale | kSegRnSum)) == 0) {
+      MergedOut mo;
+      mo.pB = col(2);
+      mo.pE = q->partials + (size_t)E0 * gx;
+      mo.pN = q->partials + (size_t)(E0 + 1) * gx;
+      mo.pL = q->partials + (size_t)(E0 + 2) * gx;
+      dispatch_merged<TR, kMgTurn>(g.c, grid, smem, s, phi, lam, N, g.s, rx0, rx0, ps, q->flag, q->cut, tab,
+                                   (int)tsz, q->per_graph, mo, seq);
     } else if (anyadj) {
       dispatch_seg<TR, true>(g.c, grid, smem, s, phi, lam, N, g.s, rx, tab, q->cut, q->partials, ps, q->norms,
                              q->flag, P, seq);
