@@ -75,13 +75,16 @@ typedef enum {
  * stream).  n in [1, IQS_MAX_QUBITS].  Errors: IQS_EINVAL, IQS_ENOMEM, IQS_ECUDA. */
 iqs_status iqs_create(int n, int dtype, void* stream, iqs_reg** out);
 
-/* Same as iqs_create but borrows ``device_ptr`` (2^n amplitudes of ``dtype``,
+/* Section 2 "Scope and basic use" (QubitRegister holds the state), with the
+ * storage supplied by the caller; the paper has no call of this form.  Same as
+ * iqs_create but borrows ``device_ptr`` (2^n amplitudes of ``dtype``,
  * 16-byte aligned, on the current device), e.g. a torch tensor's storage.
  * The contents are not modified; iqs_destroy never frees the borrowed buffer,
  * and the caller keeps it alive while the register exists. */
 iqs_status iqs_wrap(int n, int dtype, void* device_ptr, void* stream, iqs_reg** out);
 
-/* Frees what the register owns (synchronising its stream first).  NULL is OK. */
+/* End of a QubitRegister's lifetime (Section 2 "Scope and basic use"): frees
+ * what the register owns (synchronising its stream first).  NULL is OK. */
 iqs_status iqs_destroy(iqs_reg* reg);
 
 /* Device address of the amplitudes, number of qubits, dtype. */
@@ -152,7 +155,8 @@ iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U)
  * i with bit q set (the raw sum; the state is not renormalised first). */
 iqs_status iqs_probability(iqs_reg* reg, int q, double* out);
 
-/* GetProbability for every qubit in one read of the state: out[q] for q in [0, n). */
+/* Section 2 "Scope and basic use", GetProbability for every qubit in one
+ * read of the state: out[q] for q in [0, n). */
 iqs_status iqs_probabilities(iqs_reg* reg, double* out);
 
 /* Section 2 "Scope and basic use": expectation of a product of Pauli matrices,
@@ -160,8 +164,10 @@ iqs_status iqs_probabilities(iqs_reg* reg, double* out);
  * {I, X, Y, Z}; character k acts on qubit k. */
 iqs_status iqs_expectation(iqs_reg* reg, const char* pauli, double* out);
 
-/* The same by bit masks: bit k of ``xmask`` and ``zmask`` marks an X (x only),
- * Z (z only) or Y (both) on qubit k.  Bits at or above n must be zero. */
+/* Section 2 "Scope and basic use" (expectation of a product of Pauli
+ * matrices), the product given by bit masks: bit k of ``xmask`` and ``zmask``
+ * marks an X (x only), Z (z only) or Y (both) on qubit k.  Bits at or above n
+ * must be zero. */
 iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, double* out);
 
 /* Section 2 "Scope and basic use": measuring qubits in groups gives the joint
@@ -184,10 +190,14 @@ iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out);
  * device memory: N / 256 + 2 N / 65536 doubles plus 16 bytes per shot. */
 iqs_status iqs_sample(iqs_reg* reg, uint64_t shots, const double* uniforms, uint64_t* out);
 
-/* Squared norm sum_i |alpha_i|^2. */
+/* Squared norm sum_i |alpha_i|^2: the sum of all outcome probabilities of
+ * Section 2's GetProbability over the basis states, 1 for a normalised state. */
 iqs_status iqs_norm2(iqs_reg* reg, double* out);
 
-/* psi <- psi / ||psi|| (norm accumulated in FP64); IQS_EINVAL for a zero state. */
+/* psi <- psi / ||psi|| (norm accumulated in FP64); IQS_EINVAL for a zero state.
+ * The paper names no renormalisation call: its probabilities (Section 2,
+ * GetProbability) assume a unit-norm state, which this restores after rounding
+ * has moved the norm (complex64 gates, long circuits). */
 iqs_status iqs_renormalize(iqs_reg* reg);
 
 /* Section 4: <H_MaxCut> = sum_x C(x) |alpha_x|^2 with C as in iqs_apply_zz_phase. */
@@ -231,7 +241,9 @@ iqs_status iqs_qaoa_set_options(iqs_qaoa* q, int renorm_every, int use_graphs);
  * passes up to 14 qubits and is slower at 16 and 18, hence the default.) */
 iqs_status iqs_qaoa_set_engine(iqs_qaoa* q, int engine);
 
-/* Evaluate ``batch`` parameter sets of depth p (1..64).  Host arrays,
+/* Section 4's L(theta) and its adjoint gradient for a pool of parameter sets
+ * (Section 2, "Pool of multiple states").
+ * Evaluate ``batch`` parameter sets of depth p (1..64).  Host arrays,
  * row-major [batch][p]: gammas, betas.  Outputs (host): energies[batch] and,
  * when both are non-NULL, grad_gammas[batch][p] and grad_betas[batch][p].
  * Energies and gradients are divided by the computed state's squared norm
@@ -242,6 +254,27 @@ iqs_status iqs_qaoa_set_engine(iqs_qaoa* q, int engine);
  * Synchronous.  IQS_ERANGE if a complex128 amplitude left the emulated range. */
 iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, const double* betas,
                         double* energies, double* grad_gammas, double* grad_betas);
+
+/* Stream-ordered variant of iqs_qaoa_run for callers whose parameters and
+ * results live in device memory (a training loop, a batched optimiser): the
+ * same evaluation (Section 4's L(theta) and its adjoint gradient for a pool of
+ * parameter sets), enqueued on the workspace's stream without any host
+ * synchronisation or host copy.  ``d_gammas`` and ``d_betas`` are DEVICE
+ * arrays [batch][p]; the outputs ``d_energies`` [batch] and, when both are
+ * non-NULL, ``d_grad_gammas`` and ``d_grad_betas`` [batch][p] are DEVICE
+ * arrays written on the stream.  The RX coefficients and phase tables are
+ * built on the device from the parameters (FP64).  Every pointer must stay
+ * valid until the stream has passed the call.  Non-finite parameters are not
+ * checked (they give non-finite results); a complex128 range error or a TMA
+ * wait that gave up is reported by iqs_qaoa_synchronize.  IQS_EINVAL for bad
+ * sizes or NULL outputs, IQS_ECUDA for a failed launch. */
+iqs_status iqs_qaoa_run_async(iqs_qaoa* q, int batch, int p, const double* d_gammas, const double* d_betas,
+                              double* d_energies, double* d_grad_gammas, double* d_grad_betas);
+
+/* Block until the workspace's stream is idle; IQS_ERANGE if a complex128
+ * amplitude left the emulated range, IQS_ETIMEOUT if a TMA wait gave up, in
+ * the evaluations since the last check (the flags are cleared). */
+iqs_status iqs_qaoa_synchronize(iqs_qaoa* q);
 
 /* Project autotuner: times TMA staging (off / forward / forward + adjoint),
  * then the candidate mixer tile shapes (the row width of the high passes,
@@ -384,7 +417,9 @@ iqs_status iqs_pool_set_noise_t1t2(iqs_pool* p, double T1, double T2, double gat
  * rounding of the dtype (the gates are grouped differently). */
 iqs_status iqs_pool_set_engine(iqs_pool* p, int engine);
 
-/* Run ``batch`` trajectories from |0...0>.  ``unitaries``: host doubles
+/* Section 2 "Pool of multiple states": run ``batch`` trajectories of one
+ * brick circuit from |0...0>, each with its own noise rotations, and average
+ * P(q = 1) over the pool.  ``unitaries``: host doubles
  * [depth][n][8] (each U row-major as (re, im) pairs).  ``angles``: host
  * doubles [batch][iqs_pool_noise_count(n, depth)][2] = (tx, tz) in the order
  * the rotations occur (layer by layer: the one-qubit gates q = 0..n-1, then
@@ -397,6 +432,21 @@ iqs_status iqs_pool_set_engine(iqs_pool* p, int engine);
  * the captured graphs.  A pool on the legacy default stream launches directly. */
 iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* unitaries, const double* angles,
                               double* probs, double* mean);
+
+/* Stream-ordered variant of iqs_pool_run_brick (Section 2 "Pool of multiple
+ * states"; the same circuit family, noise model and results) for inputs and
+ * outputs in device memory: ``d_unitaries`` [depth][n][8] and ``d_angles``
+ * (pairs or T1/T2 triples per trajectory, or NULL) are DEVICE arrays, copied
+ * on the pool's stream into its buffers; ``d_probs`` [batch][n] (or NULL) and
+ * ``d_mean`` [n] are DEVICE arrays written on the stream.  No host
+ * synchronisation; every pointer must stay valid until the stream has passed
+ * the call.  A complex128 range error is reported by iqs_pool_synchronize. */
+iqs_status iqs_pool_run_brick_async(iqs_pool* p, int batch, int depth, const double* d_unitaries,
+                                    const double* d_angles, double* d_probs, double* d_mean);
+
+/* Block until the pool's stream is idle; IQS_ERANGE if a complex128 amplitude
+ * left the emulated range since the last check (the flag is cleared). */
+iqs_status iqs_pool_synchronize(iqs_pool* p);
 
 /* Copy trajectory ``index``'s final state to host memory. */
 iqs_status iqs_pool_download_state(iqs_pool* p, int index, void* host, size_t bytes);

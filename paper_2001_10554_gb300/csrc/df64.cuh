@@ -32,7 +32,7 @@ struct Coef {
   float h, l, h52;
 };
 
-inline Coef make_coef(double c) {
+__host__ __device__ inline Coef make_coef(double c) {
   Coef r;
   r.h = (float)c;
   r.l = (float)(c - (double)r.h);

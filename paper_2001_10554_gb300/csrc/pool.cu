@@ -412,6 +412,14 @@ iqs_status iqs_pool_create(int n, int dtype, int batch_max, int depth_max, void*
   }
   cudaError_t e = cudaMemsetAsync(p->flag, 0, sizeof(unsigned), p->stream);
   if (e == cudaSuccess) e = dtype == IQS_C128 ? set_pool_attrs<P128>() : set_pool_attrs<P64>();
+  // index of each layer's first noise rotation: depends on n and the layer only, so it is built once
+  std::vector<int> base(depth_max);
+  for (int l = 0, k = 0; l < depth_max; ++l) {
+    base[l] = k;
+    k += n + 2 * ((n - (l & 1)) / 2);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->layer_base, base.data(), sizeof(int) * (size_t)depth_max, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_pool(p);
     return report(IQS_ECUDA, "pool set-up: %s", cudaGetErrorString(e));
@@ -468,15 +476,8 @@ iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* u
   if (unitaries == nullptr || mean == nullptr) return report(IQS_EINVAL, "unitaries and mean must not be NULL");
   if (fault_now(2)) return report(IQS_ECUDA, "iqs_pool_run_brick: injected launch failure");
   const int nn = n_noise_ops(p->n, depth);
-  std::vector<int> base(depth);
-  for (int l = 0, k = 0; l < depth; ++l) {
-    base[l] = k;
-    k += p->n + 2 * ((p->n - (l & 1)) / 2);
-  }
   cudaStream_t s = p->stream;
   cudaError_t e = cudaMemcpyAsync(p->U, unitaries, sizeof(double) * 8 * (size_t)p->n * depth, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(p->layer_base, base.data(), sizeof(int) * depth, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && angles)
     e = cudaMemcpyAsync(p->angles, angles, sizeof(double) * (p->noise_model == 1 ? 3 : 2) * (size_t)nn * batch,
                         cudaMemcpyHostToDevice, s);
@@ -492,6 +493,45 @@ iqs_status iqs_pool_run_brick(iqs_pool* p, int batch, int depth, const double* u
   if (e != cudaSuccess) return report(IQS_ECUDA, "pool results: %s", cudaGetErrorString(e));
   if (f) {
     cudaMemsetAsync(p->flag, 0, sizeof(unsigned), s);
+    return report(IQS_ERANGE, "an amplitude outside the emulated-FP64 range was met");
+  }
+  return IQS_OK;
+}
+
+iqs_status iqs_pool_run_brick_async(iqs_pool* p, int batch, int depth, const double* d_unitaries,
+                                    const double* d_angles, double* d_probs, double* d_mean) {
+  using namespace iqs;
+  if (p == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (batch < 1 || batch > p->bmax) return report(IQS_EINVAL, "batch %d outside [1, %d]", batch, p->bmax);
+  if (depth < 1 || depth > p->depth_max) return report(IQS_EINVAL, "depth %d outside [1, %d]", depth, p->depth_max);
+  if (d_unitaries == nullptr || d_mean == nullptr) return report(IQS_EINVAL, "unitaries and mean must not be NULL");
+  if (fault_now(2)) return report(IQS_ECUDA, "iqs_pool_run_brick_async: injected launch failure");
+  const int nn = n_noise_ops(p->n, depth);
+  cudaStream_t s = p->stream;
+  cudaError_t e = cudaMemcpyAsync(p->U, d_unitaries, sizeof(double) * 8 * (size_t)p->n * depth,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && d_angles)
+    e = cudaMemcpyAsync(p->angles, d_angles, sizeof(double) * (p->noise_model == 1 ? 3 : 2) * (size_t)nn * batch,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = p->dtype == IQS_C128 ? run_pool<P128>(p, batch, depth, d_angles != nullptr)
+                             : run_pool<P64>(p, batch, depth, d_angles != nullptr);
+  if (e == cudaSuccess && d_probs)
+    e = cudaMemcpyAsync(d_probs, p->probs, sizeof(double) * (size_t)p->n * batch, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_mean, p->mean, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return report(IQS_ECUDA, "pool asynchronous launch: %s", cudaGetErrorString(e));
+  return IQS_OK;
+}
+
+iqs_status iqs_pool_synchronize(iqs_pool* p) {
+  using namespace iqs;
+  if (p == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  unsigned f = 0;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&f, p->flag, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return report(IQS_ECUDA, "pool synchronize: %s", cudaGetErrorString(e));
+  if (f) {
+    cudaMemset(p->flag, 0, sizeof(unsigned));
     return report(IQS_ERANGE, "an amplitude outside the emulated-FP64 range was met");
   }
   return IQS_OK;

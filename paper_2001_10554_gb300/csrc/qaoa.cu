@@ -2495,6 +2495,59 @@ cudaError_t enqueue_any(iqs_qaoa* q, int B, int p, bool grad, int* n_launches) {
   return q->dtype == IQS_C128 ? enqueue<T128>(q, B, p, grad, n_launches) : enqueue<T64>(q, B, p, grad, n_launches);
 }
 
+// Device-side parameter tables (iqs_qaoa_run_async): the same FP64-built RX
+// coefficients and exp(-i gamma k) tables as fill_params_c64/c128, from
+// parameter arrays in device memory ([batch][p] each).  One thread per
+// (layer, state, table entry); entry tsize holds the RX coefficients.
+__device__ __forceinline__ void put_params(float2* rx, float2* tab, uint64_t i_rx, uint64_t i_tab, double be,
+                                           double ga, int k, bool do_rx) {
+  if (do_rx) rx[i_rx] = make_float2((float)cos(be), (float)sin(be));
+  else tab[i_tab] = make_float2((float)cos(ga * k), (float)-sin(ga * k));
+}
+__device__ __forceinline__ void put_params(qops::RXc* rx, qops::Ph* tab, uint64_t i_rx, uint64_t i_tab, double be,
+                                           double ga, int k, bool do_rx) {
+  if (do_rx) {
+    qops::RXc r;
+    r.c = dfx::make_coef(cos(be));
+    r.s = dfx::make_coef(sin(be));
+    r.ns = dfx::make_coef(-sin(be));
+    rx[i_rx] = r;
+  } else {
+    const double tr = cos(ga * k), ti = -sin(ga * k);
+    qops::Ph t;
+    t.tr = dfx::make_coef(tr);
+    t.ti = dfx::make_coef(ti);
+    t.nti = dfx::make_coef(-ti);
+    tab[i_tab] = t;
+  }
+}
+
+template <class TR>
+__global__ void k_qaoa_params(const double* __restrict__ gam, const double* __restrict__ bet, int B, int p, int bmax,
+                              int tsize, typename TR::RX* __restrict__ rx, typename TR::PH* __restrict__ tab) {
+  const uint64_t total = (uint64_t)p * B * (tsize + 1);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % (tsize + 1));
+    const uint64_t lb = i / (tsize + 1);
+    const int b = (int)(lb % B), l = (int)(lb / B);
+    const double be = bet[(uint64_t)b * p + l], ga = gam[(uint64_t)b * p + l];
+    put_params(rx, tab, (uint64_t)l * bmax + b, ((uint64_t)l * bmax + b) * tsize + k, be, ga, k, k == tsize);
+  }
+}
+
+// results[b][0 | 1 + l | 1 + p + l] -> energies[b], grad_gammas[b][l], grad_betas[b][l] (device arrays).
+__global__ void k_scatter_results(const double* __restrict__ results, int stride, int B, int p,
+                                  double* __restrict__ E, double* __restrict__ dg, double* __restrict__ db) {
+  const int per = dg ? 1 + 2 * p : 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * per; i += gridDim.x * blockDim.x) {
+    const int b = i / per, j = i % per;
+    const double v = results[(uint64_t)b * stride + j];
+    if (j == 0) E[b] = v;
+    else if (j <= p) dg[(uint64_t)b * p + j - 1] = v;
+    else db[(uint64_t)b * p + j - 1 - p] = v;
+  }
+}
+
 // Host-side parameters: RX(2 beta) coefficients and exp(-i gamma k) tables, FP64-built.
 void fill_params_c64(iqs_qaoa* q, int B, int p, const double* gam, const double* bet) {
   float2* rx = (float2*)q->host_params;
@@ -2661,10 +2714,93 @@ void free_qaoa(iqs_qaoa* q) {
   delete q;
 }
 
+// One evaluation of the workspace's current parameter tables on its stream:
+// the captured CUDA graph of this (batch, p, gradient, renormalisation) shape,
+// captured on first use, or a direct enqueue.  Counts the kernels launched.
+cudaError_t launch_evaluation(iqs_qaoa* q, int batch, int p, bool grad) {
+  cudaStream_t s = q->stream;
+  cudaError_t e = cudaSuccess;
+  const auto key = std::make_tuple(batch, p, grad ? 1 : 0, q->renorm_every);
+  int kernels = 0;
+  if (q->use_graphs) {
+    auto it = q->graphs.find(key);
+    if (it == q->graphs.end()) {
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t ee = enqueue_any(q, batch, p, grad, &kernels);
+        e = cudaStreamEndCapture(s, &graph);
+        if (ee != cudaSuccess) e = ee;
+      }
+      cudaGraphExec_t exec = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return e;
+      it = q->graphs.emplace(key, std::make_pair(exec, kernels)).first;
+    }
+    kernels = it->second.second;
+    e = cudaGraphLaunch(it->second.first, s);
+  } else {
+    e = enqueue_any(q, batch, p, grad, &kernels);
+  }
+  if (e == cudaSuccess) note_launches(kernels);
+  return e;
+}
+
 }  // namespace
 }  // namespace iqs
 
 extern "C" {
+
+iqs_status iqs_qaoa_run_async(iqs_qaoa* q, int batch, int p, const double* d_gammas, const double* d_betas,
+                              double* d_energies, double* d_grad_gammas, double* d_grad_betas) {
+  using namespace iqs;
+  if (q == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (batch < 1 || batch > q->bmax) return report(IQS_EINVAL, "batch %d outside [1, %d]", batch, q->bmax);
+  if (p < 1 || p > kMaxP) return report(IQS_EINVAL, "depth p = %d outside [1, %d]", p, kMaxP);
+  if (!d_gammas || !d_betas || !d_energies) return report(IQS_EINVAL, "gammas, betas and energies must not be NULL");
+  const bool grad = d_grad_gammas != nullptr || d_grad_betas != nullptr;
+  if (grad && (!d_grad_gammas || !d_grad_betas)) return report(IQS_EINVAL, "give both gradient outputs or neither");
+  if (fault_now(2)) return report(IQS_ECUDA, "iqs_qaoa_run_async: injected launch failure");
+  cudaStream_t s = q->stream;
+  const int tsize = q->n_edges + 1;
+  const uint64_t work = (uint64_t)p * batch * (tsize + 1);
+  if (q->dtype == IQS_C128)
+    k_qaoa_params<T128><<<grid_for(work, 1, 4), kThreads, 0, s>>>(d_gammas, d_betas, batch, p, q->bmax, tsize,
+                                                                  (qops::RXc*)q->rx, (qops::Ph*)q->tables);
+  else
+    k_qaoa_params<T64><<<grid_for(work, 1, 4), kThreads, 0, s>>>(d_gammas, d_betas, batch, p, q->bmax, tsize,
+                                                                 (float2*)q->rx, (float2*)q->tables);
+  cudaError_t e = launched(1);
+  if (e == cudaSuccess) e = launch_evaluation(q, batch, p, grad);
+  if (e == cudaSuccess) {
+    const int stride = 1 + 2 * kMaxP;
+    k_scatter_results<<<grid_for((uint64_t)batch * (1 + 2 * p), 1, 4), kThreads, 0, s>>>(
+        q->results, stride, batch, p, d_energies, grad ? d_grad_gammas : nullptr, grad ? d_grad_betas : nullptr);
+    e = launched(1);
+  }
+  if (e != cudaSuccess) return report(IQS_ECUDA, "QAOA asynchronous launch: %s", cudaGetErrorString(e));
+  return IQS_OK;
+}
+
+iqs_status iqs_qaoa_synchronize(iqs_qaoa* q) {
+  using namespace iqs;
+  if (q == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  unsigned w[2] = {0, 0};
+  cudaError_t e = cudaStreamSynchronize(q->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&w[0], q->flag, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&w[1], q->tma_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return report(IQS_ECUDA, "QAOA synchronize: %s", cudaGetErrorString(e));
+  if (w[1]) {
+    cudaMemset(q->tma_err, 0, sizeof(unsigned));
+    return report(IQS_ETIMEOUT, "a TMA tile load did not complete within its wait limit; results are invalid");
+  }
+  if (w[0]) {
+    cudaMemset(q->flag, 0, sizeof(unsigned));
+    return report(IQS_ERANGE, "an amplitude outside the emulated-FP64 range was met");
+  }
+  return IQS_OK;
+}
 
 iqs_status iqs_qaoa_create(int n, int dtype, int batch_max, int n_edges, const int32_t* edges, void* stream,
                            iqs_qaoa** out) {
@@ -2851,31 +2987,8 @@ iqs_status iqs_qaoa_run(iqs_qaoa* q, int batch, int p, const double* gammas, con
     e = cudaMemcpyAsync(q->tables, q->host_params + q->rx_bytes, (size_t)p * q->bmax * (q->n_edges + 1) * ph_elem,
                         cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return report(IQS_ECUDA, "parameter upload: %s", cudaGetErrorString(e));
-  const auto key = std::make_tuple(batch, p, grad ? 1 : 0, q->renorm_every);
-  int kernels = 0;
-  if (q->use_graphs) {
-    auto it = q->graphs.find(key);
-    if (it == q->graphs.end()) {
-      cudaGraph_t graph = nullptr;
-      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        const cudaError_t ee = enqueue_any(q, batch, p, grad, &kernels);
-        e = cudaStreamEndCapture(s, &graph);
-        if (ee != cudaSuccess) e = ee;
-      }
-      cudaGraphExec_t exec = nullptr;
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-      if (graph) cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return report(IQS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-      it = q->graphs.emplace(key, std::make_pair(exec, kernels)).first;
-    }
-    kernels = it->second.second;
-    e = cudaGraphLaunch(it->second.first, s);
-  } else {
-    e = enqueue_any(q, batch, p, grad, &kernels);
-  }
+  e = launch_evaluation(q, batch, p, grad);
   if (e != cudaSuccess) return report(IQS_ECUDA, "QAOA launch: %s", cudaGetErrorString(e));
-  note_launches(kernels);
   const int stride = 1 + 2 * kMaxP;
   e = cudaMemcpyAsync(q->host_results, q->results, sizeof(double) * (size_t)batch * stride, cudaMemcpyDeviceToHost, s);
   unsigned f = 0, terr = 0;

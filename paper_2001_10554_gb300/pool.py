@@ -63,6 +63,18 @@ class Pool:
              probs.ctypes.data_as(_dp), mean.ctypes.data_as(_dp))
         return probs, mean
 
+    def run_brick_async(self, batch: int, depth: int, d_unitaries, d_angles, d_probs, d_mean) -> None:
+        """Stream-ordered run on device arrays (iqs_pool_run_brick_async): float64 CUDA tensors
+        ``d_unitaries`` [depth][n][8] (row-major U as (re, im) pairs), ``d_angles`` [batch][noise][2 or 3]
+        or None, outputs ``d_probs`` [batch][n] (or None) and ``d_mean`` [n], written on the pool's
+        stream.  Returns at once; call synchronize() before reading."""
+        dp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        call("iqs_pool_run_brick_async", self._h, int(batch), int(depth), dp(d_unitaries), dp(d_angles), dp(d_probs),
+             dp(d_mean))
+
+    def synchronize(self) -> None:
+        call("iqs_pool_synchronize", self._h)
+
     def state(self, index: int = 0) -> np.ndarray:
         out = np.empty(1 << self.n, dtype=np.complex128 if self.dtype_code == _lib.IQS_C128 else np.complex64)
         call("iqs_pool_download_state", self._h, int(index), C.c_void_p(out.ctypes.data), C.c_size_t(out.nbytes))

@@ -104,6 +104,20 @@ class QAOA:
         call("iqs_qaoa_run", self._h, batch, p, _ptr(g), _ptr(b), _ptr(E), None, None)
         return E
 
+    def run_async(self, gammas, betas, energies, grad_gammas=None, grad_betas=None) -> None:
+        """Stream-ordered evaluation on device arrays (iqs_qaoa_run_async): ``gammas`` and ``betas``
+        are contiguous float64 CUDA tensors [batch][p]; ``energies`` [batch] and, optionally,
+        ``grad_gammas``/``grad_betas`` [batch][p] are float64 CUDA tensors written on the workspace's
+        stream.  Returns at once; call synchronize() (or order on the stream) before reading."""
+        batch, p = int(gammas.shape[0]), int(gammas.shape[1])
+        dp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        call("iqs_qaoa_run_async", self._h, batch, p, dp(gammas), dp(betas), dp(energies), dp(grad_gammas),
+             dp(grad_betas))
+
+    def synchronize(self) -> None:
+        """Wait for the workspace's stream; raises on a range error or a TMA wait that gave up."""
+        call("iqs_qaoa_synchronize", self._h)
+
     def autotune(self, batch: int | None = None, p: int = 4) -> dict:
         """Pick the fastest mixer tile shape and grid size for (batch, p); returns the choice."""
         ms = C.c_double()

@@ -102,3 +102,25 @@ def test_pool_noise_count_and_brick_layout_without_gpu(lib, n, depth):
     one_q = [op for op in ops if op[0] == "1q"]
     for k, op in enumerate(one_q):
         assert np.array_equal(U[k // n, op[1]], op[2])
+
+
+def comment_above(name):
+    """The comment block that ends closest above ``name``'s declaration."""
+    src = open(HEADER).read()
+    i = re.search(r"\b" + name + r"\s*\(", re.sub(r"/\*.*?\*/", lambda m: " " * len(m.group(0)), src, flags=re.S)).start()
+    j = src.rfind("*/", 0, i)
+    return src[src.rfind("/*", 0, j): j]
+
+
+BOUNDARY_CALLS = ("iqs_create", "iqs_wrap", "iqs_destroy", "iqs_init_basis", "iqs_apply_1q", "iqs_apply_c1q",
+                  "iqs_apply_zz_phase", "iqs_probability", "iqs_probabilities", "iqs_expectation",
+                  "iqs_expectation_masks", "iqs_norm2", "iqs_renormalize", "iqs_energy_maxcut", "iqs_apply_kq",
+                  "iqs_qaoa_run", "iqs_qaoa_run_async", "iqs_pool_run_brick", "iqs_pool_run_brick_async")
+
+
+@pytest.mark.parametrize("name", BOUNDARY_CALLS)
+def test_boundary_calls_cite_the_paper_or_say_it_has_none(name):
+    """Every call of the hot-path boundary states the passage that defines it,
+    or says that the paper has no such call."""
+    text = comment_above(name)
+    assert "Section" in text or "paper names no" in text or "paper has no" in text, name
