@@ -491,6 +491,47 @@ iqs_status iqs_pool_many_set_engine(iqs_pool_many* w, int engine);
 iqs_status iqs_pool_many_run(iqs_pool_many* w, int n_circuits, const iqs_circuit_desc* circuits, double* probs,
                              double* means);
 
+/* Pools of circuits given as gate lists (Section 2 "Pool of multiple states":
+ * every pool state runs its own circuit; noise gates are one-qubit rotations
+ * with stochastic angles).  An op applies the 2x2 matrix U (row-major,
+ * (re, im) pairs, as iqs_apply_1q) to ``target``, or, with control >= 0, to
+ * the target of the basis states whose ``control`` qubit is 1 (as
+ * iqs_apply_c1q; CNOT = U = X).  Ops act in order. */
+typedef struct iqs_op {
+  int control;  /* -1: one-qubit gate; else the control qubit, != target */
+  int target;
+  double U[8];
+} iqs_op;
+
+typedef struct iqs_ops_circuit {
+  int n;                 /* qubits, 2..24 */
+  int n_ops;
+  const iqs_op* ops;     /* host array of n_ops ops */
+  int trajectories;      /* pool states of this circuit (1 when angles is NULL) */
+  const double* angles;  /* host [trajectories][iqs_ops_noise_count(n_ops, ops)][2], or NULL (noiseless) */
+} iqs_ops_circuit;
+
+/* Noise rotations per trajectory of a gate list: after every op, each qubit
+ * it touched (the target; the control, then the target) gets RX(tx) then
+ * RZ(tz), R(t) = exp(-i t sigma / 2); the count is the number of one-qubit ops
+ * plus twice the number of controlled ops (-1 for a bad argument). */
+int iqs_ops_noise_count(int n_ops, const iqs_op* ops);
+
+/* Run every trajectory of every gate-list circuit from |0...0> in one launch
+ * (one CTA per trajectory; each state in shared memory when it fits, 2^14
+ * complex64 or 2^13 complex128 amplitudes, else in an L2-resident slot of the
+ * workspace).  The ops are compiled once per circuit: noise rotations fuse
+ * into the one-qubit matrix before them, consecutive one-qubit matrices on a
+ * qubit fuse, and commuting steps are packed into register rounds of 4
+ * (complex64) or 3 (complex128) target bits.  Outputs (host), as for
+ * iqs_pool_many_run: probs = per-trajectory P(q = 1) divided by the state's
+ * squared norm, concatenated circuit by circuit as [trajectories][n], or NULL;
+ * means = per-circuit pool averages, concatenated as [n].  Synchronous.
+ * IQS_EINVAL for a qubit out of range, control == target, a non-finite
+ * matrix entry or bad sizes. */
+iqs_status iqs_pool_many_run_ops(iqs_pool_many* w, int n_circuits, const iqs_ops_circuit* circuits, double* probs,
+                                 double* means);
+
 /* ------------------------------------------------------------ allocation-free variant */
 
 /* The paper has no counterpart to this call: it is an interface for callers

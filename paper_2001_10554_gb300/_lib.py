@@ -83,6 +83,8 @@ SIGNATURES = {
     "iqs_qaoa_synchronize": ([C.c_void_p], C.c_int),
     "iqs_pool_run_brick_async": ([C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 4, C.c_int),
     "iqs_pool_synchronize": ([C.c_void_p], C.c_int),
+    "iqs_pool_many_run_ops": ([C.c_void_p, C.c_int, C.c_void_p, _dp, _dp], C.c_int),
+    "iqs_ops_noise_count": ([C.c_int, C.c_void_p], C.c_int),
     "iqs_qaoa_get_schedule": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "iqs_qaoa_get_tma": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "iqs_qaoa_download_state": ([C.c_void_p, C.c_int, C.c_void_p, C.c_size_t], C.c_int),

@@ -32,6 +32,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "pool_common.cuh"
+#include "pool_many_ws.h"
 
 namespace iqs {
 
@@ -268,22 +269,7 @@ __global__ void k_many_means(const double* __restrict__ probs, const uint64_t* _
 }  // namespace
 }  // namespace iqs
 
-// ================================================================ host workspace
-struct iqs_pool_many {
-  int dtype = IQS_C64;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  uint64_t timeout_ns = 2000000000ull;  // 2 s per wait
-  int debug_never = 0;
-  // device buffers (grown on demand)
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  void* blob = nullptr;  // params, tables, jobs, counters, partials, outputs
-  size_t blob_bytes = 0;
-  int engine = 0;         // 0 auto (cluster-resident for complex64 when every state fits), 1 persistent, 2 cluster
-  void* mats = nullptr;   // fused matrices of the cluster-resident path
-  size_t mats_bytes = 0;
-};
+// ================================================================ host workspace: pool_many_ws.h
 
 namespace iqs {
 namespace {
@@ -358,6 +344,7 @@ iqs_status iqs_pool_many_destroy(iqs_pool_many* w) {
   cudaFree(w->arena);
   cudaFree(w->blob);
   cudaFree(w->mats);
+  cudaFree(w->ops_buf);
   if (w->own_stream) cudaStreamDestroy(w->stream);
   delete w;
   return IQS_OK;

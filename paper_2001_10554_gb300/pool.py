@@ -97,12 +97,48 @@ class _Desc(C.Structure):
                 ("unitaries", C.c_void_p), ("angles", C.c_void_p)]
 
 
-class PoolMany:
-    """Brick circuits of uneven qubit counts, depths and trajectory counts in
-    one persistent kernel launch (``iqs_pool_many_*``).
+class _Op(C.Structure):
+    _fields_ = [("control", C.c_int), ("target", C.c_int), ("U", C.c_double * 8)]
 
-    ``run([(unitaries, angles_or_None), ...])`` returns, per circuit,
-    (probs[trajectories, n], mean[n]).
+
+class _OpsCircuit(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_ops", C.c_int), ("ops", C.c_void_p), ("trajectories", C.c_int),
+                ("angles", C.c_void_p)]
+
+
+_X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+
+
+def ops_array(ops):
+    """Gate list -> iqs_op array.  Ops are ("1q", q, U), ("c1q", c, t, U) or ("cx", c, t)."""
+    arr = (_Op * max(len(ops), 1))()
+    for i, op in enumerate(ops):
+        if op[0] == "1q":
+            c, t, U = -1, op[1], op[2]
+        elif op[0] == "c1q":
+            c, t, U = op[1], op[2], op[3]
+        elif op[0] == "cx":
+            c, t, U = op[1], op[2], _X
+        else:
+            raise ValueError(f"unknown op {op[0]!r}")
+        u = np.asarray(U, dtype=np.complex128).reshape(2, 2)
+        arr[i].control, arr[i].target = int(c), int(t)
+        arr[i].U[:] = [float(v) for z in u.reshape(-1) for v in (z.real, z.imag)]
+    return arr
+
+
+def ops_noise_count(ops) -> int:
+    """Noise rotations per trajectory of a gate list (one per one-qubit op, two per controlled op)."""
+    return sum(1 if op[0] == "1q" else 2 for op in ops)
+
+
+class PoolMany:
+    """Pools of circuits of uneven qubit counts, depths and trajectory counts in
+    one kernel launch (``iqs_pool_many_*``).
+
+    ``run([(unitaries, angles_or_None), ...])`` (brick circuits) and
+    ``run_ops([(n, ops, angles_or_None), ...])`` (gate lists) return, per
+    circuit, (probs[trajectories, n], mean[n]).
     """
 
     def __init__(self, dtype="complex64", stream=None):
@@ -139,6 +175,35 @@ class PoolMany:
         probs = np.empty(sum(t * n for t, n in shapes))
         means = np.empty(sum(n for _, n in shapes))
         call("iqs_pool_many_run", self._h, len(descs), C.cast(arr, C.c_void_p), probs.ctypes.data_as(_dp),
+             means.ctypes.data_as(_dp))
+        out, po, mo = [], 0, 0
+        for t, n in shapes:
+            out.append((probs[po:po + t * n].reshape(t, n), means[mo:mo + n]))
+            po += t * n
+            mo += n
+        return out
+
+    def run_ops(self, circuits):
+        """Gate-list circuits: [(n, ops, angles or None), ...] with ops as in ``ops_array`` and angles of
+        shape (trajectories, ops_noise_count(ops), 2)."""
+        keep, descs, shapes = [], [], []
+        for n, ops, ang in circuits:
+            arr = ops_array(ops)
+            keep.append(arr)
+            if ang is None:
+                traj, ap = 1, None
+            else:
+                a = np.ascontiguousarray(np.asarray(ang, dtype=np.float64))
+                if a.shape[1:] != (ops_noise_count(ops), 2):
+                    raise ValueError(f"angles must have shape (trajectories, {ops_noise_count(ops)}, 2)")
+                keep.append(a)
+                traj, ap = a.shape[0], a.ctypes.data
+            descs.append(_OpsCircuit(int(n), len(ops), C.cast(arr, C.c_void_p), traj, ap))
+            shapes.append((traj, int(n)))
+        darr = (_OpsCircuit * len(descs))(*descs)
+        probs = np.empty(sum(t * n for t, n in shapes))
+        means = np.empty(sum(n for _, n in shapes))
+        call("iqs_pool_many_run_ops", self._h, len(descs), C.cast(darr, C.c_void_p), probs.ctypes.data_as(_dp),
              means.ctypes.data_as(_dp))
         out, po, mo = [], 0, 0
         for t, n in shapes:

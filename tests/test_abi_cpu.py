@@ -124,3 +124,13 @@ def test_boundary_calls_cite_the_paper_or_say_it_has_none(name):
     or says that the paper has no such call."""
     text = comment_above(name)
     assert "Section" in text or "paper names no" in text or "paper has no" in text, name
+
+
+def test_gate_list_noise_count_without_gpu(lib):
+    from paper_2001_10554_gb300.pool import ops_array, ops_noise_count
+    import workloads as W
+    ops = W.random_gate_list(7, 50, seed=9)
+    arr = ops_array(ops)
+    assert lib.lib.iqs_ops_noise_count(len(ops), C.cast(arr, C.c_void_p)) == ops_noise_count(ops)
+    assert ops_noise_count(ops) == sum(1 if o[0] == "1q" else 2 for o in ops)
+    assert lib.lib.iqs_ops_noise_count(-1, None) == -1

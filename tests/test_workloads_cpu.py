@@ -90,3 +90,17 @@ def test_pso_inputs_and_noise_draws():
     assert rp.min() >= 0 and rp.max() < 1 and rg.min() >= 0 and rg.max() < 1
     z = W.noise_draws(50, 100, 3)
     assert z.shape == (50, 100, 3) and abs(z.mean()) < 0.05 and abs(z.std() - 1) < 0.05
+
+
+def test_random_gate_list_is_seeded_and_well_formed():
+    a = W.random_gate_list(9, 200, seed=5)
+    b = W.random_gate_list(9, 200, seed=5)
+    assert len(a) == 200
+    kinds = {op[0] for op in a}
+    assert kinds == {"1q", "c1q", "cx"}
+    for x, y in zip(a, b):
+        assert x[:3] == y[:3] if x[0] != "1q" else x[1] == y[1]
+        if x[0] in ("c1q", "cx"):
+            assert x[1] != x[2] and 0 <= x[1] < 9 and 0 <= x[2] < 9
+        else:
+            assert 0 <= x[1] < 9

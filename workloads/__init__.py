@@ -31,6 +31,7 @@ __all__ = [
     "qaoa_parameter_sets",
     "cnot_pairs",
     "random_circuit_layers",
+    "random_gate_list",
     "noise_ensemble",
     "PAULI_CHARS",
     "random_pauli_string",
@@ -152,6 +153,25 @@ def random_circuit_layers(n: int, layers: int, seed: int) -> list:
             ops.append(("1q", q, haar_u2(g)))
         for i in range(layer % 2, n - 1, 2):
             ops.append(("cx", i, i + 1))
+    return ops
+
+
+def random_gate_list(n: int, n_ops: int, seed: int, p_controlled: float = 0.4) -> list:
+    """A random circuit as a plain gate list (no layer structure): each op is,
+    with probability ``p_controlled``, a controlled gate on a uniform random
+    (control, target) pair, control != target (half of them CNOTs, half a
+    controlled Haar unitary), and otherwise a Haar one-qubit gate on a uniform
+    random qubit.  Ops: ("1q", q, U), ("c1q", c, t, U), ("cx", c, t)."""
+    g = rng(seed)
+    ops = []
+    for _ in range(n_ops):
+        if g.uniform() < p_controlled:
+            c = int(g.integers(0, n))
+            t = int(g.integers(0, n - 1))
+            t = t + 1 if t >= c else t
+            ops.append(("cx", c, t) if g.uniform() < 0.5 else ("c1q", c, t, haar_u2(g)))
+        else:
+            ops.append(("1q", int(g.integers(0, n)), haar_u2(g)))
     return ops
 
 
