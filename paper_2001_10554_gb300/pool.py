@@ -225,13 +225,23 @@ class PoolMany:
 
 
 def brick_unitaries(ops, n: int):
-    """(depth, n, 2, 2) unitaries from a layered op list (("1q", q, U) / ("cx", c, t))."""
+    """(depth, n, 2, 2) unitaries of a brick circuit given as an op list: layer l
+    is ("1q", q, U_q) for q = 0..n-1 in order, then ("cx", i, i + 1) for
+    i = l mod 2, l mod 2 + 2, ... (i + 1 < n).  Any other op list is rejected
+    with ValueError (run gate lists with PoolMany.run_ops instead)."""
     layers = []
-    cur = None
-    for op in ops:
-        if op[0] == "1q":
-            if op[1] == 0:
-                cur = [None] * n
-                layers.append(cur)
-            cur[op[1]] = op[2]
+    i = 0
+    while i < len(ops):
+        layer = len(layers)
+        us = []
+        for q in range(n):
+            if i >= len(ops) or ops[i][0] != "1q" or ops[i][1] != q:
+                raise ValueError(f"not a brick circuit: layer {layer} must start with one-qubit gates on 0..{n - 1}")
+            us.append(ops[i][2])
+            i += 1
+        for c in range(layer % 2, n - 1, 2):
+            if i >= len(ops) or ops[i][0] != "cx" or tuple(ops[i][1:3]) != (c, c + 1):
+                raise ValueError(f"not a brick circuit: layer {layer} needs CNOT({c}, {c + 1}) here")
+            i += 1
+        layers.append(us)
     return np.array(layers, dtype=np.complex128)

@@ -134,3 +134,16 @@ def test_gate_list_noise_count_without_gpu(lib):
     assert lib.lib.iqs_ops_noise_count(len(ops), C.cast(arr, C.c_void_p)) == ops_noise_count(ops)
     assert ops_noise_count(ops) == sum(1 if o[0] == "1q" else 2 for o in ops)
     assert lib.lib.iqs_ops_noise_count(-1, None) == -1
+
+
+def test_brick_unitaries_rejects_op_lists_that_are_not_the_brick():
+    import workloads as W
+    from paper_2001_10554_gb300.pool import brick_unitaries
+    ops = W.random_circuit_layers(6, 5, seed=1)
+    assert brick_unitaries(ops, 6).shape == (5, 6, 2, 2)
+    for bad in (ops[:-1],                        # the last layer's CNOT dropped
+                ops[:7] + ops[8:],               # a CNOT missing inside the first layer
+                ops[:6] + [("cx", 1, 0)] + ops[7:],  # a reversed CNOT
+                W.random_gate_list(6, 30, seed=2)):
+        with pytest.raises(ValueError):
+            brick_unitaries(bad, 6)
