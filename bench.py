@@ -693,6 +693,46 @@ def sig3(x):
     return None if x is None else float(f"{x:.3g}")
 
 
+def fused_row(iqs, torch, state, reg, stream, U8, n: int):
+    """The sweep's one-qubit gates q = 0..n-1 with gate fusion (iqs_set_fusion:
+    the gates on qubits 0..10 queue and run as one tiled pass) against the
+    same gates one pass each, on two copies of the state: time of all n gates
+    (CUDA events on the register's stream), kernel launches, largest amplitude
+    difference."""
+    from paper_2001_10554_gb300 import _lib
+    L = _lib.lib
+    with torch.cuda.stream(stream):
+        copy = state.clone()
+    stream.synchronize()
+    fz = iqs.Register.wrap(copy, stream=stream)
+    fz.set_fusion(True)
+    out = {}
+    for name, r in (("unfused", reg), ("fused", fz)):
+        for _ in range(2):   # the second round is timed
+            l0 = _lib.kernel_launches()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for q in range(n):
+                _lib.check(L.iqs_apply_1q(r.handle, q, U8[q]), "iqs_apply_1q")
+            _lib.check(L.iqs_flush(r.handle), "iqs_flush")
+            b.record(stream)
+            b.synchronize()
+            out[name] = {"ms": round(a.elapsed_time(b), 3), "launches": int(_lib.kernel_launches() - l0)}
+    diff = 0.0
+    chunk = 1 << 26
+    with torch.cuda.stream(stream):
+        for i in range(0, state.numel(), chunk):
+            diff = max(diff, float((state[i:i + chunk] - copy[i:i + chunk]).abs().max()))
+    fz.close()
+    del copy
+    torch.cuda.empty_cache()
+    N = 1 << n
+    return {"gates": n, "unfused_ms": out["unfused"]["ms"], "fused_ms": out["fused"]["ms"],
+            "unfused_launches": out["unfused"]["launches"], "fused_launches": out["fused"]["launches"],
+            "fused_gate_GBs": round(n * 2 * 16 * N / (out["fused"]["ms"] * 1e-3) / 1e9, 1),
+            "max_abs_diff": diff}
+
+
 def compact(extra: dict, native) -> dict:
     """Short summaries of the sections for the one stdout line (the full
     records go to stderr).  ``by_n`` lists, per QAOA row, batched complex64
@@ -933,6 +973,9 @@ def main(argv=None):
     native = None
     if not args.no_native and args.math != "native":
         native = native_row(iqs, torch, state, reg, stream, U8, n)
+    fused = None
+    if not args.no_extra:
+        fused = fused_row(iqs, torch, state, reg, stream, U8, n)
 
     reg.close()
     del state
@@ -963,12 +1006,17 @@ def main(argv=None):
                          "bytes_per_launch": sb["1q"] // n, "avg_launch_ms": round(avg_1q_ms, 4)},
         }
         line.update(compact(extra, native))
+        if fused:
+            line["fused_1q_sweep"] = {k: (sig3(v) if k == "max_abs_diff" else v) for k, v in fused.items()
+                                      if k != "fused_gate_GBs"}
         line.update({"cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                      "check": {"norm2": nn, "expectation": ex, "p_mean": float(np.mean(probs))}})
         details = dict(extra)
         details["roofline_per_target_ms"] = [round(float(x), 3) for x in per_q]
         if native:
             details["native_fp64_1q"] = native
+        if fused:
+            details["fused_1q_sweep"] = fused
         blob = json.dumps({"bench_details": details})
         print(blob, file=sys.stderr, flush=True)
         if args.details:

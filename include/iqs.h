@@ -97,6 +97,22 @@ iqs_status iqs_set_stream(iqs_reg* reg, void* stream);
 /* Arithmetic mode of complex128 gates (an iqs_math value); ignored for complex64. */
 iqs_status iqs_set_math(iqs_reg* reg, int math);
 
+/* Gate fusion on the register path (the tiles of Section 2's one-qubit gate
+ * equation applied several gates at a time).  With ``on`` != 0, iqs_apply_1q
+ * on a qubit below 12 (complex64) or 11 (complex128) only queues the gate:
+ * the gates queued on a qubit are multiplied in FP64 on the host, and all
+ * queued products run as ONE pass over the state (shared-memory tiles of
+ * 2^12 / 2^11 amplitudes, register rounds) when anything else touches the
+ * register: any other gate or reduction, iqs_data, iqs_download,
+ * iqs_synchronize, iqs_set_stream, iqs_set_math, iqs_destroy or iqs_flush
+ * (iqs_init_* and iqs_upload discard the queue: the state is replaced).  A
+ * caller that reads the device buffer by other means (a wrapped torch
+ * tensor) must call iqs_flush first.  Gates on higher qubits run at once,
+ * after a flush.  Queued gates are not queued for complex128 with
+ * IQS_MATH_NATIVE.  ``on`` = 0 flushes and stops queueing (the default). */
+iqs_status iqs_set_fusion(iqs_reg* reg, int on);
+iqs_status iqs_flush(iqs_reg* reg);
+
 /* Block the host until the register's stream is idle; reports IQS_ERANGE if
  * an emulated complex128 gate met an out-of-range amplitude since the last
  * check (the flag is cleared by the check). */

@@ -55,6 +55,23 @@ iqs_status cuda_fail(cudaError_t e, const char* what) {
     if ((r) == nullptr) return fail(IQS_EINVAL, "register is NULL");  \
   } while (0)
 
+// Apply the gates queued under iqs_set_fusion before anything else reads or
+// changes the state.
+iqs_status flush_pending(iqs_reg* r) {
+  if (r->fmask == 0) return IQS_OK;
+  if (iqs::fault_now(2)) return fail(IQS_ECUDA, "flush of queued gates: injected launch failure");
+  const cudaError_t e = iqs::launch_fused(r);
+  if (e != cudaSuccess) return fail(IQS_ECUDA, "flush of queued gates: %s", cudaGetErrorString(e));
+  r->fmask = 0;
+  return IQS_OK;
+}
+
+#define FLUSH(r)                                                            \
+  do {                                                                      \
+    iqs_status s_ = flush_pending(const_cast<iqs_reg*>(r));                 \
+    if (s_ != IQS_OK) return s_;                                            \
+  } while (0)
+
 // A kernel-launching call: an armed launch fault fails it before anything is queued.
 #define LAUNCH_TRY(expr, what)                                                              \
   do {                                                                                      \
@@ -257,6 +274,7 @@ iqs_status iqs_wrap(int n, int dtype, void* device_ptr, void* stream, iqs_reg** 
 
 iqs_status iqs_destroy(iqs_reg* reg) {
   if (reg == nullptr) return IQS_OK;
+  flush_pending(reg);  // a borrowed buffer outlives the register: it gets the queued gates
   cudaStreamSynchronize(reg->stream);
   free_reg(reg);
   return IQS_OK;
@@ -264,6 +282,7 @@ iqs_status iqs_destroy(iqs_reg* reg) {
 
 iqs_status iqs_data(const iqs_reg* reg, void** device_ptr) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (device_ptr == nullptr) return fail(IQS_EINVAL, "out is NULL");
   *device_ptr = reg->data;
   return IQS_OK;
@@ -278,12 +297,14 @@ iqs_status iqs_info(const iqs_reg* reg, int* n, int* dtype) {
 
 iqs_status iqs_set_stream(iqs_reg* reg, void* stream) {
   CHECK_REG(reg);
+  FLUSH(reg);
   reg->stream = (cudaStream_t)stream;
   return IQS_OK;
 }
 
 iqs_status iqs_set_math(iqs_reg* reg, int math) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (math != IQS_MATH_AUTO && math != IQS_MATH_EMULATED && math != IQS_MATH_NATIVE)
     return fail(IQS_EINVAL, "unknown math mode %d", math);
   reg->math = math;
@@ -292,11 +313,13 @@ iqs_status iqs_set_math(iqs_reg* reg, int math) {
 
 iqs_status iqs_synchronize(iqs_reg* reg) {
   CHECK_REG(reg);
+  FLUSH(reg);
   return check_flag(reg);
 }
 
 iqs_status iqs_init_basis(iqs_reg* reg, uint64_t index) {
   CHECK_REG(reg);
+  reg->fmask = 0;  // the state is replaced: queued gates are void
   if (index >= iqs::num_amps(reg)) return fail(IQS_EINVAL, "basis index out of range");
   LAUNCH_TRY(iqs::launch_init_basis(reg, index), "init_basis");
   return IQS_OK;
@@ -304,12 +327,14 @@ iqs_status iqs_init_basis(iqs_reg* reg, uint64_t index) {
 
 iqs_status iqs_init_uniform(iqs_reg* reg) {
   CHECK_REG(reg);
+  reg->fmask = 0;  // the state is replaced: queued gates are void
   LAUNCH_TRY(iqs::launch_init_uniform(reg), "init_uniform");
   return IQS_OK;
 }
 
 iqs_status iqs_upload(iqs_reg* reg, const void* host, size_t bytes) {
   CHECK_REG(reg);
+  reg->fmask = 0;  // the state is replaced: queued gates are void
   if (host == nullptr || bytes != iqs::num_amps(reg) * iqs::amp_bytes(reg))
     return fail(IQS_EINVAL, "upload: NULL buffer or size %zu != state size", bytes);
   CUDA_TRY(cudaMemcpyAsync(reg->data, host, bytes, cudaMemcpyHostToDevice, reg->stream), "upload");
@@ -319,6 +344,7 @@ iqs_status iqs_upload(iqs_reg* reg, const void* host, size_t bytes) {
 
 iqs_status iqs_download(const iqs_reg* reg, void* host, size_t bytes) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (host == nullptr || bytes != iqs::num_amps(reg) * iqs::amp_bytes(reg))
     return fail(IQS_EINVAL, "download: NULL buffer or size %zu != state size", bytes);
   CUDA_TRY(cudaMemcpyAsync(host, reg->data, bytes, cudaMemcpyDeviceToHost, reg->stream), "download");
@@ -330,12 +356,47 @@ iqs_status iqs_apply_1q(iqs_reg* reg, int q, const double U[8]) {
   CHECK_REG(reg);
   if (U == nullptr) return fail(IQS_EINVAL, "U is NULL");
   if (q < 0 || q >= reg->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, reg->n);
+  if (reg->fuse && q < iqs::fuse_bits(reg) && !(reg->dtype == IQS_C128 && reg->math == IQS_MATH_NATIVE)) {
+    double* m = reg->fmat[q];
+    if (!((reg->fmask >> q) & 1u)) {
+      for (int k = 0; k < 8; ++k) m[k] = U[k];
+    } else {  // m <- U m, FP64
+      double t[8];
+      for (int row = 0; row < 2; ++row)
+        for (int col = 0; col < 2; ++col) {
+          const double ar = U[2 * (2 * row)], ai = U[2 * (2 * row) + 1];
+          const double br = U[2 * (2 * row + 1)], bi = U[2 * (2 * row + 1) + 1];
+          const double cr = m[2 * col], ci = m[2 * col + 1];
+          const double dr = m[2 * (2 + col)], di = m[2 * (2 + col) + 1];
+          t[2 * (2 * row + col)] = ar * cr - ai * ci + br * dr - bi * di;
+          t[2 * (2 * row + col) + 1] = ar * ci + ai * cr + br * di + bi * dr;
+        }
+      for (int k = 0; k < 8; ++k) m[k] = t[k];
+    }
+    reg->fmask |= 1u << q;
+    return IQS_OK;
+  }
+  FLUSH(reg);
   LAUNCH_TRY(iqs::launch_1q(reg, q, to_mat(U)), "apply_1q");
+  return IQS_OK;
+}
+
+iqs_status iqs_set_fusion(iqs_reg* reg, int on) {
+  CHECK_REG(reg);
+  if (!on) FLUSH(reg);
+  reg->fuse = on != 0;
+  return IQS_OK;
+}
+
+iqs_status iqs_flush(iqs_reg* reg) {
+  CHECK_REG(reg);
+  FLUSH(reg);
   return IQS_OK;
 }
 
 iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (U == nullptr) return fail(IQS_EINVAL, "U is NULL");
   if (c < 0 || c >= reg->n || t < 0 || t >= reg->n) return fail(IQS_EINVAL, "control/target outside [0, %d)", reg->n);
   if (c == t) return fail(IQS_EINVAL, "control and target are the same qubit (%d)", c);
@@ -346,6 +407,7 @@ iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]) {
 
 iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges, const double* weights, double gamma) {
   CHECK_REG(reg);
+  FLUSH(reg);
   iqs_status s = check_edges(reg, n_edges, edges);
   if (s != IQS_OK) return s;
   if (!std::isfinite(gamma)) return fail(IQS_EINVAL, "gamma is not finite");
@@ -358,6 +420,7 @@ iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges, c
 
 iqs_status iqs_norm2(iqs_reg* reg, double* out) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
   LAUNCH_TRY(iqs::launch_norm2(reg), "norm2");
   iqs_status s = read_results(reg, 1, out);
@@ -366,6 +429,7 @@ iqs_status iqs_norm2(iqs_reg* reg, double* out) {
 
 iqs_status iqs_probability(iqs_reg* reg, int q, double* out) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
   if (q < 0 || q >= reg->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, reg->n);
   LAUNCH_TRY(iqs::launch_probability(reg, q), "probability");
@@ -375,6 +439,7 @@ iqs_status iqs_probability(iqs_reg* reg, int q, double* out) {
 
 iqs_status iqs_probabilities(iqs_reg* reg, double* out) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
   LAUNCH_TRY(iqs::launch_probabilities(reg), "probabilities");
   iqs_status s = read_results(reg, reg->n, out);
@@ -383,6 +448,7 @@ iqs_status iqs_probabilities(iqs_reg* reg, double* out) {
 
 iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, double* out) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
   const uint64_t all = reg->n >= 64 ? ~0ull : ((1ull << reg->n) - 1ull);
   if ((xmask | zmask) & ~all) return fail(IQS_EINVAL, "mask bits at or above n = %d", reg->n);
@@ -430,6 +496,7 @@ iqs_status iqs_renormalize(iqs_reg* reg) {
 
 iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges, const double* weights, double* out) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
   iqs_status s = check_edges(reg, n_edges, edges);
   if (s != IQS_OK) return s;
@@ -447,6 +514,7 @@ iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges, co
 
 iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (U == nullptr || qubits == nullptr) return fail(IQS_EINVAL, "qubits or U is NULL");
   const int kmax = iqs::max_kq(reg->dtype);
   if (k < 1 || k > kmax || k > reg->n) return fail(IQS_EINVAL, "k = %d outside [1, %d] for this register", k, kmax);
@@ -461,6 +529,7 @@ iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U)
 
 iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (qubits == nullptr || out == nullptr) return fail(IQS_EINVAL, "qubits or out is NULL");
   const int kmax = std::min(reg->n, iqs::max_marginal_qubits());
   if (k < 1 || k > kmax) return fail(IQS_EINVAL, "k = %d outside [1, %d]", k, kmax);
@@ -481,6 +550,7 @@ iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out) {
 
 iqs_status iqs_sample(iqs_reg* reg, uint64_t shots, const double* uniforms, uint64_t* out) {
   CHECK_REG(reg);
+  FLUSH(reg);
   if (shots == 0) return IQS_OK;
   if (uniforms == nullptr || out == nullptr) return fail(IQS_EINVAL, "uniforms or out is NULL");
   if (shots > (1ull << 32)) return fail(IQS_EINVAL, "at most 2^32 shots per call");

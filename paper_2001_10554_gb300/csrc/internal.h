@@ -22,6 +22,11 @@ struct iqs_reg {
   double* results = nullptr;     // kRedSlots doubles
   unsigned* flag = nullptr;      // 1 unsigned
   double* host_results = nullptr;  // pinned, kRedSlots doubles
+  // queued one-qubit gates on the qubits of one shared-memory tile (iqs_set_fusion):
+  // fmat[q] is the FP64 product of the gates queued on qubit q (bit q of fmask set)
+  bool fuse = false;
+  uint32_t fmask = 0;
+  double fmat[16][8];
 };
 
 namespace iqs {
@@ -87,6 +92,10 @@ bool as_monomial(const Mat2& u, Mono* m);
 
 // ---- gates.cu
 cudaError_t launch_1q(iqs_reg* r, int q, const Mat2& u);
+// fuse.cu: qubits [0, fuse_bits(r)) are queued under iqs_set_fusion; launch_fused
+// applies the queued products in one tiled pass (it does not clear them).
+int fuse_bits(const iqs_reg* r);
+cudaError_t launch_fused(iqs_reg* r);
 cudaError_t launch_c1q(iqs_reg* r, int c, int t, const Mat2& u);
 
 // ---- phase.cu

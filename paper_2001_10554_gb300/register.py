@@ -143,6 +143,14 @@ class Register:
     def synchronize(self) -> None:
         call("iqs_synchronize", self._h)
 
+    def set_fusion(self, on: bool = True) -> None:
+        """Queue one-qubit gates on low qubits and run them as one tiled pass (iqs_set_fusion)."""
+        call("iqs_set_fusion", self._h, int(bool(on)))
+
+    def flush(self) -> None:
+        """Apply the queued gates now (needed before reading a wrapped tensor directly)."""
+        call("iqs_flush", self._h)
+
     # ------------------------------------------------------------ state set-up
     def init_basis(self, index: int) -> None:
         call("iqs_init_basis", self._h, C.c_uint64(int(index)))

@@ -362,3 +362,36 @@ def test_33q_c64_beyond_32bit_indices(gpu_lib, dev):
     reg.close()
     del st
     torch.cuda.empty_cache()
+
+
+def test_fused_low_qubit_gates_30q_c128_one_pass(gpu_lib, dev):
+    """Gate fusion at full size: apply_1q on q = 0..9 of the 30-qubit
+    complex128 sweep state runs as ONE pass (one launch); four gathered
+    1024-amplitude blocks (the ten low qubits, high bits fixed) against the
+    oracle's gates applied to each block as a 10-qubit state (1e-12)."""
+    from paper_2001_10554_gb300 import _lib
+    n, N = 30, 1 << 30
+    g = W.rng(5301)
+    stream = torch.cuda.Stream(dev)
+    st = device_state(n, 5302, torch.complex128, dev, stream)
+    reg = gpu_lib.Register.wrap(st, stream=stream)
+    blocks = g.integers(0, N >> 10, size=4)
+    idx = (blocks[:, None] << 10) | np.arange(1024)[None, :]
+    before_vals = gather(st, idx.reshape(-1)).reshape(4, 1024)
+    reg.set_fusion(True)
+    Us = [W.haar_u2(g) for _ in range(10)]
+    l0 = _lib.kernel_launches()
+    for q in range(10):
+        reg.apply_1q(q, Us[q])
+    reg.flush()
+    assert _lib.kernel_launches() - l0 == 1
+    reg.synchronize()
+    after = gather(st, idx.reshape(-1)).reshape(4, 1024)
+    for b in range(4):
+        ref = before_vals[b]
+        for q in range(10):
+            ref = sv.apply_1q(ref, q, Us[q])
+        assert np.max(np.abs(after[b] - ref)) <= 1e-12
+    reg.close()
+    del st
+    torch.cuda.empty_cache()
