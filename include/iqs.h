@@ -165,6 +165,21 @@ iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges,
  * finite.  IQS_EINVAL otherwise, with the state untouched.  Asynchronous. */
 iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U);
 
+/* Project autotuner of iqs_apply_kq: times every kernel variant (0 the fixed
+ * rule, 1 shared-memory tiles for targets below bit 5, 2 one group per thread
+ * with U in constant memory, 3 rolled rows with U in shared memory) at 4, 8,
+ * 16 and 32 blocks per SM, on this register's state with these targets,
+ * applying U and its conjugate transpose alternately (an even number of
+ * times, so the state comes back up to rounding: U must be unitary), and keeps
+ * the fastest for every later iqs_apply_kq of the same dtype, arithmetic, k
+ * and target class (a target below bit 5, or none) in this process.  With
+ * IQS_AUTOTUNE_CACHE=<file> the choice is appended there and read back by
+ * later processes.  A variant that does not apply to a shape falls back to
+ * the fixed rule.  Outputs (may be NULL): the time of one gate with the
+ * choice, the variant, the blocks per SM. */
+iqs_status iqs_kq_autotune(iqs_reg* reg, int k, const int* qubits, const double* U, double* best_ms, int* variant,
+                           int* blocks_per_sm);
+
 /* ------------------------------------------------------------ reductions (FP64 results, synchronous) */
 
 /* Section 2 "Scope and basic use", GetProbability(q): sum of |alpha_i|^2 over
@@ -292,8 +307,9 @@ iqs_status iqs_qaoa_run_async(iqs_qaoa* q, int batch, int p, const double* d_gam
  * the evaluations since the last check (the flags are cleared). */
 iqs_status iqs_qaoa_synchronize(iqs_qaoa* q);
 
-/* Project autotuner: times TMA staging (off / forward / forward + adjoint),
- * then the candidate mixer tile shapes (the row width of the high passes,
+/* Project autotuner: times the pass schedule (chained, or per layer with TMA
+ * staging off / forward / forward + adjoint), then the candidate mixer tile
+ * shapes (the row width of the high passes,
  * hence gate bits per pass: 4..6 row bits for complex64, 3..5 for complex128)
  * and grid sizes (1x, 2x blocks per state) on this workspace
  * for ``batch`` parameter sets of depth p, and keeps the fastest (every shape
@@ -432,6 +448,21 @@ iqs_status iqs_pool_set_noise_t1t2(iqs_pool* p, double T1, double T2, double gat
  * qubits).  Results agree within the
  * rounding of the dtype (the gates are grouped differently). */
 iqs_status iqs_pool_set_engine(iqs_pool* p, int engine);
+
+/* Project autotuner of the pool engine: times the tiled passes and the
+ * cluster-resident engine at every cluster size that can hold the state
+ * (2^logc CTAs, from the smallest that fits up to 16) on ``batch``
+ * trajectories of a ``depth``-layer brick circuit (noisy or not), keeps the
+ * fastest for this pool (iqs_pool_set_engine is overridden) and, with
+ * IQS_AUTOTUNE_CACHE=<file>, appends it there; pools created later with the
+ * same dtype, n and batch_max start from it.  ``best_ms`` (may be NULL): time
+ * of one run with the choice.  Results agree within the dtype's rounding
+ * whatever the choice. */
+iqs_status iqs_pool_autotune(iqs_pool* p, int batch, int depth, int noisy, double* best_ms);
+
+/* Current engine (1 tiled passes, 2 cluster-resident, 0 automatic) and
+ * cluster size exponent (-1: the smallest that holds the state). */
+iqs_status iqs_pool_tuning(const iqs_pool* p, int* engine, int* logc);
 
 /* Section 2 "Pool of multiple states": run ``batch`` trajectories of one
  * brick circuit from |0...0>, each with its own noise rotations, and average

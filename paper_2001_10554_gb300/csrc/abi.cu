@@ -527,6 +527,26 @@ iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U)
   return IQS_OK;
 }
 
+iqs_status iqs_kq_autotune(iqs_reg* reg, int k, const int* qubits, const double* U, double* best_ms, int* variant,
+                           int* blocks_per_sm) {
+  CHECK_REG(reg);
+  FLUSH(reg);
+  if (U == nullptr || qubits == nullptr) return fail(IQS_EINVAL, "qubits or U is NULL");
+  const int kmax = iqs::max_kq(reg->dtype);
+  if (k < 1 || k > kmax || k > reg->n) return fail(IQS_EINVAL, "k = %d outside [1, %d] for this register", k, kmax);
+  iqs_status s = check_qubit_set(reg, k, qubits);
+  if (s != IQS_OK) return s;
+  for (int i = 0; i < (2 << (2 * k)); ++i)
+    if (!std::isfinite(U[i])) return fail(IQS_EINVAL, "U entry %d is not finite", i / 2);
+  double ms = 0.0;
+  int v = 0, ps = 0;
+  LAUNCH_TRY(iqs::tune_kq(reg, k, qubits, U, &ms, &v, &ps), "kq_autotune");
+  if (best_ms) *best_ms = ms;
+  if (variant) *variant = v;
+  if (blocks_per_sm) *blocks_per_sm = ps;
+  return check_flag(reg);
+}
+
 iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out) {
   CHECK_REG(reg);
   FLUSH(reg);

@@ -92,6 +92,8 @@ bool as_monomial(const Mat2& u, Mono* m);
 
 // ---- gates.cu
 cudaError_t launch_1q(iqs_reg* r, int q, const Mat2& u);
+// kgate.cu: iqs_kq_autotune's timing of the k-qubit gate variants.
+cudaError_t tune_kq(iqs_reg* r, int k, const int* qubits, const double* U, double* best_ms, int* variant, int* per_sm);
 // fuse.cu: qubits [0, fuse_bits(r)) are queued under iqs_set_fusion; launch_fused
 // applies the queued products in one tiled pass (it does not clear them).
 int fuse_bits(const iqs_reg* r);

@@ -15,7 +15,13 @@
 // paired .f32x2 instructions, two groups per thread) or, for small states or
 // on request, in native FP64.  One read and one write of the state per gate.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "common.cuh"
 #include "df64.cuh"
@@ -488,11 +494,55 @@ Targets<K> make_targets(const int* qubits) {
   return T;
 }
 
+// Kernel choices of iqs_kq_autotune, per (dtype, emulated arithmetic, k,
+// targets below bit 5): the variant (kVarAuto: the fixed rule below) and the
+// grid size in blocks per SM of the grid-stride variants.
+enum { kVarAuto = 0, kVarTiled = 1, kVarUnrolled = 2, kVarRows = 3 };
+struct KqChoice {
+  int variant = kVarAuto;
+  int per_sm = 8;
+};
+std::mutex g_kq_mutex;
+std::map<std::tuple<int, int, int, int>, KqChoice> g_kq_choice;
+bool g_kq_cache_loaded = false;
+
+std::tuple<int, int, int, int> kq_key(const iqs_reg* r, int k, const int* qubits) {
+  bool low = false;
+  for (int j = 0; j < k; ++j) low |= qubits[j] < 5;
+  return std::make_tuple(r->dtype, use_emulated(r) ? 1 : 0, k, low ? 1 : 0);
+}
+
+// Lines "kq <dtype> <emulated> <k> <low> <variant> <per_sm>" of IQS_AUTOTUNE_CACHE.
+void load_kq_cache_locked() {
+  if (g_kq_cache_loaded) return;
+  g_kq_cache_loaded = true;
+  const char* path = std::getenv("IQS_AUTOTUNE_CACHE");
+  if (path == nullptr) return;
+  FILE* f = std::fopen(path, "r");
+  if (f == nullptr) return;
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    char kind[16];
+    int dt, em, k, low, var, per_sm;
+    if (std::sscanf(line, "%15s %d %d %d %d %d %d", kind, &dt, &em, &k, &low, &var, &per_sm) == 7 &&
+        std::strcmp(kind, "kq") == 0 && var >= 0 && var <= 3 && per_sm >= 1 && per_sm <= 64)
+      g_kq_choice[std::make_tuple(dt, em, k, low)] = KqChoice{var, per_sm};
+  }
+  std::fclose(f);
+}
+
+KqChoice kq_choice(const iqs_reg* r, int k, const int* qubits) {
+  std::lock_guard<std::mutex> lock(g_kq_mutex);
+  load_kq_cache_locked();
+  auto it = g_kq_choice.find(kq_key(r, k, qubits));
+  return it == g_kq_choice.end() ? KqChoice() : it->second;
+}
+
 template <int K>
-cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
+cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U, KqChoice ch) {
   constexpr int D = 1 << K;
   const uint64_t n_groups = num_amps(r) >> K;
-  const unsigned grid = grid_for(n_groups, 1, 8);
+  const unsigned grid = grid_for(n_groups, 1, ch.per_sm);
   const Targets<K> T = make_targets<K>(qubits);
   if (r->dtype == IQS_C64) {
     if constexpr (K <= kMaxK64) {
@@ -501,7 +551,7 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
       bool low = false;
       for (int j = 0; j < K; ++j) low |= qubits[j] < 5;
       TilePlan<K> P;
-      if (low && make_tile_plan<K>(r->n, qubits, P)) {
+      if (low && ch.variant != kVarUnrolled && ch.variant != kVarRows && make_tile_plan<K>(r->n, qubits, P)) {
         const size_t smem = sizeof(float2) * ((size_t)(1 << tile_bits<K>()) + (size_t)(D * D)) + sizeof(uint64_t) * D;
         static PerDevice resident;  // per K instantiation: resident blocks per SM
         int per_sm = 0;
@@ -517,9 +567,9 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
         k_kgate_c64_tiled<K><<<tg, kThreads, smem, r->stream>>>((float2*)r->data, n_tiles, P, u);
         return launched(1);
       }
-      if constexpr (K >= 4)
+      if (K >= 4 || ch.variant == kVarRows)
         k_kgate_c64_rows<K><<<grid, kThreads, 0, r->stream>>>((float2*)r->data, n_groups, T, u);
-      else
+      else if constexpr (K < 4)
         k_kgate_c64<K><<<grid, kThreads, 0, r->stream>>>((float2*)r->data, n_groups, T, u);
       return launched(1);
     }
@@ -527,9 +577,9 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
     if constexpr (K <= kMaxK128) {
       UF64<K> u;
       for (int i = 0; i < D * D; ++i) u.u[i] = make_double2(U[2 * i], U[2 * i + 1]);
-      if constexpr (K >= 4)
+      if (K >= 4 || ch.variant == kVarRows)
         k_kgate_c128_native_rows<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u);
-      else
+      else if constexpr (K < 4)
         k_kgate_c128_native<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u);
       return launched(1);
     }
@@ -546,7 +596,7 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
           u.c[(2 * row + 1) * M + 2 * c + 1] = dfx::make_coef(ur);   // im += Re(u) Im(x)
         }
       if constexpr (K >= 2) {
-        const unsigned grid2 = grid_for((n_groups + 1) / 2, 1, 8);
+        const unsigned grid2 = grid_for((n_groups + 1) / 2, 1, ch.per_sm);
         k_kgate_c128_df2<K><<<grid2, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
       } else {
         k_kgate_c128_df<K><<<grid, kThreads, 0, r->stream>>>((double2*)r->data, n_groups, T, u, r->flag);
@@ -561,15 +611,86 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U) {
 
 int max_kq(int dtype) { return dtype == IQS_C64 ? kMaxK64 : kMaxK128; }
 
-cudaError_t launch_kq(iqs_reg* r, int k, const int* qubits, const double* U) {
+namespace {
+cudaError_t launch_kq_with(iqs_reg* r, int k, const int* qubits, const double* U, KqChoice ch) {
   switch (k) {
-    case 1: return launch_k<1>(r, qubits, U);
-    case 2: return launch_k<2>(r, qubits, U);
-    case 3: return launch_k<3>(r, qubits, U);
-    case 4: return launch_k<4>(r, qubits, U);
-    case 5: return launch_k<5>(r, qubits, U);
+    case 1: return launch_k<1>(r, qubits, U, ch);
+    case 2: return launch_k<2>(r, qubits, U, ch);
+    case 3: return launch_k<3>(r, qubits, U, ch);
+    case 4: return launch_k<4>(r, qubits, U, ch);
+    case 5: return launch_k<5>(r, qubits, U, ch);
     default: return cudaErrorInvalidValue;
   }
+}
+}  // namespace
+
+cudaError_t launch_kq(iqs_reg* r, int k, const int* qubits, const double* U) {
+  return launch_kq_with(r, k, qubits, U, kq_choice(r, k, qubits));
+}
+
+// Times every variant and grid size of a k-qubit gate on these targets on the
+// register's state (applying U and then its conjugate transpose, so the state
+// comes back up to rounding), and keeps the fastest for (dtype, arithmetic,
+// k, low targets).  Returns the best time of one gate in ms.
+cudaError_t tune_kq(iqs_reg* r, int k, const int* qubits, const double* U, double* best_ms, int* variant, int* per_sm) {
+  const int D = 1 << k;
+  std::vector<double> Uh((size_t)2 * D * D);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      Uh[2 * (i * D + j)] = U[2 * (j * D + i)];
+      Uh[2 * (i * D + j) + 1] = -U[2 * (j * D + i) + 1];
+    }
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return e;
+  std::vector<KqChoice> cands;
+  const int vars[4] = {kVarAuto, kVarTiled, kVarUnrolled, kVarRows};
+  for (int v : vars)
+    for (int ps : {4, 8, 16, 32}) cands.push_back(KqChoice{v, ps});
+  double best = 1e300;
+  KqChoice pick;
+  for (const KqChoice& c : cands) {
+    float tot = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // U then U^dagger, timed together
+      e = launch_kq_with(r, k, qubits, U, c);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, r->stream);
+      if (e == cudaSuccess) e = launch_kq_with(r, k, qubits, Uh.data(), c);
+      if (e == cudaSuccess) e = launch_kq_with(r, k, qubits, U, c);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, r->stream);
+      if (e == cudaSuccess) e = launch_kq_with(r, k, qubits, Uh.data(), c);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (e != cudaSuccess) break;
+    const double per_gate = tot / 4.0;
+    if (per_gate < best) {
+      best = per_gate;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(g_kq_mutex);
+    load_kq_cache_locked();
+    g_kq_choice[kq_key(r, k, qubits)] = pick;
+  }
+  if (const char* path = std::getenv("IQS_AUTOTUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "a")) {
+      const auto key = kq_key(r, k, qubits);
+      std::fprintf(f, "kq %d %d %d %d %d %d\n", std::get<0>(key), std::get<1>(key), std::get<2>(key),
+                   std::get<3>(key), pick.variant, pick.per_sm);
+      std::fclose(f);
+    }
+  }
+  *best_ms = best;
+  *variant = pick.variant;
+  *per_sm = pick.per_sm;
+  return cudaSuccess;
 }
 
 }  // namespace iqs

@@ -19,6 +19,9 @@
 // pass holds its qubits plus the qubit just below them, so the brick's
 // boundary CNOT runs after both its qubits' one-qubit gates.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -38,7 +41,9 @@ namespace iqs {
 // pool_cluster.cu
 bool pool_cluster_eligible(int n, int dtype);
 int pool_cluster_logc(int n, int dtype);
-cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s);
+cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s,
+                                int logc);
+bool pool_cluster_logc_ok(int n, int dtype, int lc);
 
 namespace {
 
@@ -179,6 +184,7 @@ struct iqs_pool {
   size_t angle_cap = 0;  // doubles
   int part_stride = 0, nblk = 0;
   int engine = 0;  // 0 auto (cluster-resident when the state fits), 1 tiled passes, 2 cluster-resident
+  int logc = -1;   // cluster size 2^logc of the cluster-resident engine (-1: the smallest that holds a state)
   int noise_model = 0;       // 0 angle pairs (tx, tz); 1 T1/T2 gates from normal triples
   double sig[3] = {0, 0, 0};  // T1/T2 gate angle standard deviations (x, y, z)
   // tiled-pass runs captured as CUDA graphs, per (batch, depth, noisy): the
@@ -296,7 +302,7 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
                            P->n, phases, depth};
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(P->cjobs, jobs.data(), sizeof(ClusterJob) * batch, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_pool_cluster(P->cjobs, batch, P->n, P->dtype, s);
+    if (e == cudaSuccess) e = launch_pool_cluster(P->cjobs, batch, P->n, P->dtype, s, P->logc);
     if (e != cudaSuccess) return e;
     k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
     return launched(1);
@@ -424,6 +430,23 @@ iqs_status iqs_pool_create(int n, int dtype, int batch_max, int depth_max, void*
     free_pool(p);
     return report(IQS_ECUDA, "pool set-up: %s", cudaGetErrorString(e));
   }
+  // choices persisted by iqs_pool_autotune: lines "pool <dtype> <n> <batch_max> <engine> <logc>"
+  if (const char* path = std::getenv("IQS_AUTOTUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "r")) {
+      char line[256];
+      while (std::fgets(line, sizeof(line), f)) {
+        char kind[16], dt[8];
+        int cn, cb, ce, cl;
+        if (std::sscanf(line, "%15s %7s %d %d %d %d", kind, dt, &cn, &cb, &ce, &cl) == 6 &&
+            std::strcmp(kind, "pool") == 0 && std::strcmp(dt, dtype == IQS_C128 ? "c128" : "c64") == 0 &&
+            cn == n && cb == batch_max && ce >= 0 && ce <= 2 && (ce != 2 || pool_cluster_logc_ok(n, dtype, cl))) {
+          p->engine = ce;  // the last matching line wins
+          p->logc = cl;
+        }
+      }
+      std::fclose(f);
+    }
+  }
   *out = p;
   return IQS_OK;
 }
@@ -534,6 +557,70 @@ iqs_status iqs_pool_synchronize(iqs_pool* p) {
     cudaMemset(p->flag, 0, sizeof(unsigned));
     return report(IQS_ERANGE, "an amplitude outside the emulated-FP64 range was met");
   }
+  return IQS_OK;
+}
+
+iqs_status iqs_pool_autotune(iqs_pool* p, int batch, int depth, int noisy, double* best_ms) {
+  using namespace iqs;
+  if (p == nullptr) return report(IQS_EINVAL, "handle is NULL");
+  if (batch < 1 || batch > p->bmax || depth < 1 || depth > p->depth_max)
+    return report(IQS_EINVAL, "batch %d or depth %d outside the pool's limits", batch, depth);
+  // timing inputs: rotations with varied angles and small noise angles (the speed does not depend on them)
+  std::vector<double> U((size_t)8 * p->n * depth);
+  for (size_t g = 0; g < (size_t)p->n * depth; ++g) {
+    const double a = 0.37 * (double)(g % 97) + 0.1, c = std::cos(a), s = std::sin(a);
+    const double u[8] = {c, 0.0, -s * 0.6, -s * 0.8, s * 0.6, -s * 0.8, c, 0.0};
+    std::memcpy(&U[8 * g], u, sizeof(u));
+  }
+  const int width = p->noise_model == 1 ? 3 : 2;
+  std::vector<double> ang(noisy ? (size_t)batch * n_noise_ops(p->n, depth) * width : 0);
+  for (size_t i = 0; i < ang.size(); ++i) ang[i] = 0.02 * std::sin(0.7 * (double)i);
+  std::vector<double> mean(p->n);
+  const int engine0 = p->engine, logc0 = p->logc;
+  struct Cand { int engine, logc; };
+  std::vector<Cand> cands{{1, -1}};
+  for (int lc = 0; lc <= 4; ++lc)
+    if (pool_cluster_logc_ok(p->n, p->dtype, lc)) cands.push_back({2, lc});
+  double best = 1e300;
+  Cand pick{engine0, logc0};
+  for (const Cand& c : cands) {
+    p->engine = c.engine;
+    p->logc = c.logc;
+    iqs_status st = iqs_pool_run_brick(p, batch, depth, U.data(), noisy ? ang.data() : nullptr, nullptr, mean.data());
+    if (st != IQS_OK) {  // a cluster size that cannot be scheduled here is skipped
+      if (c.engine == 1) return st;
+      continue;
+    }
+    double t = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {
+      const auto t0 = std::chrono::steady_clock::now();
+      st = iqs_pool_run_brick(p, batch, depth, U.data(), noisy ? ang.data() : nullptr, nullptr, mean.data());
+      const double dt = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (st != IQS_OK) return st;
+      t = std::min(t, dt);
+    }
+    if (t < best) {
+      best = t;
+      pick = c;
+    }
+  }
+  p->engine = pick.engine;
+  p->logc = pick.logc;
+  if (const char* path = std::getenv("IQS_AUTOTUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "pool %s %d %d %d %d\n", p->dtype == IQS_C128 ? "c128" : "c64", p->n, p->bmax, p->engine,
+                   p->logc);
+      std::fclose(f);
+    }
+  }
+  if (best_ms) *best_ms = best;
+  return IQS_OK;
+}
+
+iqs_status iqs_pool_tuning(const iqs_pool* p, int* engine, int* logc) {
+  if (p == nullptr) return iqs::report(IQS_EINVAL, "handle is NULL");
+  if (engine) *engine = p->engine;
+  if (logc) *logc = p->logc;
   return IQS_OK;
 }
 

@@ -468,10 +468,18 @@ bool pool_cluster_eligible(int n, int dtype) { return cluster_logc(n, dtype) >= 
 
 int pool_cluster_logc(int n, int dtype) { return cluster_logc(n, dtype); }
 
+// Whether an n-qubit state may be split over 2^lc CTAs: at least the smallest
+// cluster that holds it, at most kMaxLogC, n >= 2 lc + 1 and n - lc >= 8.
+bool pool_cluster_logc_ok(int n, int dtype, int lc) {
+  const int lo = cluster_logc(n, dtype);
+  return lo >= 0 && lc >= lo && lc <= kMaxLogC && n >= 2 * lc + 1 && n - lc >= 8;
+}
+
 // Jobs of qubit counts in [2 logc + 1, max_n] on clusters of 2^logc CTAs
-// (logc = pool_cluster_logc(max_n, dtype)); ``jobs`` is a device array.
-cudaError_t launch_pool_cluster(const ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s) {
-  const int lc = cluster_logc(max_n, dtype);
+// (logc = ``logc`` when pool_cluster_logc_ok, else pool_cluster_logc(max_n,
+// dtype)); ``jobs`` is a device array.
+cudaError_t launch_pool_cluster(const ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s, int logc) {
+  const int lc = pool_cluster_logc_ok(max_n, dtype, logc) ? logc : cluster_logc(max_n, dtype);
   cudaError_t e = cudaErrorInvalidValue;
   if (n_jobs < 1) return cudaSuccess;
   if (dtype == IQS_C128) {

@@ -38,7 +38,8 @@ namespace iqs {
 
 // pool_cluster.cu
 int pool_cluster_logc(int n, int dtype);
-cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s);
+cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s,
+                                int logc);
 
 namespace {
 
@@ -655,7 +656,7 @@ iqs_status run_many(iqs_pool_many* W, int nc, const iqs_circuit_desc* cd, double
       cj[j] = ClusterJob{jobs[j].mats, static_cast<V*>(W->arena) + jobs[j].state_off,
                          dprobs + out_off[jobs[j].out_index], jobs[j].n, jobs[j].phases, jobs[j].depth};
     e = cudaMemcpyAsync(dcj, cj.data(), njobs * sizeof(ClusterJob), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_pool_cluster(dcj, (int)njobs, max_n, W->dtype, st);
+    if (e == cudaSuccess) e = launch_pool_cluster(dcj, (int)njobs, max_n, W->dtype, st, -1);
     if (e == cudaSuccess) {
       k_many_means<<<nc, 32, 0, st>>>(dprobs, reinterpret_cast<const uint64_t*>(B + o_cf),
                                       reinterpret_cast<const int*>(B + o_ct), reinterpret_cast<const int*>(B + o_cn),

@@ -2667,20 +2667,24 @@ void replan(iqs_qaoa* q) {
 const char* dtype_name(int dtype) { return dtype == IQS_C128 ? "c128" : "c64"; }
 
 // Tile-shape choices persisted by the autotuner:
-// lines "qaoa <dtype> <n> <batch_max> <row_bits> <grid_mult> <tma_mode>".
+// lines "qaoa <dtype> <n> <batch_max> <row_bits> <grid_mult> <tma_mode> <schedule>"
+// (a line without the schedule field means the chained schedule).
 void load_tuning(iqs_qaoa* q) {
   const char* path = std::getenv("IQS_AUTOTUNE_CACHE");
   if (path == nullptr) return;
   FILE* f = std::fopen(path, "r");
   if (f == nullptr) return;
-  char kind[16], dt[8];
-  int n, bm, rows, mult, tma;
-  while (std::fscanf(f, "%15s %7s %d %d %d %d %d", kind, dt, &n, &bm, &rows, &mult, &tma) == 7) {
-    if (std::strcmp(kind, "qaoa") == 0 && std::strcmp(dt, dtype_name(q->dtype)) == 0 && n == q->n && bm == q->bmax &&
-        mult >= 1 && mult <= 4 && tma >= 0 && tma <= 2) {
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    char kind[16], dt[8];
+    int n, bm, rows, mult, tma, sched = 0;
+    const int got = std::sscanf(line, "%15s %7s %d %d %d %d %d %d", kind, dt, &n, &bm, &rows, &mult, &tma, &sched);
+    if (got >= 7 && std::strcmp(kind, "qaoa") == 0 && std::strcmp(dt, dtype_name(q->dtype)) == 0 && n == q->n &&
+        bm == q->bmax && mult >= 1 && mult <= 4 && tma >= 0 && tma <= 2 && sched >= 0 && sched <= 1) {
       q->row_bits = rows;
       q->grid_mult = mult;  // the last matching line wins
       q->tma_mode = tma;
+      q->schedule = sched;
     }
   }
   std::fclose(f);
@@ -2691,8 +2695,8 @@ void save_tuning(const iqs_qaoa* q) {
   if (path == nullptr) return;
   FILE* f = std::fopen(path, "a");
   if (f == nullptr) return;
-  std::fprintf(f, "qaoa %s %d %d %d %d %d\n", dtype_name(q->dtype), q->n, q->bmax, q->row_bits, q->grid_mult,
-               q->tma_mode);
+  std::fprintf(f, "qaoa %s %d %d %d %d %d %d\n", dtype_name(q->dtype), q->n, q->bmax, q->row_bits, q->grid_mult,
+               q->tma_mode, q->schedule);
   std::fclose(f);
 }
 
@@ -3047,20 +3051,30 @@ iqs_status iqs_qaoa_autotune(iqs_qaoa* q, int batch, int p, double* best_ms) {
     cudaEventElapsedTime(ms, e0, e1);
     return r;
   };
-  // 1) TMA staging off / forward / forward + adjoint, at the default shape
-  int best_tma = 0;
+  // 1) pass schedule and TMA staging at the default shape: the chained schedule
+  //    (forward tiles TMA-staged when available) against the per-layer schedule
+  //    with staging off / forward / forward + adjoint
+  int best_tma = 0, best_sched = 0;
   q->row_bits = rows0;
   q->grid_mult = 1;
-  for (int tma = 0; tma <= 2 && st == IQS_OK; ++tma) {
-    q->tma_mode = tma;
-    float ms = 0.f;
-    st = time_one(&ms);
-    if (st == IQS_OK && ms < best) {
-      best = ms;
-      best_tma = tma;
+  const int sched0 = q->schedule;
+  for (int sched = 0; sched <= 1 && st == IQS_OK; ++sched) {
+    q->schedule = sched;
+    if (sched == 0 && !chain_available(q)) continue;
+    for (int tma = sched == 0 ? 1 : 0; tma <= (sched == 0 ? 1 : 2) && st == IQS_OK; ++tma) {
+      q->tma_mode = tma;
+      float ms = 0.f;
+      st = time_one(&ms);
+      if (st == IQS_OK && ms < best) {
+        best = ms;
+        best_tma = tma;
+        best_sched = sched;
+      }
+      if (!q->tma_ok) break;  // no tensor maps here: staging unavailable
     }
-    if (!q->tma_ok) break;  // no tensor maps here: staging unavailable
   }
+  (void)sched0;
+  q->schedule = best_sched;
   q->tma_mode = best_tma;
   // 2) high-pass row width and grid size with that staging
   for (int rows = rows0; rows <= rows0 + 2 && st == IQS_OK; ++rows) {

@@ -37,6 +37,17 @@ class Pool:
         """"auto" (cluster-resident when a state fits), "passes" or "cluster"."""
         call("iqs_pool_set_engine", self._h, {"auto": 0, "passes": 1, "cluster": 2}[engine])
 
+    def autotune(self, batch: int, depth: int, noisy: bool = True) -> dict:
+        """Pick the fastest engine and cluster size for (batch, depth) (iqs_pool_autotune)."""
+        ms = C.c_double()
+        call("iqs_pool_autotune", self._h, int(batch), int(depth), int(bool(noisy)), C.byref(ms))
+        return dict(self.tuning(), best_ms=ms.value)
+
+    def tuning(self) -> dict:
+        e, lc = C.c_int(), C.c_int()
+        call("iqs_pool_tuning", self._h, C.byref(e), C.byref(lc))
+        return {"engine": ("auto", "tiled", "cluster")[e.value], "logc": lc.value}
+
     def set_noise_t1t2(self, T1: float, T2: float, gate_time: float) -> None:
         """Noise gates of duration gate_time from T1/T2: ``angles`` of run_brick
         become standard normal triples (batch, noise_count, 3).  T1 <= 0 restores

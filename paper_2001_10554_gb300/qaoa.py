@@ -128,7 +128,8 @@ class QAOA:
         rows, mult, tma, avail = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         call("iqs_qaoa_tuning", self._h, C.byref(rows), C.byref(mult))
         call("iqs_qaoa_get_tma", self._h, C.byref(tma), C.byref(avail))
-        return {"row_bits": rows.value, "grid_mult": mult.value, "tma_mode": tma.value, "tma_available": bool(avail.value)}
+        return {"row_bits": rows.value, "grid_mult": mult.value, "tma_mode": tma.value, "tma_available": bool(avail.value),
+                **self.schedule()}
 
     def set_schedule(self, schedule: str = "chained") -> None:
         """Pass schedule: "chained" (segments that merge the passes at layer boundaries, the default) or

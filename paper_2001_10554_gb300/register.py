@@ -195,6 +195,18 @@ class Register:
         buf = u.view(np.float64).reshape(-1)
         call("iqs_apply_kq", self._h, k, (C.c_int * k)(*qs), buf.ctypes.data_as(C.POINTER(C.c_double)))
 
+    def kq_autotune(self, qubits, U) -> dict:
+        """Time the k-qubit gate variants on these targets (iqs_kq_autotune; U must be unitary) and keep
+        the fastest; returns {"best_ms", "variant", "blocks_per_sm"}."""
+        qs = [int(q) for q in qubits]
+        k = len(qs)
+        u = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).reshape(1 << k, 1 << k))
+        buf = u.view(np.float64).reshape(-1)
+        ms, var, ps = C.c_double(), C.c_int(), C.c_int()
+        call("iqs_kq_autotune", self._h, k, (C.c_int * k)(*qs), buf.ctypes.data_as(C.POINTER(C.c_double)),
+             C.byref(ms), C.byref(var), C.byref(ps))
+        return {"best_ms": ms.value, "variant": var.value, "blocks_per_sm": ps.value}
+
     # ------------------------------------------------------------ reductions
     def probability(self, q: int) -> float:
         out = C.c_double()
