@@ -131,6 +131,27 @@ iqs_status iqs_init_uniform(iqs_reg* reg);
 iqs_status iqs_upload(iqs_reg* reg, const void* host, size_t bytes);
 iqs_status iqs_download(const iqs_reg* reg, void* host, size_t bytes);
 
+/* Stream-ordered partial copies: amplitudes [first, first + count) between a
+ * host buffer and the register, asynchronous on the register's stream (host
+ * memory must be pinned for the copy to overlap other work, and must stay
+ * valid until the stream has passed the copy).  With several streams (one
+ * register on a copy stream, registers wrapping slices of the same state on
+ * a compute stream, ordered by events) a caller can start the gates that act
+ * inside one slice while the next slice is still arriving.  IQS_EINVAL for a
+ * NULL buffer or a range outside the state.  Copying in discards queued
+ * (iqs_set_fusion) gates; copying out flushes them first. */
+iqs_status iqs_copy_to_device(iqs_reg* reg, const void* host, uint64_t first, uint64_t count);
+iqs_status iqs_copy_to_host(iqs_reg* reg, void* host, uint64_t first, uint64_t count);
+
+/* Checkpoint and resume (the paper has no such call): write the register's
+ * state to ``path`` (the 8 bytes "IQSSTATE", uint32 version 1, n, dtype and a
+ * zero word, then the 2^n amplitudes as stored), and read such a file back
+ * into a register of the same n and dtype (IQS_EINVAL otherwise, or for a
+ * file that is not a state file or is truncated; the register is then
+ * unspecified).  Synchronous; staged through a 64 MiB pinned buffer. */
+iqs_status iqs_save(iqs_reg* reg, const char* path);
+iqs_status iqs_load(iqs_reg* reg, const char* path);
+
 /* ------------------------------------------------------------ gates */
 
 /* Section 2 "Distributed implementation", the one-qubit gate equation:

@@ -80,6 +80,10 @@ SIGNATURES = {
     "iqs_qaoa_set_tma": ([C.c_void_p, C.c_int], C.c_int),
     "iqs_qaoa_set_schedule": ([C.c_void_p, C.c_int], C.c_int),
     "iqs_set_fusion": ([C.c_void_p, C.c_int], C.c_int),
+    "iqs_save": ([C.c_void_p, C.c_char_p], C.c_int),
+    "iqs_load": ([C.c_void_p, C.c_char_p], C.c_int),
+    "iqs_copy_to_device": ([C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64], C.c_int),
+    "iqs_copy_to_host": ([C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64], C.c_int),
     "iqs_kq_autotune": ([C.c_void_p, C.c_int, C.c_void_p, _dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "iqs_pool_autotune": ([C.c_void_p, C.c_int, C.c_int, C.c_int, _dp], C.c_int),
     "iqs_pool_tuning": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),

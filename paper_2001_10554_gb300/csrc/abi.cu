@@ -13,6 +13,8 @@
 
 #include "internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
@@ -54,6 +56,14 @@ iqs_status cuda_fail(cudaError_t e, const char* what) {
   do {                                                                \
     if ((r) == nullptr) return fail(IQS_EINVAL, "register is NULL");  \
   } while (0)
+
+// One NVTX range per ABI call, named after the call, so a profiler timeline
+// shows which library call issued which kernels (a no-op without a profiler).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+};
+#define TRACE() TraceRange trace_range_(__func__)
 
 // Apply the gates queued under iqs_set_fusion before anything else reads or
 // changes the state.
@@ -266,13 +276,18 @@ iqs_status iqs::report(iqs_status s, const char* fmt, ...) {
 
 extern "C" {
 
-iqs_status iqs_create(int n, int dtype, void* stream, iqs_reg** out) { return new_reg(n, dtype, nullptr, true, stream, out); }
+iqs_status iqs_create(int n, int dtype, void* stream, iqs_reg** out) {
+  TRACE();
+  return new_reg(n, dtype, nullptr, true, stream, out);
+}
 
 iqs_status iqs_wrap(int n, int dtype, void* device_ptr, void* stream, iqs_reg** out) {
+  TRACE();
   return new_reg(n, dtype, device_ptr, false, stream, out);
 }
 
 iqs_status iqs_destroy(iqs_reg* reg) {
+  TRACE();
   if (reg == nullptr) return IQS_OK;
   flush_pending(reg);  // a borrowed buffer outlives the register: it gets the queued gates
   cudaStreamSynchronize(reg->stream);
@@ -281,6 +296,7 @@ iqs_status iqs_destroy(iqs_reg* reg) {
 }
 
 iqs_status iqs_data(const iqs_reg* reg, void** device_ptr) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (device_ptr == nullptr) return fail(IQS_EINVAL, "out is NULL");
@@ -289,6 +305,7 @@ iqs_status iqs_data(const iqs_reg* reg, void** device_ptr) {
 }
 
 iqs_status iqs_info(const iqs_reg* reg, int* n, int* dtype) {
+  TRACE();
   CHECK_REG(reg);
   if (n) *n = reg->n;
   if (dtype) *dtype = reg->dtype;
@@ -296,6 +313,7 @@ iqs_status iqs_info(const iqs_reg* reg, int* n, int* dtype) {
 }
 
 iqs_status iqs_set_stream(iqs_reg* reg, void* stream) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   reg->stream = (cudaStream_t)stream;
@@ -303,6 +321,7 @@ iqs_status iqs_set_stream(iqs_reg* reg, void* stream) {
 }
 
 iqs_status iqs_set_math(iqs_reg* reg, int math) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (math != IQS_MATH_AUTO && math != IQS_MATH_EMULATED && math != IQS_MATH_NATIVE)
@@ -312,12 +331,14 @@ iqs_status iqs_set_math(iqs_reg* reg, int math) {
 }
 
 iqs_status iqs_synchronize(iqs_reg* reg) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   return check_flag(reg);
 }
 
 iqs_status iqs_init_basis(iqs_reg* reg, uint64_t index) {
+  TRACE();
   CHECK_REG(reg);
   reg->fmask = 0;  // the state is replaced: queued gates are void
   if (index >= iqs::num_amps(reg)) return fail(IQS_EINVAL, "basis index out of range");
@@ -326,6 +347,7 @@ iqs_status iqs_init_basis(iqs_reg* reg, uint64_t index) {
 }
 
 iqs_status iqs_init_uniform(iqs_reg* reg) {
+  TRACE();
   CHECK_REG(reg);
   reg->fmask = 0;  // the state is replaced: queued gates are void
   LAUNCH_TRY(iqs::launch_init_uniform(reg), "init_uniform");
@@ -333,6 +355,7 @@ iqs_status iqs_init_uniform(iqs_reg* reg) {
 }
 
 iqs_status iqs_upload(iqs_reg* reg, const void* host, size_t bytes) {
+  TRACE();
   CHECK_REG(reg);
   reg->fmask = 0;  // the state is replaced: queued gates are void
   if (host == nullptr || bytes != iqs::num_amps(reg) * iqs::amp_bytes(reg))
@@ -343,6 +366,7 @@ iqs_status iqs_upload(iqs_reg* reg, const void* host, size_t bytes) {
 }
 
 iqs_status iqs_download(const iqs_reg* reg, void* host, size_t bytes) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (host == nullptr || bytes != iqs::num_amps(reg) * iqs::amp_bytes(reg))
@@ -352,7 +376,36 @@ iqs_status iqs_download(const iqs_reg* reg, void* host, size_t bytes) {
   return IQS_OK;
 }
 
+iqs_status iqs_copy_to_device(iqs_reg* reg, const void* host, uint64_t first, uint64_t count) {
+  TRACE();
+  CHECK_REG(reg);
+  if (host == nullptr || first > iqs::num_amps(reg) || count > iqs::num_amps(reg) - first)
+    return fail(IQS_EINVAL, "copy_to_device: NULL buffer or amplitudes [%llu, +%llu) outside the state",
+                (unsigned long long)first, (unsigned long long)count);
+  if (count == 0) return IQS_OK;
+  reg->fmask = 0;  // part of the state is replaced: queued gates are void
+  const size_t ab = iqs::amp_bytes(reg);
+  CUDA_TRY(cudaMemcpyAsync((char*)reg->data + first * ab, host, count * ab, cudaMemcpyHostToDevice, reg->stream),
+           "copy_to_device");
+  return IQS_OK;
+}
+
+iqs_status iqs_copy_to_host(iqs_reg* reg, void* host, uint64_t first, uint64_t count) {
+  TRACE();
+  CHECK_REG(reg);
+  FLUSH(reg);
+  if (host == nullptr || first > iqs::num_amps(reg) || count > iqs::num_amps(reg) - first)
+    return fail(IQS_EINVAL, "copy_to_host: NULL buffer or amplitudes [%llu, +%llu) outside the state",
+                (unsigned long long)first, (unsigned long long)count);
+  if (count == 0) return IQS_OK;
+  const size_t ab = iqs::amp_bytes(reg);
+  CUDA_TRY(cudaMemcpyAsync(host, (const char*)reg->data + first * ab, count * ab, cudaMemcpyDeviceToHost, reg->stream),
+           "copy_to_host");
+  return IQS_OK;
+}
+
 iqs_status iqs_apply_1q(iqs_reg* reg, int q, const double U[8]) {
+  TRACE();
   CHECK_REG(reg);
   if (U == nullptr) return fail(IQS_EINVAL, "U is NULL");
   if (q < 0 || q >= reg->n) return fail(IQS_EINVAL, "qubit %d outside [0, %d)", q, reg->n);
@@ -382,6 +435,7 @@ iqs_status iqs_apply_1q(iqs_reg* reg, int q, const double U[8]) {
 }
 
 iqs_status iqs_set_fusion(iqs_reg* reg, int on) {
+  TRACE();
   CHECK_REG(reg);
   if (!on) FLUSH(reg);
   reg->fuse = on != 0;
@@ -389,12 +443,14 @@ iqs_status iqs_set_fusion(iqs_reg* reg, int on) {
 }
 
 iqs_status iqs_flush(iqs_reg* reg) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   return IQS_OK;
 }
 
 iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (U == nullptr) return fail(IQS_EINVAL, "U is NULL");
@@ -406,6 +462,7 @@ iqs_status iqs_apply_c1q(iqs_reg* reg, int c, int t, const double U[8]) {
 }
 
 iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges, const double* weights, double gamma) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   iqs_status s = check_edges(reg, n_edges, edges);
@@ -419,6 +476,7 @@ iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges, c
 }
 
 iqs_status iqs_norm2(iqs_reg* reg, double* out) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
@@ -428,6 +486,7 @@ iqs_status iqs_norm2(iqs_reg* reg, double* out) {
 }
 
 iqs_status iqs_probability(iqs_reg* reg, int q, double* out) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
@@ -438,6 +497,7 @@ iqs_status iqs_probability(iqs_reg* reg, int q, double* out) {
 }
 
 iqs_status iqs_probabilities(iqs_reg* reg, double* out) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
@@ -447,6 +507,7 @@ iqs_status iqs_probabilities(iqs_reg* reg, double* out) {
 }
 
 iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, double* out) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
@@ -467,6 +528,7 @@ iqs_status iqs_expectation_masks(iqs_reg* reg, uint64_t xmask, uint64_t zmask, d
 }
 
 iqs_status iqs_expectation(iqs_reg* reg, const char* pauli, double* out) {
+  TRACE();
   CHECK_REG(reg);
   if (pauli == nullptr) return fail(IQS_EINVAL, "pauli is NULL");
   const size_t len = strnlen(pauli, IQS_MAX_QUBITS + 2);
@@ -485,6 +547,7 @@ iqs_status iqs_expectation(iqs_reg* reg, const char* pauli, double* out) {
 }
 
 iqs_status iqs_renormalize(iqs_reg* reg) {
+  TRACE();
   CHECK_REG(reg);
   double nn;
   iqs_status s = iqs_norm2(reg, &nn);
@@ -495,6 +558,7 @@ iqs_status iqs_renormalize(iqs_reg* reg) {
 }
 
 iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges, const double* weights, double* out) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (out == nullptr) return fail(IQS_EINVAL, "out is NULL");
@@ -513,6 +577,7 @@ iqs_status iqs_energy_maxcut(iqs_reg* reg, int n_edges, const int32_t* edges, co
 }
 
 iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (U == nullptr || qubits == nullptr) return fail(IQS_EINVAL, "qubits or U is NULL");
@@ -529,6 +594,7 @@ iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U)
 
 iqs_status iqs_kq_autotune(iqs_reg* reg, int k, const int* qubits, const double* U, double* best_ms, int* variant,
                            int* blocks_per_sm) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (U == nullptr || qubits == nullptr) return fail(IQS_EINVAL, "qubits or U is NULL");
@@ -548,6 +614,7 @@ iqs_status iqs_kq_autotune(iqs_reg* reg, int k, const int* qubits, const double*
 }
 
 iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (qubits == nullptr || out == nullptr) return fail(IQS_EINVAL, "qubits or out is NULL");
@@ -569,6 +636,7 @@ iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out) {
 }
 
 iqs_status iqs_sample(iqs_reg* reg, uint64_t shots, const double* uniforms, uint64_t* out) {
+  TRACE();
   CHECK_REG(reg);
   FLUSH(reg);
   if (shots == 0) return IQS_OK;
@@ -593,6 +661,74 @@ iqs_status iqs_sample(iqs_reg* reg, uint64_t shots, const double* uniforms, uint
   return IQS_OK;
 }
 
+// State files: the 8 bytes "IQSSTATE", then uint32 version (1), n, dtype and
+// a zero word, then the 2^n amplitudes as stored (interleaved re, im).
+iqs_status iqs_save(iqs_reg* reg, const char* path) {
+  TRACE();
+  CHECK_REG(reg);
+  FLUSH(reg);
+  if (path == nullptr) return fail(IQS_EINVAL, "path is NULL");
+  FILE* f = std::fopen(path, "wb");
+  if (f == nullptr) return fail(IQS_EINVAL, "cannot open %s for writing", path);
+  const uint32_t hdr[4] = {1u, (uint32_t)reg->n, (uint32_t)reg->dtype, 0u};
+  bool ok = std::fwrite("IQSSTATE", 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
+  const size_t total = iqs::num_amps(reg) * iqs::amp_bytes(reg), step = (size_t)64 << 20;
+  void* buf = nullptr;
+  if (ok && cudaMallocHost(&buf, std::min(total, step)) != cudaSuccess) {
+    cudaGetLastError();
+    std::fclose(f);
+    return fail(IQS_ENOMEM, "save: no pinned staging buffer");
+  }
+  for (size_t off = 0; ok && off < total; off += step) {
+    const size_t m = std::min(step, total - off);
+    ok = cudaMemcpyAsync(buf, (const char*)reg->data + off, m, cudaMemcpyDeviceToHost, reg->stream) == cudaSuccess &&
+         cudaStreamSynchronize(reg->stream) == cudaSuccess && std::fwrite(buf, 1, m, f) == m;
+  }
+  if (buf) cudaFreeHost(buf);
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(IQS_ECUDA, "save to %s failed", path);
+  return IQS_OK;
+}
+
+iqs_status iqs_load(iqs_reg* reg, const char* path) {
+  TRACE();
+  CHECK_REG(reg);
+  if (path == nullptr) return fail(IQS_EINVAL, "path is NULL");
+  FILE* f = std::fopen(path, "rb");
+  if (f == nullptr) return fail(IQS_EINVAL, "cannot open %s", path);
+  char magic[8];
+  uint32_t hdr[4];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, "IQSSTATE", 8) != 0 || std::fread(hdr, sizeof(hdr), 1, f) != 1 ||
+      hdr[0] != 1u) {
+    std::fclose(f);
+    return fail(IQS_EINVAL, "%s is not a state file", path);
+  }
+  if ((int)hdr[1] != reg->n || (int)hdr[2] != reg->dtype) {
+    std::fclose(f);
+    return fail(IQS_EINVAL, "%s holds %u qubits of dtype %u; the register has %d of dtype %d", path, hdr[1], hdr[2],
+                reg->n, reg->dtype);
+  }
+  reg->fmask = 0;  // the state is replaced: queued gates are void
+  const size_t total = iqs::num_amps(reg) * iqs::amp_bytes(reg), step = (size_t)64 << 20;
+  void* buf = nullptr;
+  if (cudaMallocHost(&buf, std::min(total, step)) != cudaSuccess) {
+    cudaGetLastError();
+    std::fclose(f);
+    return fail(IQS_ENOMEM, "load: no pinned staging buffer");
+  }
+  bool ok = true;
+  for (size_t off = 0; ok && off < total; off += step) {
+    const size_t m = std::min(step, total - off);
+    ok = std::fread(buf, 1, m, f) == m &&
+         cudaMemcpyAsync((char*)reg->data + off, buf, m, cudaMemcpyHostToDevice, reg->stream) == cudaSuccess &&
+         cudaStreamSynchronize(reg->stream) == cudaSuccess;
+  }
+  cudaFreeHost(buf);
+  std::fclose(f);
+  if (!ok) return fail(IQS_EINVAL, "%s is truncated or could not be copied", path);
+  return IQS_OK;
+}
+
 const char* iqs_last_error(void) { return g_err; }
 
 const char* iqs_version(void) { return "iqs-gb300 0.1.0 (sm_103a)"; }
@@ -600,6 +736,7 @@ const char* iqs_version(void) { return "iqs-gb300 0.1.0 (sm_103a)"; }
 uint64_t iqs_kernel_launches(void) { return g_launches.load(); }
 
 iqs_status iqs_inject_fault(int kind, int after) {
+  TRACE();
   if (kind < 0 || kind > 2 || after < 0) return fail(IQS_EINVAL, "fault kind must be 0, 1 or 2 and after >= 0");
   g_fault_countdown = after;
   g_fault_kind = kind;

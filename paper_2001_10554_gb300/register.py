@@ -173,6 +173,22 @@ class Register:
         call("iqs_download", self._h, C.c_void_p(out.ctypes.data), C.c_size_t(out.nbytes))
         return out
 
+    def save(self, path) -> None:
+        """Write the state to a file (iqs_save)."""
+        call("iqs_save", self._h, str(path).encode())
+
+    def load(self, path) -> None:
+        """Read a state file of the same n and dtype (iqs_load)."""
+        call("iqs_load", self._h, str(path).encode())
+
+    def copy_to_device_ptr(self, host_ptr: int, first: int, count: int) -> None:
+        """Asynchronous copy of amplitudes [first, first + count) from (pinned) host memory (iqs_copy_to_device)."""
+        call("iqs_copy_to_device", self._h, C.c_void_p(host_ptr), C.c_uint64(first), C.c_uint64(count))
+
+    def copy_to_host_ptr(self, host_ptr: int, first: int, count: int) -> None:
+        """Asynchronous copy of amplitudes [first, first + count) to (pinned) host memory (iqs_copy_to_host)."""
+        call("iqs_copy_to_host", self._h, C.c_void_p(host_ptr), C.c_uint64(first), C.c_uint64(count))
+
     def download_ptr(self, host_ptr: int, nbytes: int) -> None:
         call("iqs_download", self._h, C.c_void_p(host_ptr), C.c_size_t(nbytes))
 
