@@ -44,6 +44,9 @@ int pool_cluster_logc(int n, int dtype);
 cudaError_t launch_pool_cluster(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s,
                                 int logc);
 bool pool_cluster_logc_ok(int n, int dtype, int lc);
+// the same launch without counting it (for graph capture)
+cudaError_t launch_pool_cluster_raw(const pool::ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s,
+                                    int logc);
 
 namespace {
 
@@ -187,9 +190,11 @@ struct iqs_pool {
   int logc = -1;   // cluster size 2^logc of the cluster-resident engine (-1: the smallest that holds a state)
   int noise_model = 0;       // 0 angle pairs (tx, tz); 1 T1/T2 gates from normal triples
   double sig[3] = {0, 0, 0};  // T1/T2 gate angle standard deviations (x, y, z)
-  // tiled-pass runs captured as CUDA graphs, per (batch, depth, noisy): the
-  // executable graph and the kernels it launches
-  std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, int>> graphs;
+  // runs captured as CUDA graphs, per (batch, depth, noisy, engine path): the
+  // executable graph and the kernels it launches (path 0: tiled passes;
+  // 1 + logc: the cluster-resident engine on clusters of 2^logc CTAs)
+  std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int>> graphs;
+  std::tuple<int, int, int> cjobs_key{-1, -1, -1};  // (batch, depth, noisy) of the job table in cjobs
 };
 
 namespace iqs {
@@ -292,25 +297,64 @@ cudaError_t run_pool(iqs_pool* P, int batch, int depth, bool noisy) {
   const bool cluster = P->engine == 2 || (P->engine == 0 && P->dtype == IQS_C64 && pool_cluster_eligible(P->n, P->dtype) &&
                                           pool_cluster_logc(P->n, P->dtype) <= 2);
   if (cluster) {
-    // the whole circuit of every trajectory in one launch, states resident in cluster shared memory
-    k_pool_compose<TR><<<grid_for((uint64_t)batch * phases * P->n, 1, 8), kThreads, 0, s>>>(circuit_of(P, depth, noisy),
-                                                                                          batch, phases, allm);
-    cudaError_t e = launched(1);
-    std::vector<ClusterJob> jobs(batch);
-    for (int b = 0; b < batch; ++b)
-      jobs[b] = ClusterJob{allm + (uint64_t)b * phases * P->n, psi + (uint64_t)b * N, P->probs + (uint64_t)b * P->n,
-                           P->n, phases, depth};
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(P->cjobs, jobs.data(), sizeof(ClusterJob) * batch, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_pool_cluster(P->cjobs, batch, P->n, P->dtype, s, P->logc);
-    if (e != cudaSuccess) return e;
-    k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
-    return launched(1);
+    // the whole circuit of every trajectory in one launch, states resident in
+    // cluster shared memory; compose, cluster launch and mean are captured as a
+    // CUDA graph per shape and replayed (the job table, fixed per shape, is
+    // uploaded before the capture when the shape changes)
+    const auto jkey = std::make_tuple(batch, depth, noisy ? 1 : 0);
+    if (P->cjobs_key != jkey) {
+      std::vector<ClusterJob> jobs(batch);
+      for (int b = 0; b < batch; ++b)
+        jobs[b] = ClusterJob{allm + (uint64_t)b * phases * P->n, psi + (uint64_t)b * N, P->probs + (uint64_t)b * P->n,
+                             P->n, phases, depth};
+      cudaError_t e = cudaMemcpyAsync(P->cjobs, jobs.data(), sizeof(ClusterJob) * batch, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return e;
+      P->cjobs_key = jkey;
+    }
+    auto enqueue_cluster = [&](int* launches) {
+      k_pool_compose<TR><<<grid_for((uint64_t)batch * phases * P->n, 1, 8), kThreads, 0, s>>>(
+          circuit_of(P, depth, noisy), batch, phases, allm);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = launch_pool_cluster_raw(P->cjobs, batch, P->n, P->dtype, s, P->logc);
+      if (e == cudaSuccess) {
+        k_pool_mean<<<P->n, kThreads, 0, s>>>(P->probs, batch, P->n, P->mean);
+        e = cudaGetLastError();
+      }
+      *launches = 3;
+      return e;
+    };
+    const int lc = pool_cluster_logc_ok(P->n, P->dtype, P->logc) ? P->logc : pool_cluster_logc(P->n, P->dtype);
+    const auto key = std::make_tuple(batch, depth, noisy ? 1 : 0, 1 + lc);
+    auto it = P->graphs.find(key);
+    if (it == P->graphs.end()) {
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) {  // a stream that cannot be captured (the legacy default stream): launch directly
+        cudaGetLastError();
+        int launches = 0;
+        e = enqueue_cluster(&launches);
+        if (e == cudaSuccess) note_launches(launches);
+        return e;
+      }
+      int launches = 0;
+      const cudaError_t ee = enqueue_cluster(&launches);
+      e = cudaStreamEndCapture(s, &graph);
+      if (ee != cudaSuccess) e = ee;
+      cudaGraphExec_t exec = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return e;
+      it = P->graphs.emplace(key, std::make_pair(exec, launches)).first;
+    }
+    const cudaError_t e = cudaGraphLaunch(it->second.first, s);
+    if (e == cudaSuccess) note_launches(it->second.second);
+    return e;
   }
   // tiled passes: about two launches per layer, replayed from a CUDA graph
   // captured on the first run of each (batch, depth, noisy) shape; the inputs
   // live in fixed device buffers, so a replay reads each call's unitaries and angles
-  const auto key = std::make_tuple(batch, depth, noisy ? 1 : 0);
+  const auto key = std::make_tuple(batch, depth, noisy ? 1 : 0, 0);
   auto it = P->graphs.find(key);
   if (it == P->graphs.end()) {
     cudaGraph_t graph = nullptr;

@@ -475,10 +475,18 @@ bool pool_cluster_logc_ok(int n, int dtype, int lc) {
   return lo >= 0 && lc >= lo && lc <= kMaxLogC && n >= 2 * lc + 1 && n - lc >= 8;
 }
 
+cudaError_t launch_pool_cluster_raw(const ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s, int logc);
+
 // Jobs of qubit counts in [2 logc + 1, max_n] on clusters of 2^logc CTAs
 // (logc = ``logc`` when pool_cluster_logc_ok, else pool_cluster_logc(max_n,
 // dtype)); ``jobs`` is a device array.
 cudaError_t launch_pool_cluster(const ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s, int logc) {
+  const cudaError_t e = launch_pool_cluster_raw(jobs, n_jobs, max_n, dtype, s, logc);
+  return e == cudaSuccess && n_jobs >= 1 ? launched(1) : e;
+}
+
+cudaError_t launch_pool_cluster_raw(const ClusterJob* jobs, int n_jobs, int max_n, int dtype, cudaStream_t s,
+                                    int logc) {
   const int lc = pool_cluster_logc_ok(max_n, dtype, logc) ? logc : cluster_logc(max_n, dtype);
   cudaError_t e = cudaErrorInvalidValue;
   if (n_jobs < 1) return cudaSuccess;
@@ -501,7 +509,7 @@ cudaError_t launch_pool_cluster(const ClusterJob* jobs, int n_jobs, int max_n, i
       default: break;
     }
   }
-  return e == cudaSuccess ? launched(1) : e;
+  return e;
 }
 
 // QAOA forward on clusters (complex64): the cluster size for n qubits and the

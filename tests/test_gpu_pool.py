@@ -282,3 +282,27 @@ def test_t1t2_rejects_unphysical_times(gpu_lib):
         with pytest.raises(IQSError):
             pool.set_noise_t1t2(T1, T2, tg)
     pool.close()
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+def test_cluster_runs_replayed_from_graphs_across_shapes(gpu_lib, dtype):
+    """The cluster-resident runs are captured as one CUDA graph per (batch,
+    depth, noisy) shape; alternating shapes A, B, A (the job table is rebuilt
+    whenever the shape changes) gives the oracle's results every time, and a
+    repeated shape replays bit for bit."""
+    n = 12
+    shapes = [(4, 5), (2, 3), (4, 5)]
+    pool = gpu_lib.Pool(n, dtype, batch_max=4, depth_max=5)
+    pool.set_engine("cluster")
+    outs = []
+    for traj, depth in shapes:
+        ops = W.random_circuit_layers(n, depth, seed=40 + depth)
+        ang = W.rng(50 + depth).normal(0.0, 0.3, size=(traj, noise_count(n, depth), 2))
+        probs, mean = pool.run_brick(brick_unitaries(ops, n), ang)
+        tol = 1e-12 if dtype == "complex128" else 4 * c64_tol(depth)
+        for b in range(traj):
+            ref = oe.all_probabilities(oe.run_ops(n, oe.noisy_trajectory_ops(ops, ang[b])))
+            assert np.max(np.abs(probs[b] - ref)) <= tol, (traj, depth, b)
+        outs.append(probs)
+    np.testing.assert_array_equal(outs[0], outs[2])
+    pool.close()
