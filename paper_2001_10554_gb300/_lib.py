@@ -85,6 +85,7 @@ SIGNATURES = {
     "iqs_copy_to_device": ([C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64], C.c_int),
     "iqs_copy_to_host": ([C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64], C.c_int),
     "iqs_kq_autotune": ([C.c_void_p, C.c_int, C.c_void_p, _dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "iqs_kq_set_variant": ([C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int], C.c_int),
     "iqs_pool_autotune": ([C.c_void_p, C.c_int, C.c_int, C.c_int, _dp], C.c_int),
     "iqs_pool_tuning": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "iqs_flush": ([C.c_void_p], C.c_int),

@@ -191,6 +191,7 @@ iqs_status check_flag(iqs_reg* r) {
   CUDA_TRY(cudaStreamSynchronize(r->stream), "synchronise");
   if (f) {
     CUDA_TRY(cudaMemsetAsync(r->flag, 0, sizeof(unsigned), r->stream), "clear flag");
+    if (f & 2u) return fail(IQS_ETIMEOUT, "a bounded wait of a tensor-core kernel gave up");
     return fail(IQS_ERANGE, "an amplitude with |a| >= 2^64, Inf or NaN was met by emulated complex128 arithmetic");
   }
   return IQS_OK;
@@ -611,6 +612,20 @@ iqs_status iqs_kq_autotune(iqs_reg* reg, int k, const int* qubits, const double*
   if (variant) *variant = v;
   if (blocks_per_sm) *blocks_per_sm = ps;
   return check_flag(reg);
+}
+
+iqs_status iqs_kq_set_variant(iqs_reg* reg, int k, const int* qubits, int variant, int blocks_per_sm) {
+  TRACE();
+  CHECK_REG(reg);
+  if (qubits == nullptr) return fail(IQS_EINVAL, "qubits is NULL");
+  const int kmax = iqs::max_kq(reg->dtype);
+  if (k < 1 || k > kmax || k > reg->n) return fail(IQS_EINVAL, "k = %d outside [1, %d] for this register", k, kmax);
+  iqs_status s = check_qubit_set(reg, k, qubits);
+  if (s != IQS_OK) return s;
+  if (variant < 0 || variant > 4) return fail(IQS_EINVAL, "variant %d outside [0, 4]", variant);
+  if (blocks_per_sm < 1 || blocks_per_sm > 64) return fail(IQS_EINVAL, "blocks_per_sm %d outside [1, 64]", blocks_per_sm);
+  iqs::set_kq_choice(reg, k, qubits, variant, blocks_per_sm);
+  return IQS_OK;
 }
 
 iqs_status iqs_marginal(iqs_reg* reg, int k, const int* qubits, double* out) {

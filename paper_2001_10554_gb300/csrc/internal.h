@@ -118,6 +118,12 @@ cudaError_t launch_probabilities_raw(const void* data, int n, int dtype, cudaStr
 // ---- kgate.cu: dense k-qubit gates (k <= max_kq(dtype))
 int max_kq(int dtype);
 cudaError_t launch_kq(iqs_reg* r, int k, const int* qubits, const double* U);
+// iqs_kq_set_variant: the variant and blocks per SM used for this register's
+// dtype, arithmetic, k and target class from now on in this process.
+void set_kq_choice(const iqs_reg* r, int k, const int* qubits, int variant, int per_sm);
+// ---- kgate_tc.cu: complex128 k-qubit gates on the tensor cores (k = 2..4)
+bool kq_tensor_supported(int k);
+cudaError_t launch_kq_c128_tensor(iqs_reg* r, int k, const int* qubits, const double* U);
 
 // ---- measure.cu: qubit-group marginals and sampling
 int max_marginal_qubits();

@@ -12,8 +12,9 @@
 // coefficients are staged once per block in shared memory (all lanes read
 // the same address, so the reads broadcast).  complex64 computes in FP32
 // (k <= 5); complex128 in the double-float emulation (k <= 4; for k >= 2 on
-// paired .f32x2 instructions, two groups per thread) or, for small states or
-// on request, in native FP64.  One read and one write of the state per gate.
+// paired .f32x2 instructions, two groups per thread; for k = 3, 4 by default
+// on the tensor cores, kgate_tc.cu) or, for small states or on request, in
+// native FP64.  One read and one write of the state per gate.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -497,7 +498,7 @@ Targets<K> make_targets(const int* qubits) {
 // Kernel choices of iqs_kq_autotune, per (dtype, emulated arithmetic, k,
 // targets below bit 5): the variant (kVarAuto: the fixed rule below) and the
 // grid size in blocks per SM of the grid-stride variants.
-enum { kVarAuto = 0, kVarTiled = 1, kVarUnrolled = 2, kVarRows = 3 };
+enum { kVarAuto = 0, kVarTiled = 1, kVarUnrolled = 2, kVarRows = 3, kVarTensor = 4 };
 struct KqChoice {
   int variant = kVarAuto;
   int per_sm = 8;
@@ -525,7 +526,7 @@ void load_kq_cache_locked() {
     char kind[16];
     int dt, em, k, low, var, per_sm;
     if (std::sscanf(line, "%15s %d %d %d %d %d %d", kind, &dt, &em, &k, &low, &var, &per_sm) == 7 &&
-        std::strcmp(kind, "kq") == 0 && var >= 0 && var <= 3 && per_sm >= 1 && per_sm <= 64)
+        std::strcmp(kind, "kq") == 0 && var >= 0 && var <= 4 && per_sm >= 1 && per_sm <= 64)
       g_kq_choice[std::make_tuple(dt, em, k, low)] = KqChoice{var, per_sm};
   }
   std::fclose(f);
@@ -585,6 +586,9 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U, KqChoice ch
     }
   } else {
     if constexpr (K <= kMaxK128) {
+      // the fixed rule: k >= 3 on the tensor cores (k = 2 is faster as paired FP32 below)
+      if (kq_tensor_supported(K) && (ch.variant == kVarTensor || (ch.variant == kVarAuto && K >= 3)))
+        return launch_kq_c128_tensor(r, K, qubits, U);
       constexpr int M = 2 * D;
       UDF<K> u;
       for (int row = 0; row < D; ++row)
@@ -628,6 +632,12 @@ cudaError_t launch_kq(iqs_reg* r, int k, const int* qubits, const double* U) {
   return launch_kq_with(r, k, qubits, U, kq_choice(r, k, qubits));
 }
 
+void set_kq_choice(const iqs_reg* r, int k, const int* qubits, int variant, int per_sm) {
+  std::lock_guard<std::mutex> lock(g_kq_mutex);
+  load_kq_cache_locked();
+  g_kq_choice[kq_key(r, k, qubits)] = KqChoice{variant, per_sm};
+}
+
 // Times every variant and grid size of a k-qubit gate on these targets on the
 // register's state (applying U and then its conjugate transpose, so the state
 // comes back up to rounding), and keeps the fastest for (dtype, arithmetic,
@@ -648,6 +658,7 @@ cudaError_t tune_kq(iqs_reg* r, int k, const int* qubits, const double* U, doubl
   const int vars[4] = {kVarAuto, kVarTiled, kVarUnrolled, kVarRows};
   for (int v : vars)
     for (int ps : {4, 8, 16, 32}) cands.push_back(KqChoice{v, ps});
+  if (use_emulated(r) && kq_tensor_supported(k)) cands.push_back(KqChoice{kVarTensor, 1});  // one CTA per SM
   double best = 1e300;
   KqChoice pick;
   for (const KqChoice& c : cands) {

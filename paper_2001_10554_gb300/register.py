@@ -223,6 +223,12 @@ class Register:
              C.byref(ms), C.byref(var), C.byref(ps))
         return {"best_ms": ms.value, "variant": var.value, "blocks_per_sm": ps.value}
 
+    def kq_set_variant(self, qubits, variant: int, blocks_per_sm: int = 8) -> None:
+        """Use k-qubit gate variant ``variant`` (0 fixed rule, 1 tiles, 2 unrolled, 3 rows, 4 tensor cores)
+        for this register's dtype, arithmetic, k and target class (iqs_kq_set_variant)."""
+        qs = [int(q) for q in qubits]
+        call("iqs_kq_set_variant", self._h, len(qs), (C.c_int * len(qs))(*qs), int(variant), int(blocks_per_sm))
+
     # ------------------------------------------------------------ reductions
     def probability(self, q: int) -> float:
         out = C.c_double()

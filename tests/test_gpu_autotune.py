@@ -54,7 +54,8 @@ def test_kq_autotune_keeps_results_and_persists(gpu_lib, dtype, qubits, tmp_path
     start = psi if dtype == "complex128" else psi.astype(np.complex64)
     reg.upload(start)
     choice = reg.kq_autotune(qubits, U)
-    assert 0 <= choice["variant"] <= 3 and choice["blocks_per_sm"] in (4, 8, 16, 32)
+    assert (0 <= choice["variant"] <= 3 and choice["blocks_per_sm"] in (4, 8, 16, 32)) or \
+        (choice["variant"] == 4 and choice["blocks_per_sm"] == 1)
     tol = 1e-12 if dtype == "complex128" else 8 * 2.0 ** -24 * 80
     # tuning applied U and U^dagger an even number of times: the state is back up to rounding
     assert np.max(np.abs(reg.download().astype(np.complex128) - start.astype(np.complex128))) <= tol
