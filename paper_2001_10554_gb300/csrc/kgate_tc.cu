@@ -228,7 +228,43 @@ __device__ __forceinline__ void stage_group(uint8_t* X, int m, int c0, const dou
   }
 }
 
+// With a target below bit 7 the elements of neighbouring groups interleave
+// in memory, and one thread per group would read and write them strided.
+// There a warp moves its 32 groups together: in round j lane i handles
+// element c0 + i % DT of the warp's group j 32/DT + i / DT, so consecutive
+// lanes touch consecutive elements; the group's base index comes from its
+// owner lane by shuffle.  ``mw`` is the warp's first row in the tile.
 template <int K>
+__device__ __forceinline__ void stage_warp(uint8_t* X, int mw, int lane, int c0, const double2* a, uint64_t base_own,
+                                           bool act_own, uint64_t off_lane) {
+  constexpr int DT = TcShape<K>::DT;
+  const int cl = lane % DT;
+#pragma unroll
+  for (int j = 0; j < DT; ++j) {
+    const int src = j * (32 / DT) + lane / DT;
+    const uint64_t b = __shfl_sync(0xffffffffu, base_own, src);
+    const int act = __shfl_sync(0xffffffffu, (int)act_own, src);
+    if (act) {
+      const uint32_t dst = tc::smem_u32(X + ((size_t)(c0 + cl) * kRows + mw + src) * 16);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(a + b + off_lane) : "memory");
+    }
+  }
+}
+
+// Staging slot of output element c of row ``ml`` of a warp (ml < 32) for the
+// strided write-back: the warp's own rows of the A operand (its 4 row groups
+// and its columns, in slices 0..3), which no other warp touches and which the
+// finished products no longer need.  Element c of a row sits at c ^ (ml % DT),
+// so the 8 lanes of one store phase hit 8 different 16-byte bank groups.
+template <int K>
+__device__ __forceinline__ uint8_t* out_slot(uint8_t* A, int wq, int sub, int ml, int c) {
+  using S = TcShape<K>;
+  const int q = ml * S::DT + (c ^ (ml % S::DT));
+  const int chunk = q / S::RT, idx = q % S::RT;
+  return A + (chunk >> 2) * S::A_SLICE + (4 * wq + (chunk & 3)) * S::SBO + sub * S::RT * 16 + idx * 16;
+}
+
+template <int K, bool LOW>
 __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
     k_kgate_c128_tc(double2* __restrict__ a, uint64_t n_groups, const __grid_constant__ TcParams<K> P,
                     unsigned* flag) {
@@ -280,15 +316,24 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   unsigned bad = 0;
   bool stalled = false;
   uint64_t tile = (uint64_t)blockIdx.x * S::TEAMS + team;
+  const int lane = tid & 31, wq = m >> 5, mw = m & 96;
+  const uint64_t off_lane = LOW ? P.off[c0 + lane % S::DT] : 0;
   // the first tile's input; each later tile's is requested while this one is computed
-  if (tile < n_tiles && tile * kRows + m < n_groups)
+  if constexpr (LOW) {
+    if (tile < n_tiles) {
+      const uint64_t g1 = tile * kRows + m;
+      stage_warp<K>(X, mw, lane, c0, a, g1 < n_groups ? group_base<K>(g1, P) : 0, g1 < n_groups, off_lane);
+    }
+  } else if (tile < n_tiles && tile * kRows + m < n_groups) {
     stage_group<K>(X, m, c0, a, group_base<K>(tile * kRows + m, P), P);
+  }
   asm volatile("cp.async.commit_group;" ::: "memory");
   for (; tile < n_tiles; tile += stride) {
     const uint64_t g = tile * kRows + m;
     const bool act = g < n_groups;
     const uint64_t base = act ? group_base<K>(g, P) : 0;
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if constexpr (LOW) __syncwarp();  // the warp's copies landed in each other's rows
     uint32_t lo[S::RT], hi[S::RT];
 #pragma unroll
     for (int c = 0; c < S::DT; ++c) {
@@ -309,8 +354,13 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
     // those reads)
     {
       const uint64_t gn = g + stride * kRows;
-      if (tile + stride < n_tiles && gn < n_groups && emax != 0x800u)
+      if constexpr (LOW) {
+        __syncwarp();  // every lane has read its rows before any lane refills them
+        if (tile + stride < n_tiles)
+          stage_warp<K>(X, mw, lane, c0, a, gn < n_groups ? group_base<K>(gn, P) : 0, gn < n_groups, off_lane);
+      } else if (tile + stride < n_tiles && gn < n_groups && emax != 0x800u) {
         stage_group<K>(X, m, c0, a, group_base<K>(gn, P), P);
+      }
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
     if constexpr (S::TPG > 1) {  // the group's exponent from the team's partial ones
@@ -362,7 +412,7 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
 #pragma unroll
       for (int acc = 0; acc < kAcc; ++acc) tc::tmem_ld8(tacc + tlane + (uint32_t)(acc * S::NP + col), v[acc]);
       tc::tmem_wait_ld();
-      if (act) {
+      if (act || LOW) {
 #pragma unroll
         for (int q = 0; q < 8; q += 2) {
           const int o = col + q;
@@ -377,9 +427,25 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
             y.x = scale_out(dfx::join(s0, l0), e0 + P.adj[o], bad);
             y.y = scale_out(dfx::join(s1, l1), e0 + P.adj[o + 1], bad);
           }
-          a[base + P.off[o / 2]] = y;
+          if constexpr (LOW)
+            *reinterpret_cast<double2*>(out_slot<K>(A, wq, sub, lane, ch * 4 + q / 2)) = y;
+          else
+            a[base + P.off[o / 2]] = y;
         }
       }
+    }
+    if constexpr (LOW) {  // write-back in element order, as the loads
+      __syncwarp();
+      const int cl = lane % S::DT;
+#pragma unroll
+      for (int j = 0; j < S::DT; ++j) {
+        const int src = j * (32 / S::DT) + lane / S::DT;
+        const uint64_t b = __shfl_sync(0xffffffffu, base, src);
+        const int ok_src = __shfl_sync(0xffffffffu, (int)act, src);
+        const double2 y = *reinterpret_cast<const double2*>(out_slot<K>(A, wq, sub, src, cl));
+        if (ok_src) a[b + off_lane] = y;
+      }
+      __syncwarp();  // the slots are this warp's A rows again for the next tile
     }
     tc::fence_before();
   }
@@ -450,17 +516,20 @@ cudaError_t launch_tc(iqs_reg* r, const int* qubits, const double* U) {
   std::lock_guard<std::mutex> lock(mu);
   make_params<K>(qubits, U, P);
   const size_t smem = std::max<size_t>(S::SMEM, 120 * 1024);  // > half an SM's shared memory: one CTA per SM
-  static PerDevice attr;
+  bool low = false;
+  for (int j = 0; j < K; ++j) low |= qubits[j] < 7;
+  auto kern = low ? k_kgate_c128_tc<K, true> : k_kgate_c128_tc<K, false>;
+  static PerDevice attr[2];
   int dummy = 0;
-  cudaError_t e = attr.get(&dummy, [&](int* x) {
+  cudaError_t e = attr[low ? 1 : 0].get(&dummy, [&](int* x) {
     *x = 1;
-    return cudaFuncSetAttribute(k_kgate_c128_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (e != cudaSuccess) return e;
   const uint64_t n_groups = num_amps(r) >> K;
   const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n_tiles + S::TEAMS - 1) / S::TEAMS, kSMs));
-  k_kgate_c128_tc<K><<<grid, S::THREADS, smem, r->stream>>>((double2*)r->data, n_groups, P, r->flag);
+  kern<<<grid, S::THREADS, smem, r->stream>>>((double2*)r->data, n_groups, P, r->flag);
   return launched(1);
 }
 
