@@ -49,7 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--qubits", type=int, default=30)
     ap.add_argument("--math", choices=["auto", "emulated", "native"], default="auto")
     ap.add_argument("--cpu-qubits", type=int, default=23, help="state size of the CPU-oracle sample")
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the complex64 32q sweep and the QAOA sections")
