@@ -32,18 +32,22 @@
 // max|W| * max|x| per output (max over the row and the group), the order of
 // an FP64 dot product's error, with the FP64 pipe unused.
 //
-// Kernel: one CTA per SM with 3 (k = 4) or 4 (k <= 3) warpgroups.  Thread m
-// of a warpgroup owns group row m of a 128-group tile: it loads the group
-// (one read of the state), writes its 6 digit slices as bf16 into the
-// warpgroup's A operand in shared memory (K-major core matrices), and after
-// the warpgroup's barrier thread 0 issues 21 digit-pair products (x R/16
-// K-steps) of M = 128, N = max(R, 16) into the warpgroup's five TMEM
-// accumulators and commits them to an mbarrier.  Each thread then reads its
-// own TMEM lane, rounds the five sums to FP64 and writes the group back (one
-// write).  The warpgroups of a CTA take turns on the tensor cores while the
-// others load, split or write.  Waits on the mbarrier are bounded: a wait
-// that gives up sets bit 1 of the error flag (IQS_ETIMEOUT) and the CTA
-// frees its tensor memory and returns.
+// Kernel: one CTA per SM, split into teams that each work on one 128-group
+// tile at a time (k = 4: two teams of 256 threads, two threads per group;
+// k = 3: five teams of 128; k = 2: six teams of 128).  Each thread stages its
+// part of the next tile's groups into shared memory with cp.async while the
+// current tile is computed (one read of the state), splits its reals into
+// six digit slices written as bf16 into the team's A operand (K-major core
+// matrices), and after the team's barrier one thread issues the 21
+// digit-pair products (x R/16 K-steps) of M = 128, N = max(R, 16) into the
+// team's five TMEM accumulators and commits them to an mbarrier.  Each thread
+// then reads its own TMEM lane, rounds the sums to FP64 and writes its part
+// of the group back (one write).  The teams of a CTA take turns on the
+// tensor cores while the others load, split or write.  With a target below
+// bit 7 a warp moves its 32 groups together so that the copies stay
+// coalesced.  Waits on the mbarrier are bounded: a wait that gives up sets
+// bit 1 of the error flag (IQS_ETIMEOUT) and the CTA frees its tensor memory
+// and returns.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
