@@ -77,7 +77,19 @@ __global__ void __launch_bounds__(kThreads) k_norm2(const V* __restrict__ a, uin
                                                      unsigned* flag) {
   dfx::Acc acc;
   unsigned bad = 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+  // four loads in flight per thread; the sums keep the one-at-a-time order
+  const uint64_t S = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * S < n; i += 4 * S) {
+    const V v[4] = {a[i], a[i + S], a[i + 2 * S], a[i + 3 * S]};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float p, e;
+      abs2(v[u], p, e, bad);
+      acc.add(p, e);
+    }
+  }
+  for (; i < n; i += S) {
     float p, e;
     abs2(a[i], p, e, bad);
     acc.add(p, e);
@@ -311,16 +323,28 @@ __global__ void __launch_bounds__(kThreads) k_expect_pair(const V* __restrict__ 
                                                            uint64_t zm, int imag, double* partials, unsigned* flag) {
   dfx::Acc acc;
   unsigned bad = 0;
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n_half; k += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t x = insert_zero(k, h);
-    const uint64_t y = x ^ xm;
+  // two pairs (four loads) in flight per thread; the sums keep the
+  // one-at-a-time order
+  const uint64_t S = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  auto term = [&](uint64_t x, const V& ax, const V& ay) {
     float p, e;
-    zterm(a[x], a[y], imag != 0, p, e, bad);
+    zterm(ax, ay, imag != 0, p, e, bad);
     if (__popcll(x & zm) & 1) {
       p = -p;
       e = -e;
     }
     acc.add(p, e);
+  };
+  for (; k + S < n_half; k += 2 * S) {
+    const uint64_t x0 = insert_zero(k, h), x1 = insert_zero(k + S, h);
+    const V a0 = a[x0], b0 = a[x0 ^ xm], a1 = a[x1], b1 = a[x1 ^ xm];
+    term(x0, a0, b0);
+    term(x1, a1, b1);
+  }
+  for (; k < n_half; k += S) {
+    const uint64_t x = insert_zero(k, h);
+    term(x, a[x], a[x ^ xm]);
   }
   if (bad) atomicOr(flag, 1u);
   double v[1] = {acc.value()};
