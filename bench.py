@@ -505,6 +505,19 @@ def qaoa_section(iqs, torch):
                                     "oracle": "stored-state adjoint, FP64 (tests/golden/qaoa_oracle.json)"}
         else:
             row["err_vs_oracle"] = None
+        # the FP64 oracle beside it: one evaluation (energy + 2p derivatives,
+        # stored-state adjoint) timed here up to 20 qubits; at 24 qubits the
+        # time recorded when the golden file was written
+        if n <= 20:
+            from oracle import qaoa as oq
+            t0 = time.perf_counter()
+            oq.qaoa_energy_grad_stored(n, edges, gm[0], bt[0])
+            row["oracle_s_per_eval"] = {"value": round(time.perf_counter() - t0, 2), "where": "this host, numpy FP64"}
+        elif ok:
+            secs = [r.get("seconds") for r in g["sets"].values() if r.get("seconds")]
+            if secs:
+                row["oracle_s_per_eval"] = {"value": round(float(np.median(secs)), 1),
+                                            "where": "stored: measured by make_qaoa_oracle.py on the build host"}
         out["rows"].append(row)
     # large adjoint: 28 qubits, p = 4, one parameter set, complex64 with FP64 reductions
     n = 28
@@ -529,6 +542,10 @@ def qaoa_section(iqs, torch):
             adj["grad_components_compared"] = len(have)
             adj["oracle"] = ("oracle energy; gradient by central differences (h = 1e-5) of oracle energies "
                              "(tests/golden/qaoa_oracle.json)")
+    if lg and lg.get("seconds"):
+        secs = list(lg["seconds"].values())
+        adj["oracle_s_per_energy"] = {"value": round(float(np.median(secs)), 1), "energies_for_gradient": 1 + 2 * 8,
+                                      "where": "stored: measured by make_qaoa_oracle.py on the build host"}
     out["adjoint_28q"] = adj
     rows = {r["n"]: r for r in out["rows"]}
     h24 = rows[24]
@@ -540,7 +557,9 @@ def qaoa_section(iqs, torch):
                        "by_n": {str(r["n"]): [r["batched_c64_evals_per_s"], r["plain_c128_evals_per_s"], r["ratio"],
                                               (r["err_vs_oracle"] or {}).get("energy_c64_max")]
                                 for r in out["rows"]},
-                       "by_n_fields": "batched c64 evals/s, plain c128 evals/s, ratio, c64 energy error vs oracle"}
+                       "by_n_fields": "batched c64 evals/s, plain c128 evals/s, ratio, c64 energy error vs oracle",
+                       "oracle_s_per_eval": {str(r["n"]): r["oracle_s_per_eval"]["value"]
+                                             for r in out["rows"] if r.get("oracle_s_per_eval")}}
     return out
 
 
@@ -752,6 +771,8 @@ def compact(extra: dict, native) -> dict:
                               for k in ("ms_per_energy_and_gradient", "model_GBs", "energy_err_vs_oracle",
                                         "grad_err_vs_oracle_central_diff_max", "grad_components_compared")
                               if k in a}
+        if a.get("oracle_s_per_energy"):
+            out["adjoint_28q"]["oracle_s_per_energy"] = a["oracle_s_per_energy"]["value"]
     c = extra.get("c64_32q")
     if c:
         out["c64_32q"] = {"GBs": c["value"], "avg_1q_GBs": c["avg_1q_GBs"],
