@@ -432,6 +432,29 @@ def kq_measure_section(iqs, torch, dev):
         reg.close()
         del st
         torch.cuda.empty_cache()
+    # the FP64 oracle beside them, on a 22-qubit complex128 state (64 MiB):
+    # one call each, same GB/s accounting
+    import workloads as W2
+    from oracle import statevector as sv
+    n = 22
+    psi = W2.gaussian_state(n, SEED_STATE)
+    nb = 16 * (1 << n)
+    orc = {"state": "22-qubit complex128, numpy FP64, this host", "apply_kq_high": []}
+    for k in (2, 3, 4):
+        U = np.linalg.qr(g.normal(size=(1 << k, 1 << k)) + 1j * g.normal(size=(1 << k, 1 << k)))[0]
+        t0 = time.perf_counter()
+        sv.apply_kq(psi, list(range(n - k, n)), U)
+        dt = time.perf_counter() - t0
+        orc["apply_kq_high"].append({"k": k, "ms": round(dt * 1e3, 1), "GBs": round(2 * nb / dt / 1e9, 3)})
+    t0 = time.perf_counter()
+    sv.marginal(psi, [0, 3, 7, 9, 12, 15, 18, 19, 20, 21])
+    dt = time.perf_counter() - t0
+    orc["marginal_10q"] = {"ms": round(dt * 1e3, 1), "GBs": round(nb / dt / 1e9, 3)}
+    t0 = time.perf_counter()
+    sv.sample(psi, g.uniform(size=1 << 16))
+    dt = time.perf_counter() - t0
+    orc["sample_2p16"] = {"ms": round(dt * 1e3, 1), "GBs_state_pass": round(nb / dt / 1e9, 3)}
+    out["oracle"] = orc
     return out
 
 
@@ -796,6 +819,8 @@ def compact(extra: dict, native) -> dict:
     if k:
         out["kq_high_GBs"] = {nm: {str(row["k"]): row["GBs"] for row in k[nm]["apply_kq"] if row["targets"] == "high"}
                               for nm in ("c128_30q", "c64_32q")}
+        if k.get("oracle"):
+            out["kq_high_GBs"]["oracle_c128_22q"] = {str(row["k"]): row["GBs"] for row in k["oracle"]["apply_kq_high"]}
     ps = extra.get("pso_qaoa")
     if ps:
         out["pso_evals_per_s"] = round(float(np.mean([row["evaluations_per_s"] for row in ps["rows"]])), 1)
