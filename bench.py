@@ -385,7 +385,7 @@ def kq_measure_section(iqs, torch, dev):
                        "10-qubit marginal, 2^20-shot sampling",
            "timing": "median of 5 calls, each bracketed by CUDA events on the register's stream, after a warm-up"}
     g = W.rng(77)
-    for n, dt, name, ks in ((30, torch.complex128, "c128_30q", (2, 3, 4)), (32, torch.complex64, "c64_32q", (2, 3, 4, 5))):
+    for n, dt, name, ks in ((30, torch.complex128, "c128_30q", (2, 3, 4, 5)), (32, torch.complex64, "c64_32q", (2, 3, 4, 5))):
         N = 1 << n
         amp = 16 if dt == torch.complex128 else 8
         stream = torch.cuda.Stream(dev)

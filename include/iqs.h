@@ -181,9 +181,9 @@ iqs_status iqs_apply_zz_phase(iqs_reg* reg, int n_edges, const int32_t* edges,
  * 2^k x 2^k matrix U acts on qubits[0..k); bit j of U's row and column index
  * is the value of qubits[j].  ``U`` is row-major, (re, im) doubles: entry
  * (row, col) at U[2 * (row * 2^k + col)].  k: 1..5 for IQS_C64 (computed in
- * FP32), 1..4 for IQS_C128 (double-float emulation or native FP64 as for
- * iqs_apply_1q; with the emulation, k = 3 and 4 run by default as exact
- * bf16 digit products on the tcgen05 tensor cores, an FP64-accurate
+ * FP32), 1..5 for IQS_C128 (double-float emulation or native FP64 as for
+ * iqs_apply_1q; with the emulation, k = 3..5 run by default as exact bf16
+ * digit products on the tcgen05 tensor cores, an FP64-accurate
  * contraction).  The qubits must be distinct and in [0, n); U must be
  * finite.  IQS_EINVAL otherwise, with the state untouched.  Asynchronous. */
 iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U);
@@ -191,7 +191,7 @@ iqs_status iqs_apply_kq(iqs_reg* reg, int k, const int* qubits, const double* U)
 /* Project autotuner of iqs_apply_kq: times every kernel variant (0 the fixed
  * rule, 1 shared-memory tiles for targets below bit 5, 2 one group per thread
  * with U in constant memory, 3 rolled rows with U in shared memory, and for
- * emulated complex128 with k = 2..4 also 4, the tensor-core product of exact
+ * emulated complex128 with k = 2..5 also 4, the tensor-core product of exact
  * bf16 digit slices) at 4, 8, 16 and 32 blocks per SM (variant 4: one block
  * per SM), on this register's state with these targets,
  * applying U and its conjugate transpose alternately (an even number of

@@ -12,9 +12,10 @@
 // coefficients are staged once per block in shared memory (all lanes read
 // the same address, so the reads broadcast).  complex64 computes in FP32
 // (k <= 5); complex128 in the double-float emulation (k <= 4; for k >= 2 on
-// paired .f32x2 instructions, two groups per thread; for k = 3, 4 by default
-// on the tensor cores, kgate_tc.cu) or, for small states or on request, in
-// native FP64.  One read and one write of the state per gate.
+// paired .f32x2 instructions, two groups per thread) or, by default for
+// k = 3..5, as exact digit products on the tensor cores (kgate_tc.cu), or,
+// for small states or on request, in native FP64.  One read and one write
+// of the state per gate.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -32,7 +33,7 @@
 namespace iqs {
 namespace {
 
-constexpr int kMaxK64 = 5, kMaxK128 = 4;
+constexpr int kMaxK64 = 5, kMaxK128 = 5;
 
 // Target positions ascending (zero insertion) and, per element c of a group,
 // the index offset sum_j bit_j(c) << qubits[j].
@@ -586,9 +587,12 @@ cudaError_t launch_k(iqs_reg* r, const int* qubits, const double* U, KqChoice ch
     }
   } else {
     if constexpr (K <= kMaxK128) {
-      // the fixed rule: k >= 3 on the tensor cores (k = 2 is faster as paired FP32 below)
-      if (kq_tensor_supported(K) && (ch.variant == kVarTensor || (ch.variant == kVarAuto && K >= 3)))
+      // the fixed rule: k >= 3 on the tensor cores (k = 2 is faster as paired
+      // FP32 below; k = 5 has only the tensor-core kernel)
+      if (kq_tensor_supported(K) && (K == 5 || ch.variant == kVarTensor || (ch.variant == kVarAuto && K >= 3)))
         return launch_kq_c128_tensor(r, K, qubits, U);
+    }
+    if constexpr (K <= 4) {
       constexpr int M = 2 * D;
       UDF<K> u;
       for (int row = 0; row < D; ++row)

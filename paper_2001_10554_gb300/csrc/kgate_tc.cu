@@ -17,12 +17,12 @@
 //     F = sign(x) floor(|x| 2^(1075 - e_max)) with |F| < 2^53, written in six balanced
 //     radix-2^9 digits f_0..f_5 in [-256, 256]
 //     (x 2^(1030 - e_max) = sum_l f_l 2^(-9 l));
-//   * each row of W is scaled the same way on the host and split into six
-//     digits b_0..b_5;
+//   * each row of W is scaled the same way and split into six digits
+//     b_0..b_5, exactly in FP64, by every CTA in its prologue;
 //   * a digit times 2^(-9 l) is exact in bf16 (at most 8 significant bits),
 //     a product of two digits exact in FP32, and the tensor cores' FP32 sums
 //     over the R terms of one digit level d = l + j are exact integers times
-//     2^(-9 d) for d <= 3 (|sum| <= (d + 1) R 2^16 < 2^24 for R <= 32);
+//     2^(-9 d) for d <= 3 (|sum| <= (d + 1) R 2^16 <= 2^24 for R <= 64);
 //   * levels 4 and 5 share one accumulator (its rounding is below 2^-56 of
 //     the row's scale) and levels above 5 are dropped (at most 7 * 2^-52 of
 //     max|W| max|x| per term; the balanced digits make it far smaller in
@@ -33,8 +33,9 @@
 // an FP64 dot product's error, with the FP64 pipe unused.
 //
 // Kernel: one CTA per SM, split into teams that each work on one 128-group
-// tile at a time (k = 4: two teams of 256 threads, two threads per group;
-// k = 3: five teams of 128; k = 2: six teams of 128).  Each thread stages its
+// tile at a time (k = 5: one team of 512 threads, four threads per group;
+// k = 4: two teams of 256 threads, two threads per group; k = 3: five teams
+// of 128; k = 2: six teams of 128).  Each thread stages its
 // part of the next tile's groups into shared memory with cp.async while the
 // current tile is computed (one read of the state), splits its reals into
 // six digit slices written as bf16 into the team's A operand (K-major core
@@ -74,10 +75,10 @@ struct TcShape {
   static constexpr int NP = R < 16 ? 16 : R;  // MMA N extent (padded rows of W are zero)
   // A team of TPG warpgroups works on one 128-group tile: thread (sub, m)
   // owns reals [sub RT, (sub + 1) RT) of group row m.  TEAMS teams per CTA.
-  static constexpr int TPG = K >= 4 ? 2 : 1;
+  static constexpr int TPG = K >= 5 ? 4 : K == 4 ? 2 : 1;
   static constexpr int RT = R / TPG;
   static constexpr int DT = D / TPG;
-  static constexpr int TEAMS = K >= 4 ? 2 : K == 3 ? 5 : 6;
+  static constexpr int TEAMS = K >= 5 ? 1 : K == 4 ? 2 : K == 3 ? 5 : 6;
   static constexpr int TEAM_THREADS = TPG * 128;
   static constexpr int THREADS = TEAMS * TEAM_THREADS;
   static constexpr uint32_t SBO = (KP / 8) * 128;
@@ -86,8 +87,11 @@ struct TcShape {
   static constexpr uint32_t B_SLICE = NP * KP * 2;
   static constexpr uint32_t B_BYTES = kSlices * B_SLICE;
   static constexpr uint32_t X_BYTES = kRows * D * 16;  // staged input of one tile: [element c][row m]
-  // shared memory: TMEM address slot at 0, mbarriers from 8, partial group
-  // exponents from 1024 (TEAMS x TPG x 128 words), then B, A, X
+  // shared memory: TMEM address slot at 0, mbarriers from 8, W's row
+  // exponents from 128 (NP words), partial group exponents from 1024
+  // (TEAMS x TPG x 128 words), then B, A, X
+  static constexpr uint32_t RO_OFF = 128;
+  static_assert(8 + 8 * TEAMS <= RO_OFF && RO_OFF + 4 * NP <= 1024, "header area");
   static constexpr uint32_t EMX_OFF = 1024;
   static constexpr uint32_t B_OFF = 4096;
   static_assert(EMX_OFF + TEAMS * TPG * 128 * 4 <= B_OFF, "exponent exchange area");
@@ -102,10 +106,9 @@ struct TcShape {
 
 template <int K>
 struct TcParams {
-  int pos[K];                                  // target positions, ascending
-  uint64_t off[1 << K];                        // index offset of group element c
-  int adj[TcShape<K>::NP];                     // per output real: ro - 1038 (see scale_out)
-  uint4 b[TcShape<K>::B_BYTES / 16];           // W's digit slices, core-matrix layout
+  int pos[K];                    // target positions, ascending
+  uint64_t off[1 << K];          // index offset of group element c
+  double u[2 << (2 * K)];        // U row-major, (re, im) pairs
 };
 
 template <int K>
@@ -220,6 +223,33 @@ __device__ __forceinline__ void issue_mmas(uint32_t tacc, uint32_t a_s, uint32_t
   }
 }
 
+// Entry (o, i) of U's real form W.
+template <int K>
+__device__ __forceinline__ double w_entry(const TcParams<K>& P, int o, int i) {
+  constexpr int D = 1 << K;
+  const int r = o >> 1, c = i >> 1;
+  const double ur = P.u[2 * (r * D + c)], ui = P.u[2 * (r * D + c) + 1];
+  return (o & 1) == 0 ? ((i & 1) == 0 ? ur : -ui) : ((i & 1) == 0 ? ui : ur);
+}
+
+// ro with max_i |W[o][i]| in [2^(ro - 1), 2^ro) (0 for a zero or padding
+// row): row o is split after scaling by 2^(8 - ro), and its outputs carry
+// 2^(ro - 1038) besides the group's own power of two.
+template <int K>
+__device__ __forceinline__ int row_exponent(const TcParams<K>& P, int o) {
+  constexpr int R = 2 << K;
+  if (o >= R) return 0;
+  double mx = 0.0;
+  for (int i = 0; i < R; ++i) mx = fmax(mx, fabs(w_entry<K>(P, o, i)));
+  int ro = 0;
+  if (mx > 0.0) frexp(mx, &ro);
+  return ro;
+}
+
+__device__ __forceinline__ float digit_weight(int j) {
+  return __uint_as_float((uint32_t)(127 - 9 * j) << 23);  // 2^(-9 j), j <= 5
+}
+
 // Stage elements [c0, c0 + DT) of group ``g`` into the team's input buffer
 // (layout [element c][row m], 16 bytes each).
 template <int K>
@@ -281,11 +311,26 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   uint8_t* As = smem + S::A_OFF;
   const int tid = threadIdx.x, team = tid / S::TEAM_THREADS, sub = (tid / 128) % S::TPG, m = tid & 127;
 
-  // W's slices to shared memory; the A slices zeroed once, so that their
-  // padding columns (k = 2: 8 reals padded to K = 16) stay zero.
-  for (int i = tid; i < (int)(S::B_BYTES / 16); i += blockDim.x) reinterpret_cast<uint4*>(Bs)[i] = P.b[i];
+  // W's digit slices (zero padding included) and row exponents; the A slices
+  // zeroed once, so that their padding columns (k = 2: 8 reals padded to
+  // K = 16) stay zero.
+  int* sro = reinterpret_cast<int*>(smem + S::RO_OFF);
+  for (int i = tid; i < (int)(S::B_BYTES / 16); i += blockDim.x) reinterpret_cast<uint4*>(Bs)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < (int)(S::TEAMS * S::A_BYTES / 16); i += blockDim.x)
     reinterpret_cast<uint4*>(As)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int o = tid; o < S::NP; o += blockDim.x) sro[o] = row_exponent<K>(P, o);
+  __syncthreads();
+  for (int e = tid; e < S::R * S::R; e += blockDim.x) {
+    const int o = e / S::R, i = e % S::R;
+    double rem = ldexp(w_entry<K>(P, o, i), 8 - sro[o]);
+    uint16_t* at = reinterpret_cast<uint16_t*>(Bs + (o / 8) * S::SBO + (i / 8) * 128 + (o % 8) * 16 + (i % 8) * 2);
+#pragma unroll
+    for (int j = 0; j < kSlices; ++j) {
+      const double b = rint(rem);
+      rem = (rem - b) * 512.0;
+      at[j * (S::B_SLICE / 2)] = (uint16_t)(__float_as_uint(__double2float_rn(b) * digit_weight(j)) >> 16);
+    }
+  }
   if (tid == 0) {
     for (int w = 0; w < S::TEAMS; ++w) tc::mbar_init(mbar0 + 8 * w, 1);
     tc::mbar_init_fence();
@@ -310,11 +355,10 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
   const uint64_t stride = (uint64_t)gridDim.x * S::TEAMS;
   // row exponent range of W (the fast epilogue needs every output normal)
-  int adj_lo = P.adj[0], adj_hi = P.adj[0];
-#pragma unroll
+  int adj_lo = sro[0] - 1038, adj_hi = adj_lo;
   for (int o = 1; o < S::R; ++o) {
-    adj_lo = min(adj_lo, P.adj[o]);
-    adj_hi = max(adj_hi, P.adj[o]);
+    adj_lo = min(adj_lo, sro[o] - 1038);
+    adj_hi = max(adj_hi, sro[o] - 1038);
   }
   uint32_t phase = 0;
   unsigned bad = 0;
@@ -425,11 +469,11 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
           combine(v, q + 1, s1, l1);
           double2 y;
           if (fast) {
-            y.x = join_scaled(s0, l0, e0 + P.adj[o]);
-            y.y = join_scaled(s1, l1, e0 + P.adj[o + 1]);
+            y.x = join_scaled(s0, l0, e0 + sro[o] - 1038);
+            y.y = join_scaled(s1, l1, e0 + sro[o + 1] - 1038);
           } else {
-            y.x = scale_out(dfx::join(s0, l0), e0 + P.adj[o], bad);
-            y.y = scale_out(dfx::join(s1, l1), e0 + P.adj[o + 1], bad);
+            y.x = scale_out(dfx::join(s0, l0), e0 + sro[o] - 1038, bad);
+            y.y = scale_out(dfx::join(s1, l1), e0 + sro[o + 1] - 1038, bad);
           }
           if constexpr (LOW)
             *reinterpret_cast<double2*>(out_slot<K>(A, wq, sub, lane, ch * 4 + q / 2)) = y;
@@ -467,9 +511,6 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   }
 }
 
-// W's digit slices and row exponents on the host (FP64, exact): row o is
-// scaled by 2^(8 - ro) with max_i |W[o][i]| < 2^ro, then peeled into six
-// balanced radix-2^9 digits.
 template <int K>
 void make_params(const int* qubits, const double* U, TcParams<K>& P) {
   using S = TcShape<K>;
@@ -483,39 +524,13 @@ void make_params(const int* qubits, const double* U, TcParams<K>& P) {
     for (int j = 0; j < K; ++j) o |= (uint64_t)((c >> j) & 1) << qubits[j];
     P.off[c] = o;
   }
-  uint16_t* img = reinterpret_cast<uint16_t*>(P.b);
-  for (int o = 0; o < S::R; ++o) {
-    double w[S::R];
-    const int r = o >> 1;
-    double mx = 0.0;
-    for (int i = 0; i < S::R; ++i) {
-      const int c = i >> 1;
-      const double ur = U[2 * (r * S::D + c)], ui = U[2 * (r * S::D + c) + 1];
-      w[i] = (o & 1) == 0 ? ((i & 1) == 0 ? ur : -ui) : ((i & 1) == 0 ? ui : ur);
-      mx = std::max(mx, std::fabs(w[i]));
-    }
-    int ro = 0;
-    if (mx > 0.0) std::frexp(mx, &ro);
-    P.adj[o] = ro - 1038;
-    for (int i = 0; i < S::R; ++i) {
-      double rem = std::ldexp(w[i], 8 - ro);
-      for (int j = 0; j < kSlices; ++j) {
-        const double b = std::nearbyint(rem);
-        rem = (rem - b) * 512.0;
-        const float f = std::ldexp((float)b, -9 * j);
-        uint32_t bits;
-        std::memcpy(&bits, &f, 4);
-        const size_t at = j * S::B_SLICE + (o / 8) * S::SBO + (i / 8) * 128 + (o % 8) * 16 + (i % 8) * 2;
-        img[at / 2] = (uint16_t)(bits >> 16);
-      }
-    }
-  }
+  std::memcpy(P.u, U, sizeof(P.u));
 }
 
 template <int K>
 cudaError_t launch_tc(iqs_reg* r, const int* qubits, const double* U) {
   using S = TcShape<K>;
-  static TcParams<K> P;  // large (up to 12.6 KiB): kept off the host stack, filled under the lock below
+  static TcParams<K> P;  // large (up to 16.6 KiB): kept off the host stack, filled under the lock below
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
   make_params<K>(qubits, U, P);
@@ -539,13 +554,14 @@ cudaError_t launch_tc(iqs_reg* r, const int* qubits, const double* U) {
 
 }  // namespace
 
-bool kq_tensor_supported(int k) { return k >= 2 && k <= 4; }
+bool kq_tensor_supported(int k) { return k >= 2 && k <= 5; }
 
 cudaError_t launch_kq_c128_tensor(iqs_reg* r, int k, const int* qubits, const double* U) {
   switch (k) {
     case 2: return launch_tc<2>(r, qubits, U);
     case 3: return launch_tc<3>(r, qubits, U);
     case 4: return launch_tc<4>(r, qubits, U);
+    case 5: return launch_tc<5>(r, qubits, U);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -69,8 +69,6 @@ TARGETS = {
 @pytest.mark.parametrize("n", [5, 10, 13])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_apply_kq_matches_oracle(gpu_lib, dtype, math, n, k):
-    if dtype == "complex128" and k > 4:
-        pytest.skip("complex128 takes k <= 4")
     g = W.rng(3000 + 10 * n + k)
     psi = state(n, 3100 + n, dtype)
     r = make_reg(gpu_lib, n, dtype, math, psi)
@@ -143,7 +141,7 @@ def test_apply_kq_rejects_bad_arguments(gpu_lib):
     psi = state(n, 3401, "complex128")
     r = make_reg(gpu_lib, n, "complex128", None, psi)
     for qs, U in (([0, 0], np.eye(4)), ([0, 6], np.eye(4)), ([-1], np.eye(2)),
-                  ([0, 1, 2, 3, 4], np.eye(32))):     # k = 5 is complex64 only
+                  ([0, 1, 2, 3, 4, 5], np.eye(64))):     # k <= 5
         with pytest.raises(IQSError):
             r.apply_kq(qs, U)
     bad = np.eye(2, dtype=complex)

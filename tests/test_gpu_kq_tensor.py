@@ -1,5 +1,5 @@
 """GPU parity of the tensor-core complex128 k-qubit gate (iqs_apply_kq,
-variant 4: exact bf16 digit slices multiplied on tcgen05, k = 2..4) against
+variant 4: exact bf16 digit slices multiplied on tcgen05, k = 2..5) against
 the FP64 oracle, ``oracle.statevector.apply_kq``, on the same seeded inputs.
 
 Tolerance, per output real o of a group with R = 2^(k+1) reals, Wmax the
@@ -39,7 +39,7 @@ def restore_default_variants(gpu_lib):
     yield
     r = gpu_lib.Register(11, "complex128")
     r.set_math("emulated")
-    for k in (2, 3, 4):
+    for k in (2, 3, 4, 5):
         r.kq_set_variant(list(range(k)), 0, 8)
         r.kq_set_variant(list(range(6, 6 + k)), 0, 8)
     r.close()
@@ -95,11 +95,12 @@ TARGETS = {
     2: [[0, 1], [4, 0], [2, 9], [8, 5]],
     3: [[0, 1, 2], [6, 0, 3], [9, 4, 7]],
     4: [[0, 1, 2, 3], [3, 8, 0, 6], [9, 7, 5, 6]],
+    5: [[0, 1, 2, 3, 4], [4, 9, 0, 7, 2], [5, 6, 7, 8, 9]],
 }
 
 
 @pytest.mark.parametrize("n", [7, 10, 14])
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_tensor_kq_matches_oracle(gpu_lib, n, k):
     """Haar gates on several target sets; n = 7 leaves 8..32 groups (one
     partly filled 128-group tile), n = 14 spans 16..64 tiles."""
@@ -124,7 +125,7 @@ def test_tensor_kq_matches_oracle(gpu_lib, n, k):
     assert applied >= 2
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_tensor_kq_wide_dynamic_range_zeros_and_scaled_matrices(gpu_lib, k):
     """Groups whose magnitudes span 1e-150..1e3, groups with exact and
     negative zeros and one all-zero group, and matrices that are not unitary
@@ -137,7 +138,7 @@ def test_tensor_kq_wide_dynamic_range_zeros_and_scaled_matrices(gpu_lib, k):
     psi = psi * scales
     psi[::7] = 0.0
     psi[3::11] = complex(-0.0, -0.0)
-    qs = [1, 5, 8, 2][:k]
+    qs = [1, 5, 8, 2, 10][:k]
     xg = group_view(np.arange(psi.size), qs)
     psi[xg[5]] = 0.0                                   # one group all zero
     U = haar(k, g) * (2.0 ** g.integers(-40, 31, size=(1 << k, 1)))
@@ -156,23 +157,24 @@ def test_tensor_kq_wide_dynamic_range_zeros_and_scaled_matrices(gpu_lib, k):
     assert np.all(got[group_view(np.arange(psi.size), qs)[5]] == 0)
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_tensor_kq_matches_double_float_kernel_at_22_qubits(gpu_lib, k):
     """A 22-qubit state (64 MiB): the tensor-core gate against the
-    double-float kernel (variant 2) on the same input, and sampled groups
-    against the oracle; U then U^dagger brings the state back."""
+    double-float kernel (variant 2; native FP64 for k = 5, which has no
+    double-float kernel) on the same input, and sampled groups against the
+    oracle; U then U^dagger brings the state back."""
     n = 22
     g = W.rng(5300 + k)
     psi = W.gaussian_state(n, 5301)
-    qs = [[0, 1, 2, 3], [21, 3, 11, 16], [20, 21, 0, 7]][k - 2][:k]
+    qs = [[0, 1, 2, 3], [21, 3, 11, 16], [20, 21, 0, 7], [9, 2, 21, 14, 5]][k - 2][:k]
     U = haar(k, g)
     a = tensor_reg(gpu_lib, n, psi, qs)
     b = gpu_lib.Register(n, "complex128")
-    b.set_math("emulated")
+    b.set_math("emulated" if k < 5 else "native")
     b.upload(psi)
     a.apply_kq(qs, U)
     got = a.download()
-    b.kq_set_variant(qs, 2, 8)  # the double-float kernel
+    b.kq_set_variant(qs, 2, 8)  # the double-float kernel (k < 5)
     b.apply_kq(qs, U)
     other = b.download()
     assert np.max(np.abs(got - other)) <= 1e-14
