@@ -87,11 +87,9 @@ struct TcShape {
   static constexpr uint32_t B_SLICE = NP * KP * 2;
   static constexpr uint32_t B_BYTES = kSlices * B_SLICE;
   static constexpr uint32_t X_BYTES = kRows * D * 16;  // staged input of one tile: [element c][row m]
-  // shared memory: TMEM address slot at 0, mbarriers from 8, W's row
-  // exponents from 128 (NP words), partial group exponents from 1024
-  // (TEAMS x TPG x 128 words), then B, A, X
-  static constexpr uint32_t RO_OFF = 128;
-  static_assert(8 + 8 * TEAMS <= RO_OFF && RO_OFF + 4 * NP <= 1024, "header area");
+  // shared memory: TMEM address slot at 0, mbarriers from 8, partial group
+  // exponents from 1024 (TEAMS x TPG x 128 words), then B, A, X
+  static_assert(8 + 8 * TEAMS <= 1024, "header area");
   static constexpr uint32_t EMX_OFF = 1024;
   static constexpr uint32_t B_OFF = 4096;
   static_assert(EMX_OFF + TEAMS * TPG * 128 * 4 <= B_OFF, "exponent exchange area");
@@ -108,6 +106,7 @@ template <int K>
 struct TcParams {
   int pos[K];                    // target positions, ascending
   uint64_t off[1 << K];          // index offset of group element c
+  int ro[TcShape<K>::NP];        // per row o of W: max_i |W[o][i]| in [2^(ro - 1), 2^ro); 0 for a zero row
   double u[2 << (2 * K)];        // U row-major, (re, im) pairs
 };
 
@@ -232,20 +231,6 @@ __device__ __forceinline__ double w_entry(const TcParams<K>& P, int o, int i) {
   return (o & 1) == 0 ? ((i & 1) == 0 ? ur : -ui) : ((i & 1) == 0 ? ui : ur);
 }
 
-// ro with max_i |W[o][i]| in [2^(ro - 1), 2^ro) (0 for a zero or padding
-// row): row o is split after scaling by 2^(8 - ro), and its outputs carry
-// 2^(ro - 1038) besides the group's own power of two.
-template <int K>
-__device__ __forceinline__ int row_exponent(const TcParams<K>& P, int o) {
-  constexpr int R = 2 << K;
-  if (o >= R) return 0;
-  double mx = 0.0;
-  for (int i = 0; i < R; ++i) mx = fmax(mx, fabs(w_entry<K>(P, o, i)));
-  int ro = 0;
-  if (mx > 0.0) frexp(mx, &ro);
-  return ro;
-}
-
 __device__ __forceinline__ float digit_weight(int j) {
   return __uint_as_float((uint32_t)(127 - 9 * j) << 23);  // 2^(-9 j), j <= 5
 }
@@ -314,15 +299,13 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   // W's digit slices (zero padding included) and row exponents; the A slices
   // zeroed once, so that their padding columns (k = 2: 8 reals padded to
   // K = 16) stay zero.
-  int* sro = reinterpret_cast<int*>(smem + S::RO_OFF);
   for (int i = tid; i < (int)(S::B_BYTES / 16); i += blockDim.x) reinterpret_cast<uint4*>(Bs)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < (int)(S::TEAMS * S::A_BYTES / 16); i += blockDim.x)
     reinterpret_cast<uint4*>(As)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (int o = tid; o < S::NP; o += blockDim.x) sro[o] = row_exponent<K>(P, o);
   __syncthreads();
   for (int e = tid; e < S::R * S::R; e += blockDim.x) {
     const int o = e / S::R, i = e % S::R;
-    double rem = ldexp(w_entry<K>(P, o, i), 8 - sro[o]);
+    double rem = ldexp(w_entry<K>(P, o, i), 8 - P.ro[o]);
     uint16_t* at = reinterpret_cast<uint16_t*>(Bs + (o / 8) * S::SBO + (i / 8) * 128 + (o % 8) * 16 + (i % 8) * 2);
 #pragma unroll
     for (int j = 0; j < kSlices; ++j) {
@@ -355,10 +338,11 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
   const uint64_t stride = (uint64_t)gridDim.x * S::TEAMS;
   // row exponent range of W (the fast epilogue needs every output normal)
-  int adj_lo = sro[0] - 1038, adj_hi = adj_lo;
+  int adj_lo = P.ro[0] - 1038, adj_hi = adj_lo;
+#pragma unroll
   for (int o = 1; o < S::R; ++o) {
-    adj_lo = min(adj_lo, sro[o] - 1038);
-    adj_hi = max(adj_hi, sro[o] - 1038);
+    adj_lo = min(adj_lo, P.ro[o] - 1038);
+    adj_hi = max(adj_hi, P.ro[o] - 1038);
   }
   uint32_t phase = 0;
   unsigned bad = 0;
@@ -469,11 +453,11 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
           combine(v, q + 1, s1, l1);
           double2 y;
           if (fast) {
-            y.x = join_scaled(s0, l0, e0 + sro[o] - 1038);
-            y.y = join_scaled(s1, l1, e0 + sro[o + 1] - 1038);
+            y.x = join_scaled(s0, l0, e0 + P.ro[o] - 1038);
+            y.y = join_scaled(s1, l1, e0 + P.ro[o + 1] - 1038);
           } else {
-            y.x = scale_out(dfx::join(s0, l0), e0 + sro[o] - 1038, bad);
-            y.y = scale_out(dfx::join(s1, l1), e0 + sro[o + 1] - 1038, bad);
+            y.x = scale_out(dfx::join(s0, l0), e0 + P.ro[o] - 1038, bad);
+            y.y = scale_out(dfx::join(s1, l1), e0 + P.ro[o + 1] - 1038, bad);
           }
           if constexpr (LOW)
             *reinterpret_cast<double2*>(out_slot<K>(A, wq, sub, lane, ch * 4 + q / 2)) = y;
@@ -525,6 +509,17 @@ void make_params(const int* qubits, const double* U, TcParams<K>& P) {
     P.off[c] = o;
   }
   std::memcpy(P.u, U, sizeof(P.u));
+  for (int o = 0; o < S::R; ++o) {  // row exponents (the digits themselves are formed on the device)
+    const int r = o >> 1;
+    double mx = 0.0;
+    for (int c = 0; c < S::D; ++c) {
+      const double ur = U[2 * (r * S::D + c)], ui = U[2 * (r * S::D + c) + 1];
+      mx = std::max(mx, std::max(std::fabs(ur), std::fabs(ui)));  // W's rows 2r and 2r + 1 hold the same magnitudes
+    }
+    int ro = 0;
+    if (mx > 0.0) std::frexp(mx, &ro);
+    P.ro[o] = ro;
+  }
 }
 
 template <int K>
