@@ -80,6 +80,8 @@ def test_invalid_arguments_are_rejected_before_any_device_call(lib):
     assert lib.lib.iqs_apply_1q(None, 0, U) == 1
     out = C.c_double()
     assert lib.lib.iqs_probability(None, 0, C.byref(out)) == 1
+    qs = (C.c_int * 2)(0, 1)
+    assert lib.lib.iqs_kq_set_variant(None, 2, qs, 4, 1) == 1
 
 
 def test_mat8_is_row_major_re_im():
