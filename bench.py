@@ -1066,9 +1066,8 @@ def main(argv=None):
             e2e = {"value": round(world * bytes_step * args.e2e_steps / dt / 1e9, 2), "unit": "GB/s",
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * (n + 2),
                    "steps": args.e2e_steps,
-                   "path": f"per step: iqs_copy_to_device in {n_chunks} slices under the gates on qubits 0..{cq - 1} "
-                           f"per slice, rest of the sweep, iqs_copy_to_host; two device buffers, so a step's "
-                           f"copies overlap the neighbouring steps' gates"}
+                   "path": f"iqs_copy_to_device in {n_chunks} slices (gates on qubits <{cq} per slice), sweep, "
+                           f"iqs_copy_to_host; 2 buffers overlap copies with gates"}
             for B in bufs:
                 for pr in B["parts"]:
                     pr.close()
