@@ -849,13 +849,13 @@ def profile_pool(spec: str) -> int:
 
 def profile_ops(n: int) -> int:
     """Single invocations for a profiler: on an n-qubit complex64 and complex128
-    Gaussian state, apply_kq with k = 2..5 (complex64) or 2..4 (complex128) on
-    the lowest and the highest k qubits, one 10-qubit marginal and one
-    2^16-shot sampling call, each once."""
+    uniform-superposition state, apply_kq with k = 2..5 on the lowest and then
+    the highest k qubits, one 10-qubit marginal and one 2^16-shot sampling
+    call, each once."""
     import paper_2001_10554_gb300 as iqs
     import workloads as W
     g = W.rng(5)
-    for dtype, ks in (("complex64", (2, 3, 4, 5)), ("complex128", (2, 3, 4))):
+    for dtype, ks in (("complex64", (2, 3, 4, 5)), ("complex128", (2, 3, 4, 5))):
         reg = iqs.Register(n, dtype)
         reg.init_uniform()
         for k in ks:
