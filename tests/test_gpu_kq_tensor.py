@@ -187,3 +187,32 @@ def test_tensor_kq_matches_double_float_kernel_at_22_qubits(gpu_lib, k):
     assert np.max(np.abs(a.download() - psi)) <= 1e-14
     a.close()
     b.close()
+
+
+def test_tensor_kq_group_scales_cover_the_fp64_range_and_flag_nan(gpu_lib):
+    """Each group carries its own power of two, so groups at 2^70, 2^-300 and
+    2^-1000 (far outside the double-float kernel's 2^-80..2^64 window; the
+    last one on the careful epilogue path) stay within the per-output bound;
+    an Inf or NaN amplitude raises IQS_ERANGE at the next check."""
+    from paper_2001_10554_gb300 import IQSError
+    n, qs = 8, [0, 1, 2]
+    g = W.rng(5400)
+    psi = W.gaussian_state(n, 5401)
+    psi[:64] *= 2.0 ** 70
+    psi[64:128] *= 2.0 ** -300
+    psi[128:192] *= 2.0 ** -1000
+    U = haar(3, g)
+    r = tensor_reg(gpu_lib, n, psi, qs)
+    r.apply_kq(qs, U)
+    r.synchronize()
+    got = r.download()
+    check_groups(got, sv.apply_kq(psi, qs, U), psi, qs, U)
+    bad = psi.copy()
+    bad[200] = np.nan
+    r.upload(bad)
+    r.apply_kq(qs, U)
+    with pytest.raises(IQSError) as ei:
+        r.synchronize()
+    assert ei.value.status == 6
+    r.synchronize()  # flag cleared
+    r.close()
